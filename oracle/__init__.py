@@ -1,0 +1,222 @@
+"""Python access to the FP64 oracle (hmfsr_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the oracle is a plain CPU restatement of the paper's method,
+used by the tests, the smoke check and the benchmark's CPU-baseline leg to check and
+time the CUDA path.  The product path never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hmfsr_oracle.c")
+_HDR = os.path.join(_HERE, "hmfsr_oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction, OpenMP)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
+        "t", "s1", "s2", "m_th", "noise_a", "noise_b")]
+
+
+@dataclass
+class MergeParams:
+    """Merge tuning parameters (supplement S.2 ranges; mid-range defaults)."""
+    k_detail: float = 0.29
+    k_denoise: float = 4.0
+    d_th: float = 0.005
+    d_tr: float = 0.012
+    k_stretch: float = 4.0
+    k_shrink: float = 2.0
+    t: float = 0.12
+    s1: float = 12.0
+    s2: float = 2.0
+    m_th: float = 0.8
+    noise_a: float = 1.0
+    noise_b: float = 4.0
+
+    def c(self) -> _Params:
+        # promote the float32 values the CUDA path sees
+        return _Params(*[float(np.float32(getattr(self, f.name))) for f in fields(self)])
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER
+        u16p, i32p, f32p, f64p = P(ctypes.c_uint16), P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_double)
+        ci = ctypes.c_int
+        L.orc_luma.argtypes = [u16p, ci, ci, i32p]
+        L.orc_structure_tensor.argtypes = [u16p, ci, ci, ci, ci, P(ctypes.c_int64)]
+        L.orc_kernel_from_tensor.argtypes = [ctypes.c_int64] * 3 + [P(_Params), ci, f64p]
+        L.orc_omega_plane.argtypes = [u16p, ci, ci, P(_Params), ci, f64p]
+        L.orc_tile_strength.argtypes = [f32p, ci, ci, P(_Params), f64p, f64p]
+        L.orc_robustness.argtypes = [u16p, u16p, ci, ci, f32p, ci, P(_Params), ci, f64p, f64p]
+        L.orc_merge_rows.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci, ci, ci,
+                                     f64p, f64p, ci]
+        L.orc_merge_pixels.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci, i32p, ci,
+                                       f64p, ci]
+        L.orc_align.argtypes = [u16p, ci, ci, ci, ci, ci, ci, i32p, ci, i32p, f64p, i32p, ci]
+        for name in ("orc_luma", "orc_structure_tensor", "orc_kernel_from_tensor", "orc_omega_plane",
+                     "orc_tile_strength", "orc_robustness", "orc_merge_rows", "orc_merge_pixels", "orc_align"):
+            getattr(L, name).restype = ci
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _u16(a) -> np.ndarray:
+    a = np.asarray(a)
+    if a.dtype != np.uint16:
+        a = a.astype(np.uint16)
+    return np.ascontiguousarray(a)
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise ValueError(f"oracle {what} failed with {rc}")
+    return rc
+
+
+def n_tiles(h: int, w: int, tile: int):
+    return -(-h // tile), -(-w // tile)
+
+
+def luma(raw) -> np.ndarray:
+    raw = _u16(raw)
+    h, w = raw.shape
+    out = np.empty((h // 2, w // 2), np.int32)
+    _check(lib().orc_luma(_ptr(raw, ctypes.c_uint16), h, w, _ptr(out, ctypes.c_int32)), "luma")
+    return out
+
+
+def structure_tensor(raw, u: int, v: int) -> tuple:
+    raw = _u16(raw)
+    out = np.zeros(3, np.int64)
+    _check(lib().orc_structure_tensor(_ptr(raw, ctypes.c_uint16), raw.shape[0], raw.shape[1], u, v,
+                                      _ptr(out, ctypes.c_int64)), "structure_tensor")
+    return tuple(int(x) for x in out)
+
+
+def kernel_from_tensor(a: int, b: int, c: int, params: MergeParams, wl: int = 4095) -> dict:
+    out = np.zeros(11, np.float64)
+    p = params.c()
+    _check(lib().orc_kernel_from_tensor(a, b, c, ctypes.byref(p), wl, _ptr(out, ctypes.c_double)), "kernel")
+    keys = ("Oxx", "Oxy", "Oyy", "l1", "l2", "A", "D", "k_along", "k_across", "cos2t", "sin2t")
+    return dict(zip(keys, out.tolist()))
+
+
+def omega_plane(raw, params: MergeParams, wl: int = 4095) -> np.ndarray:
+    raw = _u16(raw)
+    h, w = raw.shape
+    out = np.empty((3, h // 2, w // 2), np.float64)
+    p = params.c()
+    _check(lib().orc_omega_plane(_ptr(raw, ctypes.c_uint16), h, w, ctypes.byref(p), wl,
+                                 _ptr(out, ctypes.c_double)), "omega_plane")
+    return out
+
+
+def tile_strength(motion_frame, params: MergeParams):
+    mv = np.ascontiguousarray(motion_frame, dtype=np.float32)
+    ty, tx = mv.shape[:2]
+    M = np.empty((ty, tx), np.float64)
+    s = np.empty((ty, tx), np.float64)
+    p = params.c()
+    _check(lib().orc_tile_strength(_ptr(mv, ctypes.c_float), ty, tx, ctypes.byref(p),
+                                   _ptr(M, ctypes.c_double), _ptr(s, ctypes.c_double)), "tile_strength")
+    return M, s
+
+
+def robustness(base, alt, motion_alt, tile: int, params: MergeParams, wl: int = 4095):
+    base, alt = _u16(base), _u16(alt)
+    h, w = base.shape
+    mv = np.ascontiguousarray(motion_alt, dtype=np.float32)
+    R = np.empty((h // 2, w // 2), np.float64)
+    Rh = np.empty((h // 2, w // 2), np.float64)
+    p = params.c()
+    _check(lib().orc_robustness(_ptr(base, ctypes.c_uint16), _ptr(alt, ctypes.c_uint16), h, w,
+                                _ptr(mv, ctypes.c_float), tile, ctypes.byref(p), wl,
+                                _ptr(R, ctypes.c_double), _ptr(Rh, ctypes.c_double)), "robustness")
+    return R, Rh
+
+
+def out_size(h: int, w: int, scale) -> tuple:
+    num, den = scale
+    return (h * num) // den, (w * num) // den
+
+
+def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: int = 16, wl: int = 4095,
+          rows=None, with_den: bool = False, n_threads: int = 0):
+    """Oracle merge of output rows [y0, y1) (all rows by default): double [3, rows, Wo]."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    mv = np.ascontiguousarray(motion, dtype=np.float32)
+    ty, tx = n_tiles(h, w, tile)
+    if mv.shape != (n, ty, tx, 2):
+        raise ValueError(f"motion must be [{n},{ty},{tx},2], got {mv.shape}")
+    ho, wo = out_size(h, w, scale)
+    y0, y1 = (0, ho) if rows is None else rows
+    out = np.empty((3, y1 - y0, wo), np.float64)
+    den = np.empty((3, y1 - y0, wo), np.float64) if with_den else None
+    p = params.c()
+    _check(lib().orc_merge_rows(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
+                                ctypes.byref(p), wl, scale[0], scale[1], y0, y1, _ptr(out, ctypes.c_double),
+                                _ptr(den, ctypes.c_double) if den is not None else None, n_threads), "merge")
+    return (out, den) if with_den else out
+
+
+def merge_pixels(burst, motion, params: MergeParams, xy, scale=(1, 1), ref: int = 0, tile: int = 16,
+                 wl: int = 4095, n_threads: int = 0) -> np.ndarray:
+    """Oracle merge of the output pixels xy[k] = (X, Y): double [k, 3]."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    mv = np.ascontiguousarray(motion, dtype=np.float32)
+    xy = np.ascontiguousarray(xy, dtype=np.int32)
+    out = np.empty((xy.shape[0], 3), np.float64)
+    p = params.c()
+    _check(lib().orc_merge_pixels(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
+                                  ctypes.byref(p), wl, scale[0], scale[1], _ptr(xy, ctypes.c_int32),
+                                  xy.shape[0], _ptr(out, ctypes.c_double), n_threads), "merge_pixels")
+    return out
+
+
+def align(burst, ref: int = 0, tile: int = 16, n_levels: int = 4, radius=(1, 4, 4, 4), lk_iters: int = 3,
+          n_threads: int = 0):
+    """Oracle alignment: (motion_int int32 [n,ty,tx,2] half-res px, motion float64
+    [n,ty,tx,2] raw px, lk_skipped int32 [n,ty,tx], n_levels_used)."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    ty, tx = n_tiles(h, w, tile)
+    mi = np.empty((n, ty, tx, 2), np.int32)
+    mf = np.empty((n, ty, tx, 2), np.float64)
+    fl = np.empty((n, ty, tx), np.int32)
+    rad = np.zeros(4, np.int32)
+    rad[:len(radius)] = radius
+    nl = _check(lib().orc_align(_ptr(burst, ctypes.c_uint16), n, h, w, ref, tile, n_levels,
+                                _ptr(rad, ctypes.c_int32), lk_iters, _ptr(mi, ctypes.c_int32),
+                                _ptr(mf, ctypes.c_double), _ptr(fl, ctypes.c_int32), n_threads), "align")
+    return mi, mf, fl, nl

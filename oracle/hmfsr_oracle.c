@@ -1,0 +1,854 @@
+/*
+ * FP64 oracle for the handheld multi-frame super-resolution merge and tile alignment
+ * (Wronski et al. 2019).  TEST INFRASTRUCTURE ONLY: a plain, slow CPU restatement of the
+ * paper's equations, used to check the CUDA path; it shares no code with that path.
+ *
+ * Every function evaluates the paper's definitions literally, per pixel, in double
+ * precision.  Where the paper is silent or ambiguous, the reading taken is stated at the
+ * place it is used.  Build: gcc -O2 -ffp-contract=off -fopenmp (no fast-math), so that
+ * the FP64 decisions (motion-prior threshold, alignment conditioning guard) are the plain
+ * IEEE operation sequence written here.
+ *
+ * Parity notes (pins live in tests/): every function below is pinned by at least one
+ * property test; none is "parity unpinned".
+ */
+#include "hmfsr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------------------ */
+/* small helpers                                                                         */
+/* ------------------------------------------------------------------------------------ */
+static inline int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static inline double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+static inline long long floor_div(long long a, long long b) /* b > 0 */
+{
+    long long q = a / b;
+    if ((a % b) != 0 && a < 0) q -= 1;
+    return q;
+}
+
+static void set_threads(int n_threads)
+{
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+}
+
+/* CFA channel of raw pixel (x, y): RGGB -> 0 R, 1 G, 2 B. */
+static inline int cfa_channel(int x, int y) { return (x & 1) + (y & 1); }
+
+/* ------------------------------------------------------------------------------------ */
+/* Half-res luminance and guide image (Sec. 5.1.2; Sec. 5.2.2)                          */
+/* ------------------------------------------------------------------------------------ */
+/* Lq = R + G1 + G2 + B of the quad.  The paper says the four channels of a Bayer quad
+ * are combined into one luminance pixel without saying how; the plain sum is used. */
+static inline int32_t luma_at(const uint16_t *raw, int h, int w, int u, int v)
+{
+    int hh = h / 2, wh = w / 2;
+    u = clampi(u, 0, wh - 1);
+    v = clampi(v, 0, hh - 1);
+    const uint16_t *r0 = raw + (size_t)(2 * v) * w + 2 * u;
+    const uint16_t *r1 = r0 + w;
+    return (int32_t)r0[0] + r0[1] + r1[0] + r1[1];
+}
+
+/* Guide pixel (Sec. 5.2.2): R and B as they are, green = average of the two greens.
+ * Returned as integers: c = 0 -> R, 1 -> G1 + G2 (twice the guide's green), 2 -> B. */
+static inline int32_t guide_at(const uint16_t *raw, int h, int w, int u, int v, int c)
+{
+    int hh = h / 2, wh = w / 2;
+    u = clampi(u, 0, wh - 1);
+    v = clampi(v, 0, hh - 1);
+    const uint16_t *r0 = raw + (size_t)(2 * v) * w + 2 * u;
+    const uint16_t *r1 = r0 + w;
+    if (c == 0) return r0[0];
+    if (c == 1) return (int32_t)r0[1] + r1[0];
+    return r1[1];
+}
+
+int orc_luma(const uint16_t *raw, int h, int w, int32_t *lq)
+{
+    if (!raw || !lq || h < 2 || w < 2 || (h & 1) || (w & 1)) return -1;
+    int hh = h / 2, wh = w / 2;
+    for (int v = 0; v < hh; ++v)
+        for (int u = 0; u < wh; ++u) lq[(size_t)v * wh + u] = luma_at(raw, h, w, u, v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Structure tensor (Eq. 3)                                                              */
+/* ------------------------------------------------------------------------------------ */
+/* Reading of "finite forward differencing in a 3x3 window giving four horizontal and
+ * vertical gradient values": the 3x3 half-res window centred on (u,v) holds four 2x2
+ * sub-squares with top-left corners (u+i, v+j), i, j in {-1, 0}.  Each sub-square gives
+ * one forward-difference gradient (the sum of its two horizontal, resp. vertical,
+ * differences); the tensor sums the four outer products.  Reads clamp at the border.
+ * Exact in int64. */
+static void tensor_at(const uint16_t *raw, int h, int w, int u, int v, int64_t *a, int64_t *b, int64_t *c)
+{
+    int64_t sa = 0, sb = 0, sc = 0;
+    for (int j = -1; j <= 0; ++j)
+        for (int i = -1; i <= 0; ++i) {
+            int64_t l00 = luma_at(raw, h, w, u + i, v + j);
+            int64_t l10 = luma_at(raw, h, w, u + i + 1, v + j);
+            int64_t l01 = luma_at(raw, h, w, u + i, v + j + 1);
+            int64_t l11 = luma_at(raw, h, w, u + i + 1, v + j + 1);
+            int64_t gx = (l10 - l00) + (l11 - l01);
+            int64_t gy = (l01 - l00) + (l11 - l10);
+            sa += gx * gx;
+            sb += gx * gy;
+            sc += gy * gy;
+        }
+    *a = sa; *b = sb; *c = sc;
+}
+
+int orc_structure_tensor(const uint16_t *raw, int h, int w, int u, int v, int64_t out[3])
+{
+    if (!raw || !out || h < 2 || w < 2) return -1;
+    tensor_at(raw, h, w, u, v, &out[0], &out[1], &out[2]);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Kernel covariance (Eq. 4 with the supplement's kernel-shape heuristics)               */
+/* ------------------------------------------------------------------------------------ */
+/* Eigen-analysis of [[a, b], [b, c]]: lambda_{1,2} = (tr +- r)/2 with
+ * r = sqrt((a-c)^2 + 4 b^2); the dominant eigenvector e1 is at angle theta with
+ * cos 2theta = (a-c)/r, sin 2theta = 2b/r.  When a == c and b == 0 the direction is
+ * undefined; the reading taken is theta = 0 (e1 = x axis).
+ *
+ * Heuristics (supplement S.1): A = 1 + sqrt((l1-l2)/(l1+l2)) (A = 1 when l1+l2 = 0);
+ * D = clamp(1 - sqrt(l1)/D_tr + D_th, 0, 1), printed formula taken literally, with l1 in
+ * units of the luminance normalised to [0,1]: one forward-difference gradient of the sum
+ * luminance spans 2 pixel differences of 4 samples, so g_norm = g / (8 WL), and the
+ * tensor is the mean over its four gradients, l_norm = l / (4 (8 WL)^2).
+ * k^_stretch = k_detail * k_stretch * A, k^_shrink = k_detail / (k_shrink * A), and
+ * k_i = ((1-D) k^_i + D k_detail k_denoise)^2 (variances, raw px^2).
+ *
+ * Reading of Eq. 4's assignment: the text stretches kernels ALONG edges, i.e. along
+ * e2 (perpendicular to the dominant gradient), so the stretched variance goes on e2 and
+ * the shrunk one on e1:  Omega = k_across e1 e1^T + k_along e2 e2^T. */
+static void kernel_from_tensor(int64_t a, int64_t b, int64_t c, const orc_params *p, int wl, double out[11])
+{
+    int64_t tr_i = a + c;
+    double amc = (double)(a - c);
+    double r = sqrt(amc * amc + 4.0 * (double)b * (double)b);
+    double tr = (double)tr_i;
+    double l1 = 0.5 * (tr + r), l2 = 0.5 * (tr - r);
+    double cs, sn;
+    if (a == c && b == 0) { cs = 1.0; sn = 0.0; }
+    else { cs = amc / r; sn = 2.0 * (double)b / r; }
+    double A = (tr_i == 0) ? 1.0 : 1.0 + sqrt(r / tr);
+    double norm = 4.0 * (8.0 * wl) * (8.0 * wl);
+    double l1n = l1 / norm;
+    double D = clampd(1.0 - sqrt(l1n) / p->d_tr + p->d_th, 0.0, 1.0);
+    double kh_along = p->k_detail * (p->k_stretch * A);
+    double kh_across = p->k_detail / (p->k_shrink * A);
+    double kd = p->k_detail * p->k_denoise;
+    double k_along = (1.0 - D) * kh_along + D * kd;
+    double k_across = (1.0 - D) * kh_across + D * kd;
+    k_along *= k_along;
+    k_across *= k_across;
+    /* e1 e1^T = 1/2 [[1+cs, sn], [sn, 1-cs]],  e2 e2^T = I - e1 e1^T */
+    double e1xx = 0.5 * (1.0 + cs), e1xy = 0.5 * sn, e1yy = 0.5 * (1.0 - cs);
+    out[0] = k_across * e1xx + k_along * (1.0 - e1xx);
+    out[1] = k_across * e1xy - k_along * e1xy;
+    out[2] = k_across * e1yy + k_along * (1.0 - e1yy);
+    out[3] = l1; out[4] = l2; out[5] = A; out[6] = D;
+    out[7] = k_along; out[8] = k_across; out[9] = cs; out[10] = sn;
+}
+
+int orc_kernel_from_tensor(int64_t a, int64_t b, int64_t c, const orc_params *p, int wl, double out[11])
+{
+    if (!p || !out || wl <= 0) return -1;
+    kernel_from_tensor(a, b, c, p, wl, out);
+    return 0;
+}
+
+static void omega_at(const uint16_t *raw, int h, int w, int u, int v, const orc_params *p, int wl, double om[3])
+{
+    int64_t a, b, c;
+    double k[11];
+    tensor_at(raw, h, w, u, v, &a, &b, &c);
+    kernel_from_tensor(a, b, c, p, wl, k);
+    om[0] = k[0]; om[1] = k[1]; om[2] = k[2];
+}
+
+int orc_omega_plane(const uint16_t *raw, int h, int w, const orc_params *p, int wl, double *omega)
+{
+    if (!raw || !p || !omega || h < 2 || w < 2 || (h & 1) || (w & 1)) return -1;
+    int hh = h / 2, wh = w / 2;
+    size_t plane = (size_t)hh * wh;
+#pragma omp parallel for schedule(static)
+    for (int v = 0; v < hh; ++v)
+        for (int u = 0; u < wh; ++u) {
+            double om[3];
+            omega_at(raw, h, w, u, v, p, wl, om);
+            for (int k = 0; k < 3; ++k) omega[k * plane + (size_t)v * wh + u] = om[k];
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Motion prior (Eq. 7-8)                                                                */
+/* ------------------------------------------------------------------------------------ */
+/* M = sqrt(Mx^2 + My^2), Mx / My = max - min of the tile vectors over the 3x3 tile
+ * neighbourhood (tiles outside the grid are left out); s = s1 if M > M_th else s2. */
+static double tile_M(const float *motion, int ty, int tx, int y, int x)
+{
+    double mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    for (int j = -1; j <= 1; ++j)
+        for (int i = -1; i <= 1; ++i) {
+            int yy = y + j, xx = x + i;
+            if (yy < 0 || yy >= ty || xx < 0 || xx >= tx) continue;
+            const float *mv = motion + ((size_t)yy * tx + xx) * 2;
+            double vx = (double)mv[0], vy = (double)mv[1];
+            if (vx < mnx) mnx = vx;
+            if (vx > mxx) mxx = vx;
+            if (vy < mny) mny = vy;
+            if (vy > mxy) mxy = vy;
+        }
+    double Mx = mxx - mnx, My = mxy - mny;
+    double sq = Mx * Mx + My * My;
+    return sqrt(sq);
+}
+
+int orc_tile_strength(const float *motion, int ty, int tx, const orc_params *p, double *M, double *s)
+{
+    if (!motion || !p || ty <= 0 || tx <= 0) return -1;
+    for (int y = 0; y < ty; ++y)
+        for (int x = 0; x < tx; ++x) {
+            double m = tile_M(motion, ty, tx, y, x);
+            if (M) M[(size_t)y * tx + x] = m;
+            if (s) s[(size_t)y * tx + x] = (m > p->m_th) ? p->s1 : p->s2;
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Robustness (Eq. 5, 6, 9; Sec. 5.2.2)                                                  */
+/* ------------------------------------------------------------------------------------ */
+/* 3x3 box sum of a guide channel (clamped reads); `sq` selects the sum of squares. */
+static int64_t box_sum(const uint16_t *raw, int h, int w, int u, int v, int c, int sq)
+{
+    int64_t s = 0;
+    for (int j = -1; j <= 1; ++j)
+        for (int i = -1; i <= 1; ++i) {
+            int64_t g = guide_at(raw, h, w, u + i, v + j, c);
+            s += sq ? g * g : g;
+        }
+    return s;
+}
+
+/* Guide-channel 3x3 mean of frame `raw` at (u,v), in DN of the guide image (green =
+ * average of the two greens). */
+static double box_mean(const uint16_t *raw, int h, int w, int u, int v, int c)
+{
+    double s = (double)box_sum(raw, h, w, u, v, c, 0);
+    return (c == 1) ? s / 18.0 : s / 9.0;
+}
+
+/* Bilinear sample of the 3x3 mean of frame `raw` at continuous half-res (fx, fy);
+ * reads clamp at the border. */
+static double mean_bilinear(const uint16_t *raw, int h, int w, double fx, double fy, int c)
+{
+    double x0 = floor(fx), y0 = floor(fy);
+    double ax = fx - x0, ay = fy - y0;
+    int ix = (int)x0, iy = (int)y0;
+    double m00 = box_mean(raw, h, w, ix, iy, c);
+    double m10 = box_mean(raw, h, w, ix + 1, iy, c);
+    double m01 = box_mean(raw, h, w, ix, iy + 1, c);
+    double m11 = box_mean(raw, h, w, ix + 1, iy + 1, c);
+    return (1.0 - ay) * ((1.0 - ax) * m00 + ax * m10) + ay * ((1.0 - ax) * m01 + ax * m11);
+}
+
+typedef struct {
+    int h, w, tile, ty, tx, wl;
+    const orc_params *p;
+} rob_geom;
+
+/* Statistical robustness R at base half-res pixel (u,v) for frame `alt`.
+ * Readings taken where the paper is silent:
+ *  - sigma_ms (local spatial std) comes from the base frame; the local means of both
+ *    frames are compared, the aligned frame's mean being sampled bilinearly at the
+ *    position displaced by the tile's vector (v/2 in half-res px).  The tile is the one
+ *    holding the half-res pixel: floor(2u / tile).
+ *  - noise model: the paper tabulates sigma_md and d_md by Monte Carlo; here the closed
+ *    form for the linear model var(x) = a x + b at x = clamp(mu_base, 0, WL) is used,
+ *    halved for the green guide channel (mean of two samples): sigma_md = sqrt(var),
+ *    d_md = sqrt(2 var / 9) (difference of two 9-sample means).
+ *  - the colour difference and sigma are vectors over (R, G, B); the ratio in Eq. 5 is
+ *    |d|^2 / max(|sigma|^2, 1e-12 WL^2).
+ *  - R is clamped to [0, 1] (a weight of one merges fully, zero rejects). */
+static double robustness_at(const uint16_t *base, const uint16_t *alt, const float *motion_alt,
+                            const double *s_tile, const rob_geom *g, int u, int v)
+{
+    const orc_params *p = g->p;
+    int tyi = clampi((2 * v) / g->tile, 0, g->ty - 1);
+    int txi = clampi((2 * u) / g->tile, 0, g->tx - 1);
+    const float *mv = motion_alt + ((size_t)tyi * g->tx + txi) * 2;
+    double fx = (double)u + 0.5 * (double)mv[0];
+    double fy = (double)v + 0.5 * (double)mv[1];
+    double dd = 0.0, ss = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double s1 = (double)box_sum(base, g->h, g->w, u, v, c, 0);
+        double s2 = (double)box_sum(base, g->h, g->w, u, v, c, 1);
+        double gs = (c == 1) ? 2.0 : 1.0; /* green guide = (G1 + G2) / 2 */
+        double mu = s1 / (9.0 * gs);
+        double var_ms = (9.0 * s2 - s1 * s1) / (81.0 * gs * gs);
+        if (var_ms < 0.0) var_ms = 0.0;
+        double sigma_ms = sqrt(var_ms);
+        double mu_n = mean_bilinear(alt, g->h, g->w, fx, fy, c);
+        double d_ms = mu - mu_n;
+        double var_md = (p->noise_a * clampd(mu, 0.0, (double)g->wl) + p->noise_b) / gs;
+        if (var_md < 0.0) var_md = 0.0;
+        double sigma_md = sqrt(var_md);
+        double d_md = sqrt(2.0 * var_md / 9.0);
+        double sigma = sigma_ms > sigma_md ? sigma_ms : sigma_md;       /* Eq. 6 */
+        double den = d_ms * d_ms + d_md * d_md;
+        double d = den > 0.0 ? d_ms * (d_ms * d_ms) / den : 0.0;        /* Eq. 6 */
+        dd += d * d;
+        ss += sigma * sigma;
+    }
+    double eps = 1e-12 * (double)g->wl * (double)g->wl;
+    double ratio = dd / (ss > eps ? ss : eps);
+    double s = s_tile[(size_t)tyi * g->tx + txi];
+    return clampd(s * exp(-ratio) - p->t, 0.0, 1.0);                     /* Eq. 5 */
+}
+
+/* Rhat = min of R over the 5x5 window of valid pixels (Eq. 9). */
+static double rhat_from_R(const double *R, int hh, int wh, int u, int v)
+{
+    double m = INFINITY;
+    for (int j = -2; j <= 2; ++j)
+        for (int i = -2; i <= 2; ++i) {
+            int uu = u + i, vv = v + j;
+            if (uu < 0 || uu >= wh || vv < 0 || vv >= hh) continue;
+            double r = R[(size_t)vv * wh + uu];
+            if (r < m) m = r;
+        }
+    return m;
+}
+
+int orc_robustness(const uint16_t *base, const uint16_t *alt, int h, int w, const float *motion_alt,
+                   int tile, const orc_params *p, int wl, double *R, double *Rhat)
+{
+    if (!base || !alt || !motion_alt || !p || h < 2 || w < 2 || (h & 1) || (w & 1) || tile < 2 || (tile & 1))
+        return -1;
+    int hh = h / 2, wh = w / 2;
+    rob_geom g = { h, w, tile, (h + tile - 1) / tile, (w + tile - 1) / tile, wl, p };
+    double *s_tile = (double *)malloc(sizeof(double) * (size_t)g.ty * g.tx);
+    double *Rb = R ? R : (double *)malloc(sizeof(double) * (size_t)hh * wh);
+    if (!s_tile || !Rb) { free(s_tile); if (!R) free(Rb); return -2; }
+    orc_tile_strength(motion_alt, g.ty, g.tx, p, NULL, s_tile);
+#pragma omp parallel for schedule(static)
+    for (int v = 0; v < hh; ++v)
+        for (int u = 0; u < wh; ++u) Rb[(size_t)v * wh + u] = robustness_at(base, alt, motion_alt, s_tile, &g, u, v);
+    if (Rhat) {
+#pragma omp parallel for schedule(static)
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) Rhat[(size_t)v * wh + u] = rhat_from_R(Rb, hh, wh, u, v);
+    }
+    free(s_tile);
+    if (!R) free(Rb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Merge (Eq. 1-2)                                                                       */
+/* ------------------------------------------------------------------------------------ */
+/* Per-frame data for the merge: Omega and Rhat on half-res rows [r0, r1) (NULL planes
+ * mean "evaluate on demand"). */
+typedef struct {
+    const uint16_t *burst;
+    int n, h, w, ref, tile, ty, tx, wl;
+    const float *motion;
+    const orc_params *p;
+    /* per frame, rows [om_r0[f], om_r1[f]) of Omega [3][rows][wh] */
+    double **om;
+    int *om_r0, *om_r1;
+    /* per frame, rows [rh_r0[f], rh_r1[f]) of Rhat [rows][wh] (base grid) */
+    double **rh;
+    int *rh_r0, *rh_r1;
+    double **s_tile;
+} merge_ctx;
+
+static inline const uint16_t *frame_ptr(const merge_ctx *m, int f) { return m->burst + (size_t)f * m->h * m->w; }
+static inline const float *motion_ptr(const merge_ctx *m, int f) { return m->motion + (size_t)f * m->ty * m->tx * 2; }
+
+static void omega_get(const merge_ctx *m, int f, int u, int v, double om[3])
+{
+    int hh = m->h / 2, wh = m->w / 2;
+    u = clampi(u, 0, wh - 1);
+    v = clampi(v, 0, hh - 1);
+    if (m->om && m->om[f] && v >= m->om_r0[f] && v < m->om_r1[f]) {
+        size_t rows = (size_t)(m->om_r1[f] - m->om_r0[f]);
+        const double *pl = m->om[f] + (size_t)(v - m->om_r0[f]) * wh + u;
+        om[0] = pl[0]; om[1] = pl[rows * wh]; om[2] = pl[2 * rows * wh];
+        return;
+    }
+    omega_at(frame_ptr(m, f), m->h, m->w, u, v, m->p, m->wl, om);
+}
+
+static double rhat_get(const merge_ctx *m, int f, int u, int v)
+{
+    int hh = m->h / 2, wh = m->w / 2;
+    u = clampi(u, 0, wh - 1);
+    v = clampi(v, 0, hh - 1);
+    if (m->rh && m->rh[f] && v >= m->rh_r0[f] && v < m->rh_r1[f])
+        return m->rh[f][(size_t)(v - m->rh_r0[f]) * wh + u];
+    /* on demand: min over the 5x5 window of R */
+    rob_geom g = { m->h, m->w, m->tile, m->ty, m->tx, m->wl, m->p };
+    double best = INFINITY;
+    for (int j = -2; j <= 2; ++j)
+        for (int i = -2; i <= 2; ++i) {
+            int uu = u + i, vv = v + j;
+            if (uu < 0 || uu >= wh || vv < 0 || vv >= hh) continue;
+            double r = robustness_at(frame_ptr(m, m->ref), frame_ptr(m, f), motion_ptr(m, f), m->s_tile[f], &g, uu, vv);
+            if (r < best) best = r;
+        }
+    return best;
+}
+
+/* Output-pixel geometry.  Reading of the (unstated) resampling grid: pixel centres at
+ * integers on both grids, so output pixel X sits at raw x0 = (X + 1/2)/s - 1/2, written
+ * exactly as the rational P/Q with P = 2 den X + den - num and Q = 2 num. */
+static void merge_pixel(const merge_ctx *m, int snum, int sden, int X, int Y, double out[3], double den_out[3])
+{
+    const long long Q = 2LL * snum;
+    const long long Px = 2LL * sden * X + sden - snum;
+    const long long Py = 2LL * sden * Y + sden - snum;
+    const double x0 = (double)Px / (double)Q, y0 = (double)Py / (double)Q;
+    /* tile of the output pixel on the base frame (motion is constant per tile) */
+    int txi = (int)floor_div(Px, Q * m->tile);
+    int tyi = (int)floor_div(Py, Q * m->tile);
+    txi = clampi(txi, 0, m->tx - 1);
+    tyi = clampi(tyi, 0, m->ty - 1);
+    double num[3] = { 0, 0, 0 }, den[3] = { 0, 0, 0 };
+    for (int f = 0; f < m->n; ++f) {
+        double vx = 0.0, vy = 0.0;
+        if (f != m->ref) {
+            const float *mv = motion_ptr(m, f) + ((size_t)tyi * m->tx + txi) * 2;
+            vx = (double)mv[0];
+            vy = (double)mv[1];
+        }
+        /* 3x3 window centre: the raw pixel nearest to x0 + v (ties round up), computed
+         * exactly: floor((P + Q/2 + Q v) / Q) with Q v exact in FP64. */
+        long long kx = floor_div(Px + Q / 2 + (long long)floor((double)Q * vx), Q);
+        long long ky = floor_div(Py + Q / 2 + (long long)floor((double)Q * vy), Q);
+        double px = x0 + vx, py = y0 + vy;
+        /* Omega: bilinear on frame f's half-res grid (centre of (u,v) at raw 2u + 1/2) */
+        double hx = (px - 0.5) / 2.0, hy = (py - 0.5) / 2.0;
+        double fx0 = floor(hx), fy0 = floor(hy);
+        double ax = hx - fx0, ay = hy - fy0;
+        int ix = (int)fx0, iy = (int)fy0;
+        double o00[3], o10[3], o01[3], o11[3], om[3];
+        omega_get(m, f, ix, iy, o00);
+        omega_get(m, f, ix + 1, iy, o10);
+        omega_get(m, f, ix, iy + 1, o01);
+        omega_get(m, f, ix + 1, iy + 1, o11);
+        for (int k = 0; k < 3; ++k)
+            om[k] = (1.0 - ay) * ((1.0 - ax) * o00[k] + ax * o10[k]) + ay * ((1.0 - ax) * o01[k] + ax * o11[k]);
+        double det = om[0] * om[2] - om[1] * om[1];
+        double ixx = om[2] / det, ixy = -om[1] / det, iyy = om[0] / det;   /* Omega^-1 */
+        /* Rhat: bilinear on the base half-res grid at the base position; 1 for the base */
+        double rhat = 1.0;
+        if (f != m->ref) {
+            double gx = (x0 - 0.5) / 2.0, gy = (y0 - 0.5) / 2.0;
+            double gx0 = floor(gx), gy0 = floor(gy);
+            double bx = gx - gx0, by = gy - gy0;
+            int jx = (int)gx0, jy = (int)gy0;
+            double r00 = rhat_get(m, f, jx, jy), r10 = rhat_get(m, f, jx + 1, jy);
+            double r01 = rhat_get(m, f, jx, jy + 1), r11 = rhat_get(m, f, jx + 1, jy + 1);
+            rhat = (1.0 - by) * ((1.0 - bx) * r00 + bx * r10) + by * ((1.0 - bx) * r01 + bx * r11);
+        }
+        const uint16_t *fr = frame_ptr(m, f);
+        /* the nine samples of the 3x3 Bayer neighbourhood; samples outside the frame
+         * are left out (the paper does not say) */
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+                long long qx = kx + i, qy = ky + j;
+                if (qx < 0 || qx >= m->w || qy < 0 || qy >= m->h) continue;
+                double dx = (double)qx - px, dy = (double)qy - py;
+                double qf = ixx * dx * dx + 2.0 * ixy * dx * dy + iyy * dy * dy;
+                double wgt = exp(-0.5 * qf);                                   /* Eq. 2 */
+                int c = cfa_channel((int)qx, (int)qy);
+                double cval = (double)fr[(size_t)qy * m->w + qx];
+                num[c] += cval * wgt * rhat;                                   /* Eq. 1 */
+                den[c] += wgt * rhat;
+            }
+    }
+    for (int c = 0; c < 3; ++c) {
+        out[c] = num[c] / den[c];
+        if (den_out) den_out[c] = den[c];
+    }
+}
+
+static void free_ctx(merge_ctx *m)
+{
+    if (m->om) for (int f = 0; f < m->n; ++f) free(m->om[f]);
+    if (m->rh) for (int f = 0; f < m->n; ++f) free(m->rh[f]);
+    if (m->s_tile) for (int f = 0; f < m->n; ++f) free(m->s_tile[f]);
+    free(m->om); free(m->rh); free(m->s_tile);
+    free(m->om_r0); free(m->om_r1); free(m->rh_r0); free(m->rh_r1);
+}
+
+static int init_ctx(merge_ctx *m, const uint16_t *burst, int n, int h, int w, int ref, const float *motion,
+                    int tile, const orc_params *p, int wl)
+{
+    memset(m, 0, sizeof(*m));
+    if (!burst || !motion || !p || n < 1 || h < 2 || w < 2 || (h & 1) || (w & 1) || ref < 0 || ref >= n ||
+        tile < 2 || (tile & 1) || wl <= 0)
+        return -1;
+    m->burst = burst; m->n = n; m->h = h; m->w = w; m->ref = ref; m->tile = tile;
+    m->ty = (h + tile - 1) / tile; m->tx = (w + tile - 1) / tile; m->wl = wl;
+    m->motion = motion; m->p = p;
+    m->s_tile = (double **)calloc((size_t)n, sizeof(double *));
+    if (!m->s_tile) return -2;
+    for (int f = 0; f < n; ++f) {
+        m->s_tile[f] = (double *)malloc(sizeof(double) * (size_t)m->ty * m->tx);
+        if (!m->s_tile[f]) return -2;
+        orc_tile_strength(motion_ptr(m, f), m->ty, m->tx, p, NULL, m->s_tile[f]);
+    }
+    return 0;
+}
+
+/* Precompute Omega and Rhat on the half-res rows that output rows [y0, y1) can touch. */
+static int precompute_rows(merge_ctx *m, int snum, int sden, int y0, int y1)
+{
+    int n = m->n, hh = m->h / 2, wh = m->w / 2;
+    m->om = (double **)calloc((size_t)n, sizeof(double *));
+    m->rh = (double **)calloc((size_t)n, sizeof(double *));
+    m->om_r0 = (int *)calloc((size_t)n, sizeof(int)); m->om_r1 = (int *)calloc((size_t)n, sizeof(int));
+    m->rh_r0 = (int *)calloc((size_t)n, sizeof(int)); m->rh_r1 = (int *)calloc((size_t)n, sizeof(int));
+    if (!m->om || !m->rh || !m->om_r0 || !m->om_r1 || !m->rh_r0 || !m->rh_r1) return -2;
+    /* raw rows of the band's base positions */
+    double ylo = ((double)y0 + 0.5) * sden / snum - 0.5;
+    double yhi = ((double)y1 - 0.5) * sden / snum - 0.5;
+    for (int f = 0; f < n; ++f) {
+        double vmin = 0.0, vmax = 0.0;
+        if (f != m->ref) {
+            const float *mv = motion_ptr(m, f);
+            vmin = INFINITY; vmax = -INFINITY;
+            for (int t = 0; t < m->ty * m->tx; ++t) {
+                double vy = mv[2 * t + 1];
+                if (vy < vmin) vmin = vy;
+                if (vy > vmax) vmax = vy;
+            }
+        }
+        int r0 = (int)floor((ylo + vmin - 0.5) / 2.0) - 2;
+        int r1 = (int)ceil((yhi + vmax - 0.5) / 2.0) + 3;
+        r0 = clampi(r0, 0, hh); r1 = clampi(r1, 0, hh);
+        m->om_r0[f] = r0; m->om_r1[f] = r1;
+        if (r1 > r0) {
+            size_t rows = (size_t)(r1 - r0);
+            m->om[f] = (double *)malloc(sizeof(double) * 3 * rows * wh);
+            if (!m->om[f]) return -2;
+            const uint16_t *fr = frame_ptr(m, f);
+            double *pl = m->om[f];
+#pragma omp parallel for schedule(static)
+            for (int v = r0; v < r1; ++v)
+                for (int u = 0; u < wh; ++u) {
+                    double om[3];
+                    omega_at(fr, m->h, m->w, u, v, m->p, m->wl, om);
+                    for (int k = 0; k < 3; ++k) pl[k * rows * wh + (size_t)(v - r0) * wh + u] = om[k];
+                }
+        }
+        if (f == m->ref) continue;
+        /* Rhat rows (base grid) and the R rows they need (+-2) */
+        int q0 = clampi((int)floor((ylo - 0.5) / 2.0) - 2, 0, hh);
+        int q1 = clampi((int)ceil((yhi - 0.5) / 2.0) + 3, 0, hh);
+        if (q1 <= q0) continue;
+        int p0 = clampi(q0 - 2, 0, hh), p1 = clampi(q1 + 2, 0, hh);
+        double *Rb = (double *)malloc(sizeof(double) * (size_t)(p1 - p0) * wh);
+        m->rh[f] = (double *)malloc(sizeof(double) * (size_t)(q1 - q0) * wh);
+        if (!Rb || !m->rh[f]) { free(Rb); return -2; }
+        rob_geom g = { m->h, m->w, m->tile, m->ty, m->tx, m->wl, m->p };
+        const uint16_t *base = frame_ptr(m, m->ref), *alt = frame_ptr(m, f);
+        const float *mva = motion_ptr(m, f);
+        const double *st = m->s_tile[f];
+#pragma omp parallel for schedule(static)
+        for (int v = p0; v < p1; ++v)
+            for (int u = 0; u < wh; ++u) Rb[(size_t)(v - p0) * wh + u] = robustness_at(base, alt, mva, st, &g, u, v);
+        double *rh = m->rh[f];
+#pragma omp parallel for schedule(static)
+        for (int v = q0; v < q1; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double best = INFINITY;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int uu = u + i, vv = v + j;
+                        if (uu < 0 || uu >= wh || vv < 0 || vv >= hh) continue;
+                        double r = Rb[(size_t)(vv - p0) * wh + uu];
+                        if (r < best) best = r;
+                    }
+                rh[(size_t)(v - q0) * wh + u] = best;
+            }
+        free(Rb);
+        m->rh_r0[f] = q0; m->rh_r1[f] = q1;
+    }
+    return 0;
+}
+
+int orc_merge_rows(const uint16_t *burst, int n, int h, int w, int ref, const float *motion, int tile,
+                   const orc_params *p, int wl, int snum, int sden, int y0, int y1, double *out,
+                   double *den, int n_threads)
+{
+    if (snum < 1 || sden < 1 || !out) return -1;
+    int ho = (int)(((long long)h * snum) / sden), wo = (int)(((long long)w * snum) / sden);
+    if (y0 < 0 || y1 > ho || y1 < y0) return -1;
+    set_threads(n_threads);
+    merge_ctx m;
+    int rc = init_ctx(&m, burst, n, h, w, ref, motion, tile, p, wl);
+    if (rc == 0 && y1 > y0) rc = precompute_rows(&m, snum, sden, y0, y1);
+    if (rc != 0) { free_ctx(&m); return rc; }
+    size_t plane = (size_t)(y1 - y0) * wo;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int Y = y0; Y < y1; ++Y)
+        for (int X = 0; X < wo; ++X) {
+            double o[3], d[3];
+            merge_pixel(&m, snum, sden, X, Y, o, d);
+            size_t idx = (size_t)(Y - y0) * wo + X;
+            for (int c = 0; c < 3; ++c) {
+                out[c * plane + idx] = o[c];
+                if (den) den[c * plane + idx] = d[c];
+            }
+        }
+    free_ctx(&m);
+    return 0;
+}
+
+int orc_merge_pixels(const uint16_t *burst, int n, int h, int w, int ref, const float *motion, int tile,
+                     const orc_params *p, int wl, int snum, int sden, const int32_t *xy, int count,
+                     double *out, int n_threads)
+{
+    if (snum < 1 || sden < 1 || !xy || !out || count < 0) return -1;
+    int ho = (int)(((long long)h * snum) / sden), wo = (int)(((long long)w * snum) / sden);
+    for (int k = 0; k < count; ++k)
+        if (xy[2 * k] < 0 || xy[2 * k] >= wo || xy[2 * k + 1] < 0 || xy[2 * k + 1] >= ho) return -1;
+    set_threads(n_threads);
+    merge_ctx m;
+    int rc = init_ctx(&m, burst, n, h, w, ref, motion, tile, p, wl);
+    if (rc != 0) { free_ctx(&m); return rc; }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < count; ++k) merge_pixel(&m, snum, sden, xy[2 * k], xy[2 * k + 1], out + 3 * (size_t)k, NULL);
+    free_ctx(&m);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Alignment (Sec. 3.2): pyramid block matching, then Lucas-Kanade refinement            */
+/* ------------------------------------------------------------------------------------ */
+/* The paper follows Hasinoff et al.'s coarse-to-fine tile search without giving its
+ * settings.  Readings taken: level 0 is Lq; level l+1 is the integer floor mean of
+ * f x f blocks of level l with f = 2, 4, 4; tiles are tile/2 px at every level; a tile's
+ * start vector is its parent's vector (the parent tile holds this tile's centre) times
+ * f; the search covers offsets |dx|, |dy| <= radius[l]; the distance is the integer sum
+ * of squared differences over the tile (reads clamped); ties go to the smallest SSD,
+ * then the smallest |dx| + |dy|, then the smaller dy, then the smaller dx. */
+typedef struct { int h, w; int32_t *px; } level_img;
+
+static inline int32_t lvl_at(const level_img *L, int x, int y)
+{
+    x = clampi(x, 0, L->w - 1);
+    y = clampi(y, 0, L->h - 1);
+    return L->px[(size_t)y * L->w + x];
+}
+
+static const int kFactors[3] = { 2, 4, 4 };
+
+static int build_pyramid(const uint16_t *raw, int h, int w, int n_levels_max, level_img *lv)
+{
+    int hh = h / 2, wh = w / 2;
+    lv[0].h = hh; lv[0].w = wh;
+    lv[0].px = (int32_t *)malloc(sizeof(int32_t) * (size_t)hh * wh);
+    if (!lv[0].px) return -2;
+    orc_luma(raw, h, w, lv[0].px);
+    int nl = 1;
+    while (nl < n_levels_max && nl < 4) {
+        int f = kFactors[nl - 1];
+        int nh = lv[nl - 1].h / f, nw = lv[nl - 1].w / f;
+        if (nh < 16 || nw < 16) break;
+        lv[nl].h = nh; lv[nl].w = nw;
+        lv[nl].px = (int32_t *)malloc(sizeof(int32_t) * (size_t)nh * nw);
+        if (!lv[nl].px) return -2;
+        for (int y = 0; y < nh; ++y)
+            for (int x = 0; x < nw; ++x) {
+                int64_t s = 0;
+                for (int j = 0; j < f; ++j)
+                    for (int i = 0; i < f; ++i) s += lv[nl - 1].px[(size_t)(y * f + j) * lv[nl - 1].w + x * f + i];
+                lv[nl].px[(size_t)y * nw + x] = (int32_t)(s / (f * f));
+            }
+        ++nl;
+    }
+    return nl;
+}
+
+/* One tile's integer search at one level: returns the best offset in (*bx, *by). */
+static void tile_search(const level_img *Lr, const level_img *La, int t, int tx, int ty, int cx, int cy, int rad,
+                        int *bx, int *by)
+{
+    int64_t best = -1;
+    int bdx = 0, bdy = 0;
+    for (int dy = -rad; dy <= rad; ++dy)
+        for (int dx = -rad; dx <= rad; ++dx) {
+            int64_t ssd = 0;
+            for (int j = 0; j < t; ++j)
+                for (int i = 0; i < t; ++i) {
+                    int x = tx * t + i, y = ty * t + j;
+                    int64_t d = (int64_t)lvl_at(Lr, x, y) - lvl_at(La, x + cx + dx, y + cy + dy);
+                    ssd += d * d;
+                }
+            int better;
+            if (best < 0 || ssd < best) better = 1;
+            else if (ssd > best) better = 0;
+            else {
+                int m_new = abs(dx) + abs(dy), m_old = abs(bdx) + abs(bdy);
+                if (m_new != m_old) better = m_new < m_old;
+                else if (dy != bdy) better = dy < bdy;
+                else better = dx < bdx;
+            }
+            if (better) { best = ssd; bdx = dx; bdy = dy; }
+        }
+    *bx = cx + bdx;
+    *by = cy + bdy;
+}
+
+/* Lucas-Kanade refinement (three iterations in the paper) of one tile at level 0, on
+ * I = Lq / 4.  Readings taken: gradients of the base frame by central differences
+ * (clamped), H = sum g g^T over the tile, each iteration r(p) = I_alt(p + u + delta)
+ * - I_ref(p) with bilinear sampling (clamped) and delta <- delta - H^-1 sum g r, delta
+ * clamped to [-1, 1] per axis; the update is skipped when tr H == 0 or
+ * det H <= 1e-9 tr(H)^2.  H is accumulated exactly in integers (64 H) so that this
+ * guard is the same FP64 operation sequence in any implementation. */
+static int lk_tile(const level_img *Lr, const level_img *La, int t, int tx, int ty, int ux, int uy, int iters,
+                   double *ox, double *oy)
+{
+    int64_t hxx = 0, hxy = 0, hyy = 0;
+    for (int j = 0; j < t; ++j)
+        for (int i = 0; i < t; ++i) {
+            int x = clampi(tx * t + i, 0, Lr->w - 1), y = clampi(ty * t + j, 0, Lr->h - 1);
+            int64_t gx = (int64_t)lvl_at(Lr, x + 1, y) - lvl_at(Lr, x - 1, y);
+            int64_t gy = (int64_t)lvl_at(Lr, x, y + 1) - lvl_at(Lr, x, y - 1);
+            hxx += gx * gx; hxy += gx * gy; hyy += gy * gy;
+        }
+    /* g = (Lq difference) / 8 since I = Lq / 4 and central differences halve */
+    double Hxx = (double)hxx, Hxy = (double)hxy, Hyy = (double)hyy;
+    double tr = Hxx + Hyy;
+    double det = Hxx * Hyy - Hxy * Hxy;
+    double trsq = tr * tr;
+    double dx = 0.0, dy = 0.0;
+    int skipped = (tr == 0.0) || (det <= 1e-9 * trsq);
+    if (!skipped) {
+        for (int it = 0; it < iters; ++it) {
+            double bx = 0.0, by = 0.0;
+            for (int j = 0; j < t; ++j)
+                for (int i = 0; i < t; ++i) {
+                    int x = clampi(tx * t + i, 0, Lr->w - 1), y = clampi(ty * t + j, 0, Lr->h - 1);
+                    double gx = ((double)lvl_at(Lr, x + 1, y) - lvl_at(Lr, x - 1, y)) / 8.0;
+                    double gy = ((double)lvl_at(Lr, x, y + 1) - lvl_at(Lr, x, y - 1)) / 8.0;
+                    double sx = x + ux + dx, sy = y + uy + dy;
+                    double fx0 = floor(sx), fy0 = floor(sy);
+                    double ax = sx - fx0, ay = sy - fy0;
+                    int ix = (int)fx0, iy = (int)fy0;
+                    double i00 = lvl_at(La, ix, iy) / 4.0, i10 = lvl_at(La, ix + 1, iy) / 4.0;
+                    double i01 = lvl_at(La, ix, iy + 1) / 4.0, i11 = lvl_at(La, ix + 1, iy + 1) / 4.0;
+                    double ia = (1.0 - ay) * ((1.0 - ax) * i00 + ax * i10) + ay * ((1.0 - ax) * i01 + ax * i11);
+                    double r = ia - lvl_at(Lr, x, y) / 4.0;
+                    bx += gx * r;
+                    by += gy * r;
+                }
+            /* H in units of the gradient g = diff / 8: H_g = H_int / 64 */
+            double gxx = Hxx / 64.0, gxy = Hxy / 64.0, gyy = Hyy / 64.0;
+            double gdet = gxx * gyy - gxy * gxy;
+            double stepx = -(gyy * bx - gxy * by) / gdet;
+            double stepy = -(-gxy * bx + gxx * by) / gdet;
+            dx = clampd(dx + stepx, -1.0, 1.0);
+            dy = clampd(dy + stepy, -1.0, 1.0);
+        }
+    }
+    *ox = dx; *oy = dy;
+    return skipped;
+}
+
+int orc_align(const uint16_t *burst, int n, int h, int w, int ref, int tile, int n_levels_max, const int *radius,
+              int lk_iters, int32_t *motion_int, double *motion, int32_t *lk_flags, int n_threads)
+{
+    if (!burst || !radius || n < 1 || h < 4 || w < 4 || (h & 1) || (w & 1) || ref < 0 || ref >= n || tile < 2 ||
+        (tile & 1) || n_levels_max < 1 || lk_iters < 0)
+        return -1;
+    set_threads(n_threads);
+    int t = tile / 2;
+    int ty0 = (h + tile - 1) / tile, tx0 = (w + tile - 1) / tile;
+    level_img ref_lv[4];
+    memset(ref_lv, 0, sizeof(ref_lv));
+    int nl = build_pyramid(burst + (size_t)ref * h * w, h, w, n_levels_max, ref_lv);
+    if (nl < 0) return nl;
+    int rc = nl;
+    for (int f = 0; f < n; ++f) {
+        size_t off = (size_t)f * ty0 * tx0;
+        if (f == ref) {
+            for (size_t k = 0; k < (size_t)ty0 * tx0; ++k) {
+                if (motion_int) { motion_int[2 * (off + k)] = 0; motion_int[2 * (off + k) + 1] = 0; }
+                if (motion) { motion[2 * (off + k)] = 0.0; motion[2 * (off + k) + 1] = 0.0; }
+                if (lk_flags) lk_flags[off + k] = 0;
+            }
+            continue;
+        }
+        level_img alt_lv[4];
+        memset(alt_lv, 0, sizeof(alt_lv));
+        int nla = build_pyramid(burst + (size_t)f * h * w, h, w, n_levels_max, alt_lv);
+        if (nla != nl) { rc = -2; for (int l = 0; l < 4; ++l) free(alt_lv[l].px); break; }
+        int *vec = NULL;   /* vectors of the previous (coarser) level */
+        int pty = 0, ptx = 0;
+        for (int l = nl - 1; l >= 0; --l) {
+            int lty = (ref_lv[l].h + t - 1) / t, ltx = (ref_lv[l].w + t - 1) / t;
+            int *cur = (int *)malloc(sizeof(int) * 2 * (size_t)lty * ltx);
+            int fct = (l < nl - 1) ? kFactors[l] : 1;
+#pragma omp parallel for schedule(static)
+            for (int y = 0; y < lty; ++y)
+                for (int x = 0; x < ltx; ++x) {
+                    int cx = 0, cy = 0;
+                    if (vec) {
+                        int px = clampi((x * t + t / 2) / fct / t, 0, ptx - 1);
+                        int py = clampi((y * t + t / 2) / fct / t, 0, pty - 1);
+                        cx = vec[2 * ((size_t)py * ptx + px)] * fct;
+                        cy = vec[2 * ((size_t)py * ptx + px) + 1] * fct;
+                    }
+                    int bx, by;
+                    tile_search(&ref_lv[l], &alt_lv[l], t, x, y, cx, cy, radius[l], &bx, &by);
+                    cur[2 * ((size_t)y * ltx + x)] = bx;
+                    cur[2 * ((size_t)y * ltx + x) + 1] = by;
+                }
+            free(vec);
+            vec = cur; pty = lty; ptx = ltx;
+        }
+        /* vec holds level-0 vectors on the ty0 x tx0 grid */
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ty0; ++y)
+            for (int x = 0; x < tx0; ++x) {
+                size_t k = (size_t)y * tx0 + x;
+                int ux = vec[2 * k], uy = vec[2 * k + 1];
+                if (motion_int) { motion_int[2 * (off + k)] = ux; motion_int[2 * (off + k) + 1] = uy; }
+                double ddx = 0.0, ddy = 0.0;
+                int sk = lk_tile(&ref_lv[0], &alt_lv[0], t, x, y, ux, uy, lk_iters, &ddx, &ddy);
+                if (lk_flags) lk_flags[off + k] = sk;
+                if (motion) {
+                    motion[2 * (off + k)] = 2.0 * (ux + ddx);
+                    motion[2 * (off + k) + 1] = 2.0 * (uy + ddy);
+                }
+            }
+        free(vec);
+        for (int l = 0; l < 4; ++l) free(alt_lv[l].px);
+    }
+    for (int l = 0; l < 4; ++l) free(ref_lv[l].px);
+    return rc;
+}

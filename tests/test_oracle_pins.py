@@ -1,0 +1,465 @@
+"""Pins for the FP64 oracle: each check compares it with something other than itself
+(closed forms, hand-worked values, invariants the paper states, textbook special cases,
+NumPy/SciPy routines and brute force on tiny inputs).  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+from oracle import MergeParams
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+WL = 4095
+
+
+def smooth_texture(h, w, seed=0, sigma=3.0, mean=2000.0, std=700.0, pad=64):
+    rng = np.random.default_rng(seed)
+    big = ndimage.gaussian_filter(rng.normal(size=(h + 2 * pad, w + 2 * pad)), sigma)
+    return mean + std * big / big.std(), pad
+
+
+def shifted_burst(shifts, h=128, w=128, seed=0, sigma=3.0):
+    """Grey smooth texture seen with raw-px shifts (base -> frame displacement)."""
+    big, pad = smooth_texture(h, w, seed, sigma)
+    yy, xx = np.mgrid[0:h, 0:w].astype(float)
+    frames = [ndimage.map_coordinates(big, [yy + pad - ty, xx + pad - tx], order=3) for tx, ty in shifts]
+    return np.clip(np.round(np.stack(frames)), 0, WL).astype(np.uint16)
+
+
+# --------------------------------------------------------------------------------------
+# luminance, structure tensor (Sec. 5.1.2, Eq. 3)
+# --------------------------------------------------------------------------------------
+def test_luma_is_quad_sum():
+    rng = np.random.default_rng(1)
+    raw = rng.integers(0, WL + 1, size=(12, 18)).astype(np.uint16)
+    lq = oracle.luma(raw)
+    r = raw.astype(np.int64)
+    assert np.array_equal(lq, r[0::2, 0::2] + r[0::2, 1::2] + r[1::2, 0::2] + r[1::2, 1::2])
+
+
+def test_tensor_of_linear_ramp_closed_form():
+    # raw(x, y) = g x in every channel -> Lq(u) = 8 g u + 2 g; each sub-square's forward
+    # gradient = 2 * 8 g = 16 g, no y gradient: a = 4 (16 g)^2, b = c = 0 (interior)
+    g = 3
+    xs = np.arange(40)
+    raw = np.tile(g * xs, (20, 1)).astype(np.uint16)
+    a, b, c = oracle.structure_tensor(raw, 7, 4)
+    assert (a, b, c) == (4 * (16 * g) ** 2, 0, 0)
+    # diagonal ramp raw = g (x + y): gx = gy = 16 g, so a = b = c
+    yy, xx = np.mgrid[0:20, 0:20]
+    raw2 = (g * (xx + yy)).astype(np.uint16)
+    assert oracle.structure_tensor(raw2, 5, 5) == (4 * 256 * g * g,) * 3
+
+
+def test_tensor_of_step_edges():
+    raw = np.zeros((16, 16), np.uint16)
+    raw[:, 8:] = 1000          # vertical edge at raw x = 8 (half-res u = 4)
+    a, b, c = oracle.structure_tensor(raw, 4, 4)
+    assert a > 0 and b == 0 and c == 0
+    a, b, c = oracle.structure_tensor(raw.T.copy(), 4, 4)
+    assert a == 0 and b == 0 and c > 0
+    # flat -> zero tensor
+    assert oracle.structure_tensor(np.full((8, 8), 77, np.uint16), 2, 2) == (0, 0, 0)
+
+
+# --------------------------------------------------------------------------------------
+# kernel shape (Eq. 4 + supplement S.1)
+# --------------------------------------------------------------------------------------
+def _golden_params(js):
+    p = js["params"]
+    return MergeParams(k_detail=p["k_detail"], k_denoise=p["k_denoise"], d_th=p["d_th"], d_tr=p["d_tr"],
+                       k_stretch=p["k_stretch"], k_shrink=p["k_shrink"])
+
+
+def test_kernel_shape_hand_worked_cases():
+    js = json.load(open(os.path.join(GOLDEN, "kernel_shape_cases.json")))
+    params = _golden_params(js)
+    for case in js["cases"]:
+        got = oracle.kernel_from_tensor(*case["tensor"], params, js["params"]["white_level"])
+        for k, v in case["expect"].items():
+            assert got[k] == pytest.approx(v, rel=1e-12, abs=1e-12), (case["name"], k, got[k], v)
+
+
+def test_kernel_eigen_matches_numpy_eigh():
+    rng = np.random.default_rng(2)
+    params = MergeParams()
+    for _ in range(200):
+        gx = rng.integers(-3000, 3000, size=4)
+        gy = rng.integers(-3000, 3000, size=4)
+        a, b, c = int((gx * gx).sum()), int((gx * gy).sum()), int((gy * gy).sum())
+        got = oracle.kernel_from_tensor(a, b, c, params)
+        lam, vec = np.linalg.eigh(np.array([[a, b], [b, c]], float))
+        assert got["l1"] == pytest.approx(lam[1], rel=1e-9, abs=1e-6)
+        assert got["l2"] == pytest.approx(lam[0], rel=1e-9, abs=1e-3)
+        e1 = vec[:, 1]
+        om = np.array([[got["Oxx"], got["Oxy"]], [got["Oxy"], got["Oyy"]]])
+        # Omega has eigenvalue k_across along the dominant gradient e1, k_along along e2
+        assert om @ e1 == pytest.approx(got["k_across"] * e1, rel=1e-9, abs=1e-12)
+        e2 = np.array([-e1[1], e1[0]])
+        assert om @ e2 == pytest.approx(got["k_along"] * e2, rel=1e-9, abs=1e-12)
+        assert got["A"] == pytest.approx(1 + math.sqrt((lam[1] - lam[0]) / (lam[1] + lam[0])), rel=1e-9)
+
+
+def test_kernel_isotropic_when_no_stretch_and_isotropic_tensor():
+    p = MergeParams(k_stretch=1.0, k_shrink=1.0, d_th=0.0, d_tr=0.001)
+    got = oracle.kernel_from_tensor(900000, 0, 900000, p)     # lambda1 == lambda2 -> A = 1
+    assert got["A"] == 1.0
+    assert got["Oxx"] == pytest.approx(got["Oyy"], rel=1e-15) and got["Oxy"] == 0.0
+    assert got["Oxx"] == pytest.approx((0.29 * float(np.float32(0.29)) / 0.29) ** 2, rel=1e-6)
+
+
+def test_kernel_denoise_limits():
+    p = MergeParams()
+    flat = oracle.kernel_from_tensor(0, 0, 0, p)
+    kd = float(np.float32(0.29)) * 4.0
+    assert flat["D"] == 1.0 and flat["k_along"] == pytest.approx(kd * kd) and flat["k_across"] == pytest.approx(kd * kd)
+    sharp = oracle.kernel_from_tensor(10 ** 12, 0, 0, p)
+    kdet = float(np.float32(0.29))
+    assert sharp["D"] == 0.0
+    assert sharp["k_along"] == pytest.approx((kdet * 4 * 2) ** 2, rel=1e-12)
+    assert sharp["k_across"] == pytest.approx((kdet / (2 * 2)) ** 2, rel=1e-12)
+
+
+# --------------------------------------------------------------------------------------
+# motion prior (Eq. 7-8) and robustness (Eq. 5, 6, 9)
+# --------------------------------------------------------------------------------------
+def test_motion_prior_uniform_and_outlier():
+    p = MergeParams()
+    mv = np.zeros((6, 7, 2), np.float32)
+    mv[...] = (1.25, -0.5)
+    M, s = oracle.tile_strength(mv, p)
+    assert np.all(M == 0) and np.all(s == np.float32(2.0))
+    mv[3, 4] += (0.6, 0.8)          # span (0.6, 0.8) -> M = 1.0 > 0.8 in the 3x3 around it
+    M, s = oracle.tile_strength(mv, p)
+    near = np.zeros((6, 7), bool)
+    near[2:5, 3:6] = True
+    assert np.allclose(M[near], 1.0, atol=1e-6) and np.all(M[~near] == 0)
+    assert np.all(s[near] == 12.0) and np.all(s[~near] == 2.0)
+    mv[3, 4] = (1.25 + 0.3, -0.5 + 0.4)   # M = 0.5 < 0.8 -> s2 everywhere
+    _, s = oracle.tile_strength(mv, p)
+    assert np.all(s == 2.0)
+
+
+def test_robustness_identical_frames_is_one(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    ty, tx = oracle.n_tiles(256, 256, 16)
+    R, Rh = oracle.robustness(raw[0], raw[0], np.zeros((ty, tx, 2), np.float32), 16, p)
+    assert np.all(R == 1.0) and np.all(Rh == 1.0)
+
+
+def test_robustness_large_difference_rejects(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    alt = np.clip(raw[0].astype(np.int32) + 1500, 0, WL).astype(np.uint16)
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    ty, tx = oracle.n_tiles(256, 256, 16)
+    R, Rh = oracle.robustness(raw[0], alt, np.zeros((ty, tx, 2), np.float32), 16, p)
+    assert np.all(Rh == 0.0)
+
+
+def test_robustness_constant_patches_closed_form():
+    # base and alt are flat (sigma_ms = 0) with per-channel offsets; noise var = b only.
+    # sigma_c^2 = var_c (G: var/2), d_md,c^2 = 2 var_c / 9, d_c = d^3 / (d^2 + d_md^2),
+    # ratio = sum d_c^2 / sum sigma_c^2, R = clamp(s2 exp(-ratio) - t, 0, 1).
+    h = w = 32
+    base = np.zeros((h, w), np.uint16)
+    base[0::2, 0::2] = 1000     # R
+    base[0::2, 1::2] = 1200     # G1
+    base[1::2, 0::2] = 1200     # G2
+    base[1::2, 1::2] = 900      # B
+    off = {"R": 5, "G": 4, "B": -6}
+    alt = base.astype(np.int32).copy()
+    alt[0::2, 0::2] += off["R"]
+    alt[0::2, 1::2] += off["G"]
+    alt[1::2, 0::2] += off["G"]
+    alt[1::2, 1::2] += off["B"]
+    alt = alt.astype(np.uint16)
+    B = 16.0
+    p = MergeParams(noise_a=0.0, noise_b=B, t=0.125, s2=2.0, s1=12.0)
+    ty, tx = oracle.n_tiles(h, w, 16)
+    R, Rh = oracle.robustness(base, alt, np.zeros((ty, tx, 2), np.float32), 16, p)
+    var = {"R": B, "G": B / 2, "B": B}
+    dd = 0.0
+    ss = 0.0
+    for ch in "RGB":
+        dms = -off[ch]
+        dmd2 = 2 * var[ch] / 9
+        d = dms ** 3 / (dms ** 2 + dmd2)
+        dd += d * d
+        ss += var[ch]
+    expect = min(1.0, max(0.0, 2.0 * math.exp(-dd / ss) - 0.125))
+    assert 0.0 < expect < 1.0
+    assert np.allclose(R, expect, rtol=1e-12, atol=0)
+    assert np.allclose(Rh, expect, rtol=1e-12, atol=0)
+
+
+def test_robustness_min5_is_sliding_minimum(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    ty, tx = oracle.n_tiles(256, 256, 16)
+    mv = np.zeros((ty, tx, 2), np.float32)
+    mv[..., 0] = 0.7
+    mv[3:6, 3:6] = (5.0, -3.0)   # misaligned patch -> low R there
+    R, Rh = oracle.robustness(raw[0], raw[1], mv, 16, p)
+    assert R.min() < 0.5 < R.max()
+    ref = ndimage.minimum_filter(R, size=5, mode="constant", cval=np.inf)
+    assert np.array_equal(Rh, ref)
+
+
+# --------------------------------------------------------------------------------------
+# merge (Eq. 1-2)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("scale", [(1, 1), (3, 2), (2, 1)])
+def test_merge_constant_scene_is_constant(scale):
+    n, h, w = 3, 24, 20
+    burst = np.full((n, h, w), 1234, np.uint16)
+    ty, tx = oracle.n_tiles(h, w, 16)
+    rng = np.random.default_rng(3)
+    mv = rng.uniform(-2.5, 2.5, size=(n, ty, tx, 2)).astype(np.float32)
+    out = oracle.merge(burst, mv, MergeParams(), scale=scale)
+    assert out.shape == (3,) + oracle.out_size(h, w, scale)
+    assert np.allclose(out, 1234.0, rtol=1e-12, atol=0)
+
+
+def test_merge_identical_frames_equals_single_frame(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    ty, tx = oracle.n_tiles(256, 256, 16)
+    one = oracle.merge(raw[:1], np.zeros((1, ty, tx, 2), np.float32), p)
+    four = oracle.merge(np.repeat(raw[:1], 4, axis=0), np.zeros((4, ty, tx, 2), np.float32), p)
+    assert np.allclose(four, one, rtol=1e-12, atol=1e-9)
+
+
+def test_merge_even_integer_shift_equals_single_frame():
+    # frame n is the base moved by an even number of raw px (Bayer phase kept) and the
+    # motion field says exactly that: every frame then contributes identical samples at
+    # identical offsets, robustness is 1, and the merge equals the base-only merge away
+    # from the border.  A wrong sign or axis of v breaks this.
+    h, w = 96, 112
+    big = np.random.default_rng(4).integers(200, 3800, size=(h + 40, w + 40)).astype(np.uint16)
+    shifts = [(0, 0), (4, -2), (-6, 2), (2, 6)]
+    frames = [big[20 - sy:20 - sy + h, 20 - sx:20 - sx + w] for sx, sy in shifts]
+    burst = np.stack(frames)
+    ty, tx = oracle.n_tiles(h, w, 16)
+    mv = np.zeros((4, ty, tx, 2), np.float32)
+    for k, (sx, sy) in enumerate(shifts):
+        mv[k] = (sx, sy)
+    p = MergeParams(noise_a=1.0, noise_b=4.0)
+    for scale in [(1, 1), (2, 1)]:
+        all4 = oracle.merge(burst, mv, p, scale=scale)
+        one = oracle.merge(burst[:1], mv[:1], p, scale=scale)
+        s = scale[0] / scale[1]
+        m = int(16 * s)
+        assert np.allclose(all4[:, m:-m, m:-m], one[:, m:-m, m:-m], rtol=1e-10, atol=1e-9)
+
+
+def test_merge_isotropic_is_normalized_gaussian_convolution():
+    # With k_stretch = k_shrink = 1 and D = 1 everywhere (huge D_th), Omega = (k_d k_dn)^2 I.
+    # One frame at 1x, zero motion: each channel is the normalized convolution of its
+    # Bayer samples with the 3x3 Gaussian exp(-|d|^2 / 2k) (Eq. 1-2), computed here with
+    # scipy.ndimage.
+    rng = np.random.default_rng(5)
+    raw = rng.integers(0, WL + 1, size=(1, 20, 24)).astype(np.uint16)
+    p = MergeParams(k_stretch=1.0, k_shrink=1.0, d_th=1000.0, d_tr=1.0, k_detail=0.5, k_denoise=1.5)
+    k = float(np.float32(0.5)) * float(np.float32(1.5))
+    k = k * k
+    out = oracle.merge(raw, np.zeros((1, 2, 2, 2), np.float32), p)
+    yy, xx = np.mgrid[-1:2, -1:2]
+    K = np.exp(-(xx ** 2 + yy ** 2) / (2 * k))
+    r = raw[0].astype(float)
+    py, px = np.mgrid[0:20, 0:24]
+    ch = (px & 1) + (py & 1)
+    for c in range(3):
+        mask = (ch == c).astype(float)
+        num = ndimage.convolve(r * mask, K, mode="constant", cval=0.0)
+        den = ndimage.convolve(mask, K, mode="constant", cval=0.0)
+        assert np.allclose(out[c], num / den, rtol=1e-12, atol=1e-9)
+
+
+def test_merge_wide_kernel_is_window_average_at_2x():
+    # Omega = (k_d k_dn)^2 I with a huge variance: every weight -> 1, so each channel is
+    # the plain mean of its samples in the 3x3 window centred on round(x0), with
+    # x0 = (X + 1/2)/2 - 1/2 at 2x.
+    rng = np.random.default_rng(6)
+    h, w = 12, 14
+    raw = rng.integers(0, WL + 1, size=(1, h, w)).astype(np.uint16)
+    p = MergeParams(k_stretch=1.0, k_shrink=1.0, d_th=1000.0, d_tr=1.0, k_detail=64.0, k_denoise=64.0)
+    out = oracle.merge(raw, np.zeros((1, 1, 1, 2), np.float32), p, scale=(2, 1))
+    r = raw[0].astype(float)
+    for Y in range(2 * h):
+        for X in range(2 * w):
+            kx = math.floor((X + 0.5) / 2 - 0.5 + 0.5)
+            ky = math.floor((Y + 0.5) / 2 - 0.5 + 0.5)
+            sums = np.zeros(3)
+            cnt = np.zeros(3)
+            for j in (-1, 0, 1):
+                for i in (-1, 0, 1):
+                    qx, qy = kx + i, ky + j
+                    if 0 <= qx < w and 0 <= qy < h:
+                        c = (qx & 1) + (qy & 1)
+                        sums[c] += r[qy, qx]
+                        cnt[c] += 1
+            assert np.allclose(out[:, Y, X], sums / cnt, rtol=1e-6)
+
+
+def test_merge_output_is_convex_combination(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    _, mf, _, _ = oracle.align(raw)
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    out, den = oracle.merge(raw, mf.astype(np.float32), p, with_den=True)
+    assert np.all(den > 0)
+    assert out.min() >= raw.min() - 1e-9 and out.max() <= raw.max() + 1e-9
+
+
+def test_merge_pixels_matches_rows(tiny_burst):
+    raw = tiny_burst["raw"].numpy()
+    _, mf, _, _ = oracle.align(raw)
+    mv = mf.astype(np.float32)
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    for scale in [(1, 1), (3, 2)]:
+        full = oracle.merge(raw, mv, p, scale=scale)
+        rng = np.random.default_rng(7)
+        ho, wo = full.shape[1:]
+        xy = np.stack([rng.integers(0, wo, 50), rng.integers(0, ho, 50)], axis=1)
+        xy[:4] = [(0, 0), (wo - 1, ho - 1), (0, ho - 1), (wo - 1, 0)]
+        pix = oracle.merge_pixels(raw, mv, p, xy, scale=scale)
+        assert np.array_equal(pix, full[:, xy[:, 1], xy[:, 0]].T)
+        band = oracle.merge(raw, mv, p, scale=scale, rows=(37, 61))
+        assert np.array_equal(band, full[:, 37:61])
+
+
+def test_merge_beats_single_frame_demosaic():
+    import burstgen
+    import torch
+    b = burstgen.make_burst(dict(n=8, h=128, w=128, gain=0.5, read=2.0, motion="global", scale=(1, 1)),
+                            seed=11, with_gt=True)
+    raw = b["raw"].numpy()
+    gt = b["gt"].numpy().astype(float)
+    _, mf, _, _ = oracle.align(raw)
+    p = MergeParams(noise_a=0.5, noise_b=4.0)
+    merged = oracle.merge(raw, mf.astype(np.float32), p)
+    # bilinear demosaic of the base frame
+    r = raw[0].astype(float)
+    py, px = np.mgrid[0:128, 0:128]
+    ch = (px & 1) + (py & 1)
+    K = np.array([[0.25, 0.5, 0.25], [0.5, 1.0, 0.5], [0.25, 0.5, 0.25]])
+    dem = np.stack([ndimage.convolve(r * (ch == c), K, mode="mirror") / ndimage.convolve((ch == c) * 1.0, K, mode="mirror")
+                    for c in range(3)])
+    sl = (slice(None), slice(8, -8), slice(8, -8))
+    mse_merge = np.mean((merged[sl] - gt[sl]) ** 2)
+    mse_dem = np.mean((dem[sl] - gt[sl]) ** 2)
+    assert mse_merge < mse_dem
+    del torch
+
+
+# --------------------------------------------------------------------------------------
+# alignment (Sec. 3.2)
+# --------------------------------------------------------------------------------------
+def test_align_even_integer_shift_is_exact():
+    shifts = [(0, 0), (2, -4), (-6, 2), (4, 4)]
+    h = w = 128
+    big, pad = smooth_texture(h, w, seed=8)
+    big = np.clip(np.round(big), 0, WL)
+    frames = [big[pad - sy:pad - sy + h, pad - sx:pad - sx + w] for sx, sy in shifts]
+    burst = np.stack(frames).astype(np.uint16)
+    mi, mf, fl, nl = oracle.align(burst)
+    assert nl >= 2
+    for k, (sx, sy) in enumerate(shifts):
+        # interior tiles (away from the clamped border by more than the shift)
+        inner_i = mi[k, 1:-1, 1:-1]
+        inner_f = mf[k, 1:-1, 1:-1]
+        assert np.all(inner_i[..., 0] == sx // 2) and np.all(inner_i[..., 1] == sy // 2)
+        assert np.all(inner_f[..., 0] == sx) and np.all(inner_f[..., 1] == sy)
+
+
+def _brute_search(Lr, La, t, tx, ty, cx, cy, rad):
+    H, W = Lr.shape
+    xs = np.clip(np.arange(tx * t, tx * t + t), 0, W - 1)
+    ys = np.clip(np.arange(ty * t, ty * t + t), 0, H - 1)
+    ref = Lr[np.ix_(ys, xs)]
+    cands = []
+    for dy in range(-rad, rad + 1):
+        for dx in range(-rad, rad + 1):
+            xa = np.clip(np.arange(tx * t, tx * t + t) + cx + dx, 0, W - 1)
+            ya = np.clip(np.arange(ty * t, ty * t + t) + cy + dy, 0, H - 1)
+            ssd = int(((ref - La[np.ix_(ya, xa)]) ** 2).sum())
+            cands.append((ssd, abs(dx) + abs(dy), dy, dx))
+    best = min(cands)
+    return cx + best[3], cy + best[2]
+
+
+def test_align_single_level_equals_exhaustive_search():
+    rng = np.random.default_rng(9)
+    burst = rng.integers(0, WL + 1, size=(3, 32, 48)).astype(np.uint16)
+    burst[1] = np.roll(burst[0], (2, -4), axis=(0, 1))
+    mi, _, _, nl = oracle.align(burst, n_levels=1, radius=(12,), lk_iters=0)
+    assert nl == 1
+    L = [oracle.luma(f).astype(np.int64) for f in burst]
+    t = 8
+    for k in range(3):
+        for ty in range(mi.shape[1]):
+            for tx in range(mi.shape[2]):
+                if k == 0:
+                    assert tuple(mi[k, ty, tx]) == (0, 0)
+                    continue
+                assert tuple(mi[k, ty, tx]) == _brute_search(L[0], L[k], t, tx, ty, 0, 0, 12)
+
+
+def test_align_pyramid_matches_restatement():
+    # coarse-to-fine restated with NumPy: level sizes, floor-mean decimation, parent
+    # lookup and search; integer vectors must agree exactly
+    rng = np.random.default_rng(10)
+    big, pad = smooth_texture(160, 200, seed=10, sigma=2.0)
+    frames = [big[pad:pad + 160, pad:pad + 200]]
+    for sx, sy in [(3, -2), (-5, 1)]:
+        frames.append(big[pad - sy:pad - sy + 160, pad - sx:pad - sx + 200])
+    burst = np.clip(np.round(np.stack(frames)) + rng.integers(-20, 20, size=(3, 160, 200)), 0, WL).astype(np.uint16)
+    mi, _, _, nl = oracle.align(burst, lk_iters=0)
+    t = 8
+    facs = [2, 4, 4]
+    radius = [1, 4, 4, 4]
+
+    def pyramid(f):
+        lv = [oracle.luma(f).astype(np.int64)]
+        for l in range(3):
+            fct = facs[l]
+            H, W = lv[-1].shape[0] // fct, lv[-1].shape[1] // fct
+            if H < 16 or W < 16:
+                break
+            lv.append(lv[-1][:H * fct, :W * fct].reshape(H, fct, W, fct).sum(axis=(1, 3)) // (fct * fct))
+        return lv
+
+    pr = pyramid(burst[0])
+    assert len(pr) == nl
+    for k in (1, 2):
+        pa = pyramid(burst[k])
+        vec = None
+        for l in range(nl - 1, -1, -1):
+            H, W = pr[l].shape
+            lty, ltx = -(-H // t), -(-W // t)
+            cur = np.zeros((lty, ltx, 2), np.int64)
+            for ty in range(lty):
+                for tx in range(ltx):
+                    cx = cy = 0
+                    if vec is not None:
+                        f = facs[l]
+                        px = min((tx * t + t // 2) // f // t, vec.shape[1] - 1)
+                        py = min((ty * t + t // 2) // f // t, vec.shape[0] - 1)
+                        cx, cy = vec[py, px] * f
+                    cur[ty, tx] = _brute_search(pr[l], pa[l], t, tx, ty, int(cx), int(cy), radius[l])
+            vec = cur
+        assert np.array_equal(mi[k], vec)
+
+
+def test_lk_recovers_subpixel_shift():
+    shifts = [(0.0, 0.0), (1.3, -0.7), (-2.2, 0.45), (0.5, 1.9)]
+    burst = shifted_burst(shifts, seed=12)
+    _, mf, fl, _ = oracle.align(burst)
+    for k, (sx, sy) in enumerate(shifts):
+        err = np.abs(mf[k, 1:-1, 1:-1] - np.array([sx, sy]))
+        assert np.median(err) < 0.05 and err.max() < 0.25
+        assert fl[k].sum() == 0
