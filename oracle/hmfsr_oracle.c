@@ -249,9 +249,12 @@ static int64_t box_sum(const uint16_t *raw, int h, int w, int u, int v, int c, i
 }
 
 /* Guide-channel 3x3 mean of frame `raw` at (u,v), in DN of the guide image (green =
- * average of the two greens). */
+ * average of the two greens).  The local-mean image is defined on the half-res grid;
+ * a read outside it takes the nearest pixel of that image (clamped read). */
 static double box_mean(const uint16_t *raw, int h, int w, int u, int v, int c)
 {
+    u = clampi(u, 0, w / 2 - 1);
+    v = clampi(v, 0, h / 2 - 1);
     double s = (double)box_sum(raw, h, w, u, v, c, 0);
     return (c == 1) ? s / 18.0 : s / 9.0;
 }
