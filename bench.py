@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Throughput of the handheld multi-frame super-resolution path (align + merge).
+
+Metric: merged raw MP/s = frames x raw megapixels of the burst / seconds per step, on the
+12-MP workload (8 RGGB frames of 4032x3024, 1x RGB output), seeded synthetic input.
+One step = hmfsr_align + hmfsr_merge_prepare + hmfsr_merge_accumulate on one burst.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {hmfsr,reference}]
+
+With N > 1 (torchrun, one process per GPU) every rank merges its own burst (replicas:
+the method has no exchange step); rank 0 prints one JSON line.  `--impl reference`
+times the FP64 CPU oracle on the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "merged raw MP/s (frames x MP / s) at 12MP x 8, align + merge"
+UNIT = "MP/s"
+WORKLOAD = "12mp"
+# Per output pixel and frame, the arithmetic the method defines for the accumulation
+# (Eq. 1-2 and the bilinear Omega / Rhat sampling); see the design notes for the count.
+ACC_FP32_OPS_PER_UNIT = 120
+ACC_MUFU_PER_UNIT = 10
+N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+FALLBACK_HBM_GBS = 6800.0
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except Exception:
+            return None
+    return None
+
+
+def kernel_traffic(name: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        js = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_1905_03277_gb300", "csrc", js["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != js["source_sha256_16"]:
+            return None
+        return js["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# -----------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# -----------------------------------------------------------------------------------------
+def oracle_align_time(raw_np, cores):
+    """Oracle alignment of the whole burst: (float32 motion, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    _, mf, _, _ = oracle.align(raw_np, n_threads=cores)
+    return mf.astype("float32"), time.perf_counter() - t0
+
+
+def oracle_merge_rows_time(raw_np, motion, params, scale, rows, cores):
+    """Oracle merge of `rows` output rows in the middle of the frame: seconds."""
+    import oracle
+    n, h, w = raw_np.shape
+    ho = (h * scale[0]) // scale[1]
+    y0 = max(0, (ho - rows) // 2)
+    t0 = time.perf_counter()
+    oracle.merge(raw_np, motion, params, scale=scale, rows=(y0, y0 + rows), n_threads=cores)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import burstgen
+    import oracle
+    import torch
+    # the input is rendered on the GPU when there is one (input generation only)
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
+    b = burstgen.make_burst(WORKLOAD, device=gen_dev)
+    raw_np = b["raw"].cpu().numpy()
+    n, h, w = raw_np.shape
+    scale = b["scale"]
+    ho = (h * scale[0]) // scale[1]
+    p = oracle.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2)
+    cores = host_cores()
+    mp = n * h * w / 1e6
+    # The oracle's alignment of the whole burst is timed once; one step is the oracle
+    # merge of a band of output rows plus the same fraction of the alignment time, with
+    # the band sized so that all steps together take about two minutes.
+    motion, t_align = oracle_align_time(raw_np, cores)
+    t16 = oracle_merge_rows_time(raw_np, motion, p, scale, 16, cores)
+    budget = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    rows = int(max(16, min(ho, 16 * budget / max(t16, 1e-3))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = oracle_merge_rows_time(raw_np, motion, p, scale, rows, cores) + t_align * rows / ho
+        if i >= args.warmup:
+            times.append(dt)
+    value = (mp * rows / ho) / statistics.mean(times)
+    sample = (f"per step: oracle merge of {rows} of {ho} output rows (all {n} frames) plus {rows}/{ho} of the "
+              f"oracle's whole-burst alignment time ({t_align:.2f} s); value = {rows}/{ho} of the burst's "
+              f"frames x MP / step time")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "12mp: 8 x 4032x3024 RGGB uint16, 1x RGB output, align + merge",
+                       "frames": n, "height": h, "width": w, "scale": "1/1"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -----------------------------------------------------------------------------------------
+# GPU arm
+# -----------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import burstgen
+    import paper_1905_03277_gb300 as hm
+
+    rank, world, local = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hm.build()
+
+    b = burstgen.make_burst(WORKLOAD, seed=burstgen.SEED_BASE + 1 + 1000 * rank, device=dev)
+    raw = b["raw"]
+    n, h, w = raw.shape
+    scale = b["scale"]
+    p = hm.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2)
+    ap = hm.AlignParams(tile=p.tile)
+    ho, wo = hm.out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    acc_ms, prep_ms, align_ms = [], [], []
+
+    def step(record=False):
+        if record:
+            ev[0].record(stream)
+        motion = hm.align(raw, 0, ap)
+        if record:
+            ev[1].record(stream)
+        ws = hm.merge_prepare(raw, motion, p)
+        if record:
+            ev[2].record(stream)
+        hm.merge_accumulate(raw, motion, ws, p, scale, out=rgb)
+        if record:
+            ev[3].record(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, inputs resident; the 195 MB burst is larger than the L2
+    barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_step = elapsed / args.steps
+    mp = n * h * w / 1e6
+    value = world * mp / (ms_step / 1e3)
+
+    # per-phase durations on the launching stream (separate pass, same work)
+    for _ in range(min(args.steps, 10)):
+        step(record=True)
+        torch.cuda.synchronize()
+        align_ms.append(ev[0].elapsed_time(ev[1]))
+        prep_ms.append(ev[1].elapsed_time(ev[2]))
+        acc_ms.append(ev[2].elapsed_time(ev[3]))
+
+    # end to end through the public API with host buffers: pinned H2D of the burst,
+    # align + merge, D2H of the RGB result, every step
+    host_burst = raw.cpu().pin_memory()
+    host_out = torch.empty((3, ho, wo), dtype=torch.float32, pin_memory=True)
+    for _ in range(2):
+        hm.align_merge(host_burst, p, scale, out=host_out)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        hm.align_merge(host_burst, p, scale, out=host_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * mp / (e2e_ms / 1e3)
+
+    if rank == 0:
+        units = ho * wo * n
+        acc_s = statistics.median(acc_ms) / 1e3
+        achieved = ACC_FP32_OPS_PER_UNIT * units / acc_s / 1e12
+        peak = N_SM * FP32_LANES * MAX_SM_MHZ * 1e6 / 1e12
+        clocks = clk.summary()
+        roof = {"bound": "alu", "kernel": "k_merge (hmfsr_merge_accumulate)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": kernel_traffic("k_merge_12mp"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock (FP32 lane-ops/s)",
+                "ops_per_unit": ACC_FP32_OPS_PER_UNIT, "units_per_launch": units,
+                "mufu": {"achieved": ACC_MUFU_PER_UNIT * units / acc_s / 1e12,
+                         "peak": N_SM * 16 * MAX_SM_MHZ * 1e6 / 1e12}}
+        peaks = measured_peaks()
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            op = oracle.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2)
+            raw_np = raw.cpu().numpy()
+            cores = host_cores()
+            rows = 512
+            motion_o, t_align = oracle_align_time(raw_np, cores)
+            t_rows = oracle_merge_rows_time(raw_np, motion_o, op, scale, rows, cores)
+            est = t_align + t_rows * ho / rows
+            cpu = {"value": mp / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"oracle alignment of the whole burst ({t_align:.1f} s) + oracle merge of {rows} of "
+                             f"{ho} output rows ({t_rows:.1f} s), merge time scaled by {ho}/{rows} to a full step"}
+        per_call = hm.launches_per_call(n, h, w, ap.n_levels)
+        launches = args.steps * sum(per_call.values())
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "12mp: 8 x 4032x3024 RGGB uint16 (12-bit), 1x RGB float32 output, "
+                                       "align + merge", "frames": n, "height": h, "width": w, "scale": "1/1",
+                           "tile": p.tile, "l2": "no flush: the 195 MB burst read each step is larger than L2",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_burst.numel() * 2),
+                        "d2h_bytes_per_step": int(host_out.numel() * 4), "ms_per_step": e2e_ms},
+                "gpu_launches": launches, "launches_per_step": per_call, "clocks": clocks,
+                "breakdown_ms": {"align": statistics.median(align_ms), "merge_prepare": statistics.median(prep_ms),
+                                 "merge_accumulate": statistics.median(acc_ms)},
+                "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("hmfsr", "reference"), default="hmfsr")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

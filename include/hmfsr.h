@@ -1,0 +1,131 @@
+/*
+ * hmfsr — handheld multi-frame super-resolution (Wronski et al., "Handheld Multi-Frame
+ * Super-Resolution", ACM TOG 38(4), 2019) on one GPU (sm_103a).
+ *
+ * C ABI.  Every call takes plain pointers and sizes.  Device pointers are CUDA device
+ * memory owned by the caller; the library never allocates device memory on these calls:
+ * scratch space is the caller's `ws` buffer, whose size is queried first with
+ * hmfsr_workspace_size().  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Calls are asynchronous on `stream`: arguments are validated on the
+ * host before any launch (errors return without touching the GPU); a failed launch
+ * returns HMFSR_ERR_CUDA.
+ *
+ * Image conventions (all calls):
+ *   raw frames  uint16, RGGB Bayer: pixel (x, y) is R when x, y are both even, B when both
+ *               odd, G otherwise.  Frame f, row y, column x is at
+ *               burst[(f * height + y) * pitch_elems + x].  Values 0..white_level.
+ *   half-res    pixel (u, v) covers raw (2u..2u+1, 2v..2v+1); its centre is raw
+ *               (2u + 1/2, 2v + 1/2).
+ *   tiles       square, `tile` raw px (even); tile (tx, ty) covers raw
+ *               [tile*tx, tile*tx + tile) x [tile*ty, tile*ty + tile);
+ *               TX = ceil(width / tile), TY = ceil(height / tile).
+ *   motion      float32 [n_frames][TY][TX][2] = (vx, vy): the base -> frame displacement
+ *               of each tile in raw px (a scene point at base position p is seen at
+ *               p + v in that frame).  The base frame's entry is ignored (taken as 0).
+ *   output      float32 planar [3][Ho][Wo] (R, G, B) in DN, Ho = floor(height*num/den),
+ *               Wo = floor(width*num/den); output pixel X sits at raw (X + 1/2)*den/num - 1/2.
+ */
+#ifndef HMFSR_H
+#define HMFSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HMFSR_OK = 0,
+    HMFSR_ERR_INVALID_ARG = -1,  /* a pointer, size, stride or parameter is out of range */
+    HMFSR_ERR_UNSUPPORTED = -2,  /* valid but not implemented (e.g. a non-RGGB CFA)      */
+    HMFSR_ERR_WORKSPACE = -3,    /* ws is NULL, misaligned or smaller than required       */
+    HMFSR_ERR_CUDA = -4,         /* a CUDA launch or runtime call failed                   */
+    HMFSR_ERR_TIMEOUT = -5       /* a bounded device-side wait gave up                     */
+} hmfsr_status;
+
+/* One burst in device memory (Sec. 3.1: a burst of raw CFA frames and a base frame). */
+typedef struct {
+    int n_frames;      /* >= 1                                                   */
+    int height, width; /* raw frame size, both even, >= 4                          */
+    int pitch_elems;   /* row stride in elements, even, >= width                   */
+    int ref;           /* index of the base frame, 0 <= ref < n_frames             */
+    int cfa;           /* 0 = RGGB (the only layout supported)                     */
+    int white_level;   /* e.g. 4095 for 12-bit data                                */
+    int black_level;   /* must be 0 (the synthetic data has none)                  */
+} hmfsr_burst_desc;
+
+/* Tile alignment (Sec. 3.2: coarse-to-fine pyramid block matching, then Lucas-Kanade). */
+typedef struct {
+    int tile;          /* raw px: 8, 16, 32 or 64; tiles are tile/2 px at every level */
+    int n_levels;      /* maximum pyramid levels, 1..4 (factors 2, 4, 4 between   */
+                       /* levels; a level is added while both sides stay >= 16 px) */
+    int radius[4];     /* search radius per level (index 0 = finest), 0..7         */
+    int lk_iters;      /* Lucas-Kanade iterations (the paper uses 3), 0..16        */
+} hmfsr_align_params;
+
+/* Merge tuning (Sec. 5; supplement S.1 heuristics and S.2 values). */
+typedef struct {
+    float k_detail, k_denoise, d_th, d_tr, k_stretch, k_shrink; /* kernel shape (S.1)    */
+    float t, s1, s2, m_th;          /* robustness threshold, scales, motion threshold   */
+    float noise_a, noise_b;         /* noise variance = noise_a * x + noise_b (DN^2)    */
+    int tile;                       /* raw px of the motion field's tiles: 8, 16, 32, 64 */
+} hmfsr_merge_params;
+
+enum { HMFSR_OP_ALIGN = 0, HMFSR_OP_MERGE = 1, HMFSR_OP_MERGE_STAGES = 2 };
+
+/* Bytes of scratch the op needs for this burst (0 on invalid arguments).  For
+ * HMFSR_OP_ALIGN, `tile` is the alignment tile; scale_num/scale_den are ignored.  For the
+ * merge ops, `tile` is the motion field's tile.  The workspace must be 256-byte aligned. */
+size_t hmfsr_workspace_size(int op, const hmfsr_burst_desc *desc, int tile, int scale_num, int scale_den);
+
+/* align(burst, ref) -> motion field (Sec. 3.2).
+ *   motion_dev      float32 [n_frames][TY][TX][2], written (raw px; base frame = 0).
+ *   motion_int_dev  optional int32 [n_frames][TY][TX][2]: the integer block-matching
+ *                   vectors in half-res px (before Lucas-Kanade); NULL to skip. */
+hmfsr_status hmfsr_align(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                         const hmfsr_align_params *params, float *motion_dev, int32_t *motion_int_dev,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* merge(burst, motion, params, scale) -> RGB (Sec. 5, Eq. 1-9 and supplement S.1): per
+ * frame, kernel covariances from the half-res structure tensor (Eq. 3-4), robustness from
+ * local statistics, the noise model and the motion prior (Eq. 5-9), then per-channel
+ * kernel regression of every Bayer sample over the 3x3 neighbourhood (Eq. 1-2) and a
+ * final normalisation.  scale_num/scale_den in {1/1, 3/2, 2/1} (any 1 <= num/den <= 4
+ * with num, den <= 8 is accepted).
+ *   rgb_dev  float32 [3][Ho][Wo], written.
+ *   den_dev  optional float32 [3][Ho][Wo]: per channel, log2 of the accumulated weight
+ *            sum(w * Rhat) of Eq. 1's denominator (NULL to skip). */
+hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                         const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
+                         float *den_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* hmfsr_merge in two halves that share the workspace (same ws, desc and params):
+ * prepare writes the per-frame planes (kernel covariances, robustness) into ws;
+ * accumulate then runs the kernel regression and normalisation from those planes.
+ * hmfsr_merge == prepare + accumulate.  Useful to time or overlap the halves. */
+hmfsr_status hmfsr_merge_prepare(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                 const hmfsr_merge_params *params, void *ws, size_t ws_bytes, void *stream);
+hmfsr_status hmfsr_merge_accumulate(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                    const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
+                                    float *den_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* The per-frame merge stages alone, for inspection and testing (Sec. 5.1.2 and 5.2):
+ *   omega_dev  optional float32 [n_frames][3][height/2][width/2]: the kernel covariance
+ *              entries (Oxx, Oxy, Oyy) in raw px^2 at each half-res pixel (Eq. 4).
+ *   rhat_dev   optional float32 [n_frames][height/2][width/2]: the final robustness Rhat
+ *              (Eq. 9) of each frame on the base frame's half-res grid (1 for the base). */
+hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                const hmfsr_merge_params *params, float *omega_dev, float *rhat_dev,
+                                void *ws, size_t ws_bytes, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *hmfsr_status_string(hmfsr_status s);
+
+/* Library version, e.g. "0.1.0" (static string). */
+const char *hmfsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMFSR_H */

@@ -1,0 +1,239 @@
+"""Handheld multi-frame super-resolution (Wronski et al. 2019) on one sm_103a GPU.
+
+Thin Python binding over the C-ABI library libhmfsr.so (include/hmfsr.h).  PyTorch
+provides device memory and streams; every step of the method runs in the library's
+hand-written CUDA kernels.  The calls follow the paper's statement of the problem:
+
+    motion = align(burst, ref)                           # Sec. 3.2
+    rgb = merge(burst, motion, params, scale)            # Sec. 5, Eq. 1-9
+
+`burst` is a torch.uint16 tensor [n_frames, height, width] of RGGB Bayer frames.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, fields
+
+import torch
+
+from . import _lib
+from ._lib import build  # noqa: F401  (re-exported)
+
+__all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "build", "workspace_size",
+           "out_size", "n_tiles"]
+
+
+@dataclass
+class MergeParams:
+    """Merge tuning (supplement S.2 ranges; mid-range defaults) and the noise model
+    var(x) = noise_a * x + noise_b in DN^2 (Sec. 5.2.2)."""
+    k_detail: float = 0.29
+    k_denoise: float = 4.0
+    d_th: float = 0.005
+    d_tr: float = 0.012
+    k_stretch: float = 4.0
+    k_shrink: float = 2.0
+    t: float = 0.12
+    s1: float = 12.0
+    s2: float = 2.0
+    m_th: float = 0.8
+    noise_a: float = 1.0
+    noise_b: float = 4.0
+    tile: int = 16
+
+    def c(self) -> _lib.MergeParamsC:
+        vals = [getattr(self, f.name) for f in fields(self) if f.name != "tile"]
+        return _lib.MergeParamsC(*[float(v) for v in vals], int(self.tile))
+
+
+@dataclass
+class AlignParams:
+    """Pyramid block matching + Lucas-Kanade (Sec. 3.2)."""
+    tile: int = 16
+    n_levels: int = 4
+    radius: tuple = (1, 4, 4, 4)
+    lk_iters: int = 3
+
+    def c(self) -> _lib.AlignParamsC:
+        r = (ctypes.c_int * 4)(*list(self.radius) + [0] * (4 - len(self.radius)))
+        return _lib.AlignParamsC(int(self.tile), int(self.n_levels), r, int(self.lk_iters))
+
+
+def n_tiles(h: int, w: int, tile: int):
+    return -(-h // tile), -(-w // tile)
+
+
+def out_size(h: int, w: int, scale) -> tuple:
+    num, den = scale
+    return (h * num) // den, (w * num) // den
+
+
+def _desc(burst: torch.Tensor, ref: int, white_level: int) -> _lib.BurstDesc:
+    if burst.dtype != torch.uint16 or burst.dim() != 3:
+        raise TypeError("burst must be a torch.uint16 tensor [n_frames, height, width]")
+    if burst.stride(2) != 1 or burst.stride(0) != burst.shape[1] * burst.stride(1):
+        raise ValueError("burst rows must be contiguous with frames packed back to back")
+    n, h, w = burst.shape
+    return _lib.BurstDesc(n, h, w, burst.stride(1), ref, 0, white_level, 0)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device, stream):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_ws_cache: dict = {}
+
+
+def _workspace(device: torch.device, nbytes: int) -> torch.Tensor:
+    """A reusable, 256-byte aligned scratch buffer per device (grown on demand)."""
+    key = (device.type, device.index)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes + 256:
+        _ws_cache[key] = buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + max(nbytes, 1)]
+
+
+def workspace_size(op: int, burst_shape, tile: int, scale=(1, 1), white_level: int = 4095) -> int:
+    n, h, w = burst_shape
+    d = _lib.BurstDesc(n, h, w, w, 0, 0, white_level, 0)
+    return int(_lib.load().hmfsr_workspace_size(op, ctypes.byref(d), tile, scale[0], scale[1]))
+
+
+def align(burst: torch.Tensor, ref: int = 0, params: AlignParams | None = None, with_int: bool = False,
+          white_level: int = 4095, stream=None):
+    """Tile motion field float32 [n, TY, TX, 2] in raw px (base -> frame), computed by
+    hmfsr_align.  With `with_int`, also the integer block-matching vectors (half-res px)."""
+    L = _lib.load()
+    params = params or AlignParams()
+    if not burst.is_cuda:
+        raise ValueError("burst must be on a CUDA device")
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ty, tx = n_tiles(h, w, params.tile)
+    motion = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
+    mint = torch.empty((n, ty, tx, 2), dtype=torch.int32, device=burst.device) if with_int else None
+    nbytes = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(d), params.tile, 1, 1)
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_align(_ptr(burst), ctypes.byref(d), ctypes.byref(pc), _ptr(motion), _ptr(mint), _ptr(ws),
+                             ws.numel(), _stream(burst.device, stream)), "hmfsr_align")
+    return (motion, mint) if with_int else motion
+
+
+def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
+          with_den: bool = False, white_level: int = 4095, stream=None):
+    """Merged RGB float32 [3, Ho, Wo] in DN (hmfsr_merge).  With `with_den`, also the
+    per-channel log2 of Eq. 1's denominator."""
+    L = _lib.load()
+    params = params or MergeParams()
+    if not (burst.is_cuda and motion.is_cuda):
+        raise ValueError("burst and motion must be on a CUDA device")
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ty, tx = n_tiles(h, w, params.tile)
+    if motion.dtype != torch.float32 or tuple(motion.shape) != (n, ty, tx, 2) or not motion.is_contiguous():
+        raise ValueError(f"motion must be contiguous float32 [{n},{ty},{tx},2]")
+    ho, wo = out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
+                             _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
+               "hmfsr_merge")
+    return (rgb, den) if with_den else rgb
+
+
+def merge_stages(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
+                 white_level: int = 4095, stream=None):
+    """Per-frame merge stages: Omega entries float32 [n, 3, H/2, W/2] (Eq. 4) and the
+    final robustness Rhat float32 [n, H/2, W/2] on the base grid (Eq. 9)."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    omega = torch.empty((n, 3, h // 2, w // 2), dtype=torch.float32, device=burst.device)
+    rhat = torch.empty((n, h // 2, w // 2), dtype=torch.float32, device=burst.device)
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_stages(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(omega),
+                                    _ptr(rhat), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
+               "hmfsr_merge_stages")
+    return omega, rhat
+
+
+def align_merge(burst: torch.Tensor, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
+                align_params: AlignParams | None = None, device=None, out=None, white_level: int = 4095,
+                stream=None):
+    """The whole path, align then merge.  A host `burst` (ideally pinned) is copied to the
+    device first and the RGB result is copied back into `out` (or a new host tensor)."""
+    params = params or MergeParams()
+    align_params = align_params or AlignParams(tile=params.tile)
+    host = not burst.is_cuda
+    dev_burst = burst.to(device or "cuda", non_blocking=True) if host else burst
+    motion = align(dev_burst, ref, align_params, white_level=white_level, stream=stream)
+    rgb = merge(dev_burst, motion, params, scale, ref, white_level=white_level, stream=stream)
+    if not host:
+        return rgb
+    if out is None:
+        out = torch.empty(rgb.shape, dtype=rgb.dtype, pin_memory=True)
+    out.copy_(rgb, non_blocking=True)
+    return out
+
+
+def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
+                  white_level: int = 4095, stream=None) -> torch.Tensor:
+    """First half of `merge` (hmfsr_merge_prepare): per-frame planes into the device's
+    cached workspace, which `merge_accumulate` then reads."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_prepare(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(ws),
+                                     ws.numel(), _stream(burst.device, stream)), "hmfsr_merge_prepare")
+    return ws
+
+
+def merge_accumulate(burst: torch.Tensor, motion: torch.Tensor, ws: torch.Tensor, params: MergeParams | None = None,
+                     scale=(1, 1), ref: int = 0, out: torch.Tensor | None = None, den: torch.Tensor | None = None,
+                     white_level: int = 4095, stream=None) -> torch.Tensor:
+    """Second half of `merge` (hmfsr_merge_accumulate) from the planes in `ws`."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ho, wo = out_size(h, w, scale)
+    if out is None:
+        out = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_accumulate(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0],
+                                        scale[1], _ptr(out), _ptr(den), _ptr(ws), ws.numel(),
+                                        _stream(burst.device, stream)), "hmfsr_merge_accumulate")
+    return out
+
+
+def pyramid_levels(h: int, w: int, n_levels_max: int = 4) -> int:
+    """Number of alignment pyramid levels for a frame (factors 2, 4, 4; sides >= 16)."""
+    lh, lw, nl = h // 2, w // 2, 1
+    for f in (2, 4, 4)[: max(0, min(n_levels_max, 4) - 1)]:
+        lh, lw = lh // f, lw // f
+        if lh < 16 or lw < 16:
+            break
+        nl += 1
+    return nl
+
+
+def launches_per_call(n_frames: int, h: int, w: int, n_levels_max: int = 4) -> dict:
+    """Kernel launches made by one hmfsr_align / hmfsr_merge_prepare / accumulate call."""
+    nl = pyramid_levels(h, w, n_levels_max)
+    return {"align": 1 + (nl - 1) + nl + 1, "merge_prepare": 4 + (n_frames - 1), "merge_accumulate": 1}

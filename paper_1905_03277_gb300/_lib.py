@@ -1,0 +1,121 @@
+"""Build and load libhmfsr.so (the C-ABI library of hand-written sm_103a kernels)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(PKG, "_build")
+LIB_PATH = os.path.join(PKG, "libhmfsr.so")
+SOURCES = ("api.cu", "align.cu", "merge.cu")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+
+
+def _nvcc() -> str:
+    home = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    cand = os.path.join(home, "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _inputs():
+    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files += [os.path.join(CSRC, "hmfsr_internal.cuh"), os.path.join(INCLUDE, "hmfsr.h")]
+    return files
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit for sm_103a (in parallel) and link libhmfsr.so."""
+    newest = max(os.path.getmtime(f) for f in _inputs())
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    os.makedirs(BUILD, exist_ok=True)
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(r.stdout, r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ---------------------------------------------------------------------------------------
+# ctypes mirror of include/hmfsr.h
+# ---------------------------------------------------------------------------------------
+class BurstDesc(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int), ("height", ctypes.c_int), ("width", ctypes.c_int),
+                ("pitch_elems", ctypes.c_int), ("ref", ctypes.c_int), ("cfa", ctypes.c_int),
+                ("white_level", ctypes.c_int), ("black_level", ctypes.c_int)]
+
+
+class AlignParamsC(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("n_levels", ctypes.c_int), ("radius", ctypes.c_int * 4),
+                ("lk_iters", ctypes.c_int)]
+
+
+class MergeParamsC(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
+                                              "t", "s1", "s2", "m_th", "noise_a", "noise_b")] + [
+        ("tile", ctypes.c_int)]
+
+
+OP_ALIGN, OP_MERGE, OP_MERGE_STAGES = 0, 1, 2
+EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
+           "hmfsr_merge_stages", "hmfsr_status_string", "hmfsr_version")
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libhmfsr.so; raises if it is missing (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhmfsr.so not found at {path}: run paper_1905_03277_gb300.build() first")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, sz, ci = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    L.hmfsr_workspace_size.argtypes = [ci, P(BurstDesc), ci, ci, ci]
+    L.hmfsr_workspace_size.restype = sz
+    L.hmfsr_align.argtypes = [vp, P(BurstDesc), P(AlignParamsC), vp, vp, vp, sz, vp]
+    L.hmfsr_align.restype = ci
+    L.hmfsr_merge.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp, sz, vp]
+    L.hmfsr_merge.restype = ci
+    L.hmfsr_merge_prepare.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, sz, vp]
+    L.hmfsr_merge_prepare.restype = ci
+    L.hmfsr_merge_accumulate.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp, sz, vp]
+    L.hmfsr_merge_accumulate.restype = ci
+    L.hmfsr_merge_stages.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, vp, vp, sz, vp]
+    L.hmfsr_merge_stages.restype = ci
+    L.hmfsr_status_string.argtypes = [ci]
+    L.hmfsr_status_string.restype = ctypes.c_char_p
+    L.hmfsr_version.argtypes = []
+    L.hmfsr_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status: int, what: str):
+    if status != 0:
+        msg = load().hmfsr_status_string(status).decode()
+        raise RuntimeError(f"{what} failed: {msg} ({status})")

@@ -1,0 +1,246 @@
+// C-ABI entry points of libhmfsr: host-side validation, workspace layout and launches.
+#include <math.h>
+#include <string.h>
+
+#include "hmfsr_internal.cuh"
+
+using namespace hmfsr;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Bump allocator over the caller's workspace (or a null base for size queries).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <typename T>
+    T *take(size_t count) {
+        size_t o = off;
+        off = align_up(off + count * sizeof(T));
+        return base ? reinterpret_cast<T *>(base + o) : nullptr;
+    }
+};
+
+bool valid_desc(const hmfsr_burst_desc *d, hmfsr_status *why) {
+    *why = HMFSR_ERR_INVALID_ARG;
+    if (!d) return false;
+    if (d->n_frames < 1 || d->n_frames > 4096) return false;
+    if (d->height < 4 || d->width < 4 || (d->height & 1) || (d->width & 1)) return false;
+    if (d->height > 65536 || d->width > 65536) return false;
+    if (d->pitch_elems < d->width || (d->pitch_elems & 1)) return false;
+    if (d->ref < 0 || d->ref >= d->n_frames) return false;
+    // 3x3 sums of a 16-bit guide channel must fit 16 bits, Lq 16 bits
+    if (d->white_level < 1 || d->white_level > 7281) return false;
+    if (d->cfa != 0 || d->black_level != 0) { *why = HMFSR_ERR_UNSUPPORTED; return false; }
+    return true;
+}
+
+bool valid_tile(int tile) { return tile == 8 || tile == 16 || tile == 32 || tile == 64; }
+
+bool valid_scale(int num, int den) { return num >= 1 && den >= 1 && num <= 8 && den <= 8 && num >= den && num <= 4 * den; }
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
+bool finite_nonneg(float x) { return isfinite(x) && x >= 0.f; }
+
+bool valid_merge_params(const hmfsr_merge_params *p) {
+    if (!p) return false;
+    if (!finite_pos(p->k_detail) || !finite_pos(p->k_denoise) || !finite_pos(p->d_tr) || !finite_pos(p->k_stretch) ||
+        !finite_pos(p->k_shrink))
+        return false;
+    if (!isfinite(p->d_th) || !isfinite(p->t) || !finite_nonneg(p->s1) || !finite_nonneg(p->s2) || !isfinite(p->m_th))
+        return false;
+    if (!finite_nonneg(p->noise_a) || !finite_nonneg(p->noise_b)) return false;
+    return valid_tile(p->tile);
+}
+
+bool valid_align_params(const hmfsr_align_params *p) {
+    if (!p || !valid_tile(p->tile) || p->n_levels < 1 || p->n_levels > 4 || p->lk_iters < 0 || p->lk_iters > 16)
+        return false;
+    for (int l = 0; l < 4; ++l)
+        if (p->radius[l] < 0 || p->radius[l] > 7) return false;
+    return true;
+}
+
+Geom make_geom(const hmfsr_burst_desc *d, int tile) {
+    Geom g;
+    g.n = d->n_frames; g.h = d->height; g.w = d->width; g.pitch = d->pitch_elems; g.ref = d->ref;
+    g.wl = d->white_level; g.hh = d->height / 2; g.wh = d->width / 2;
+    g.tile = tile; g.ty = div_up(d->height, tile); g.tx = div_up(d->width, tile);
+    return g;
+}
+
+// alignment workspace: pyramid levels and the integer vectors of every level
+size_t carve_align(void *ws, const Geom &g, int tile, int n_levels_max, AlignLevels *L) {
+    static const int fac[3] = {2, 4, 4};
+    Carver c(ws);
+    int t = tile / 2;
+    L->lh[0] = g.hh; L->lw[0] = g.wh;
+    int nl = 1;
+    while (nl < n_levels_max && nl < 4) {
+        int nh = L->lh[nl - 1] / fac[nl - 1], nw = L->lw[nl - 1] / fac[nl - 1];
+        if (nh < 16 || nw < 16) break;
+        L->lh[nl] = nh; L->lw[nl] = nw;
+        ++nl;
+    }
+    L->n_levels = nl;
+    for (int l = 0; l < nl; ++l) {
+        L->lty[l] = div_up(L->lh[l], t);
+        L->ltx[l] = div_up(L->lw[l], t);
+        L->img[l] = c.take<uint16_t>((size_t)g.n * L->lh[l] * L->lw[l]);
+        L->vec[l] = c.take<int2>((size_t)g.n * L->lty[l] * L->ltx[l]);
+    }
+    return c.off;
+}
+
+size_t carve_merge(void *ws, const Geom &g, MergePlanes *P) {
+    Carver c(ws);
+    size_t hw = (size_t)g.hh * g.wh;
+    P->guide = c.take<ushort4>(g.n * hw);
+    P->s1 = c.take<uint2>(g.n * hw);
+    P->base_stats = c.take<float4>(hw);
+    P->kern = c.take<float4>(g.n * hw);
+    P->rhat = c.take<float>(g.n * hw);
+    P->s_tile = c.take<float>((size_t)g.n * g.ty * g.tx);
+    return c.off;
+}
+
+MergeConsts consts_of(const hmfsr_merge_params *p) {
+    MergeConsts c;
+    c.k_detail = p->k_detail; c.k_denoise = p->k_denoise; c.d_th = p->d_th; c.d_tr = p->d_tr;
+    c.k_stretch = p->k_stretch; c.k_shrink = p->k_shrink; c.t = p->t; c.s1 = p->s1; c.s2 = p->s2;
+    c.m_th = p->m_th; c.noise_a = p->noise_a; c.noise_b = p->noise_b;
+    return c;
+}
+
+hmfsr_status check_ws(void *ws, size_t ws_bytes, size_t need) {
+    if (need == 0) return HMFSR_OK;
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1))) return HMFSR_ERR_WORKSPACE;
+    return HMFSR_OK;
+}
+
+bool aligned4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; }
+
+hmfsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HMFSR_OK : HMFSR_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+size_t hmfsr_workspace_size(int op, const hmfsr_burst_desc *desc, int tile, int scale_num, int scale_den) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why) || !valid_tile(tile)) return 0;
+    Geom g = make_geom(desc, tile);
+    if (op == HMFSR_OP_ALIGN) {
+        AlignLevels L;
+        return carve_align(nullptr, g, tile, 4, &L);
+    }
+    if (op == HMFSR_OP_MERGE || op == HMFSR_OP_MERGE_STAGES) {
+        if (op == HMFSR_OP_MERGE && !valid_scale(scale_num, scale_den)) return 0;
+        MergePlanes P;
+        return carve_merge(nullptr, g, &P);
+    }
+    return 0;
+}
+
+hmfsr_status hmfsr_align(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const hmfsr_align_params *params,
+                         float *motion_dev, int32_t *motion_int_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !aligned4(burst_dev) || !valid_align_params(params)) return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    AlignLevels L;
+    size_t need = carve_align(nullptr, g, params->tile, params->n_levels, &L);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_align(ws, g, params->tile, params->n_levels, &L);
+    return cuda_status(launch_align(burst_dev, g, *params, L, motion_dev, motion_int_dev, (cudaStream_t)stream));
+}
+
+hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                         const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
+                         float *den_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !rgb_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params) ||
+        !valid_scale(scale_num, scale_den))
+        return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    size_t need = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    cudaStream_t s = (cudaStream_t)stream;
+    MergeConsts c = consts_of(params);
+    cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
+    if (e != cudaSuccess) return HMFSR_ERR_CUDA;
+    return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
+}
+
+hmfsr_status hmfsr_merge_prepare(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                 const hmfsr_merge_params *params, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params)) return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    hmfsr_status st = check_ws(ws, ws_bytes, carve_merge(nullptr, g, &P));
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    return cuda_status(launch_merge_prep(burst_dev, motion_dev, g, consts_of(params), P, (cudaStream_t)stream));
+}
+
+hmfsr_status hmfsr_merge_accumulate(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                    const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
+                                    float *den_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !rgb_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params) ||
+        !valid_scale(scale_num, scale_den))
+        return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    hmfsr_status st = check_ws(ws, ws_bytes, carve_merge(nullptr, g, &P));
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    return cuda_status(
+        launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, (cudaStream_t)stream));
+}
+
+hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                const hmfsr_merge_params *params, float *omega_dev, float *rhat_dev, void *ws,
+                                size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params)) return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    size_t need = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, consts_of(params), P, s);
+    if (e != cudaSuccess) return HMFSR_ERR_CUDA;
+    return cuda_status(launch_export_stages(g, P, omega_dev, rhat_dev, s));
+}
+
+const char *hmfsr_status_string(hmfsr_status s) {
+    switch (s) {
+        case HMFSR_OK: return "ok";
+        case HMFSR_ERR_INVALID_ARG: return "invalid argument";
+        case HMFSR_ERR_UNSUPPORTED: return "unsupported";
+        case HMFSR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case HMFSR_ERR_CUDA: return "CUDA error";
+        case HMFSR_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *hmfsr_version(void) { return "0.1.0"; }
+
+}  // extern "C"

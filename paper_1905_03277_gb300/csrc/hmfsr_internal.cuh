@@ -1,0 +1,82 @@
+// Internal declarations shared by the hmfsr CUDA translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmfsr.h"
+
+namespace hmfsr {
+
+// ---------------------------------------------------------------------------------------
+// integer helpers (exact; both operands small)
+// ---------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int floor_div(int a, int b) {  // b > 0
+    int q = a / b;
+    return (q * b > a) ? q - 1 : q;
+}
+__host__ __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+__host__ __device__ __forceinline__ int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// floor(q * v) for a small positive integer q and a float v, exactly: the FP32 product is
+// rounded once; when it lands on an integer from above, the exact remainder (fma) says so.
+__device__ __forceinline__ int floor_mul(int q, float v) {
+    float h = (float)q * v;
+    float f = floorf(h);
+    if (f == h && fmaf((float)q, v, -h) < 0.0f) f -= 1.0f;
+    return (int)f;
+}
+
+// 2^x on the SFU (ex2.approx, flush-to-zero): relative error ~2^-22.
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------------------
+// geometry of one burst
+// ---------------------------------------------------------------------------------------
+struct Geom {
+    int n, h, w, pitch, ref, wl;
+    int hh, wh;          // half-res size
+    int tile, ty, tx;    // motion-field tiles (raw px)
+};
+
+// Per-frame merge planes in the workspace (one entry per half-res pixel per frame).
+struct MergePlanes {
+    ushort4 *guide;      // [n][hh*wh] {R, G1+G2, B, Lq}
+    uint2 *s1;           // [n][hh*wh] 3x3 guide sums {R | B << 16, G1+G2}
+    float4 *base_stats;  // [hh*wh] {max(sum sigma^2, eps), dmd^2 R, G, B} of the base frame
+    float4 *kern;        // [n][hh*wh] kernel covariance as {a, delta, ux, uy}: Omega = a I + delta u u^T
+    float *rhat;         // [n][hh*wh] final robustness (base grid); unused for the base frame
+    float *s_tile;       // [n][ty*tx] robustness scale from the motion prior
+};
+
+struct MergeConsts {
+    float k_detail, k_denoise, d_th, d_tr, k_stretch, k_shrink;
+    float t, s1, s2, m_th, noise_a, noise_b;
+};
+
+// ---------------------------------------------------------------------------------------
+// launchers (return cudaGetLastError() of the launches)
+// ---------------------------------------------------------------------------------------
+// alignment
+struct AlignLevels {
+    int n_levels;
+    int lh[4], lw[4];          // level sizes
+    int lty[4], ltx[4];        // tile grid per level
+    uint16_t *img[4];          // [n][lh*lw] per level
+    int2 *vec[4];              // [n][lty*ltx] integer vectors per level
+};
+cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
+                         float *motion, int32_t *motion_int, cudaStream_t s);
+
+// merge
+cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                              const MergePlanes &P, cudaStream_t s);
+cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
+                               int snum, int sden, float *rgb, float *den, cudaStream_t s);
+cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *omega, float *rhat, cudaStream_t s);
+
+}  // namespace hmfsr

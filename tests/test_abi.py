@@ -1,0 +1,128 @@
+"""The C-ABI library builds, loads, exports what include/hmfsr.h declares, and rejects bad
+arguments on the host before any launch.  No GPU needed (no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1905_03277_gb300 as hm
+from paper_1905_03277_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    hm.build()
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(hmfsr_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert {"hmfsr_align", "hmfsr_merge", "hmfsr_workspace_size"} <= names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(_lib.EXPORTS) <= names
+
+
+def test_status_strings(L):
+    assert L.hmfsr_status_string(0) == b"ok"
+    assert b"workspace" in L.hmfsr_status_string(-3)
+    assert L.hmfsr_version().startswith(b"0.")
+
+
+def desc(n=8, h=256, w=256, pitch=None, ref=0, cfa=0, wl=4095, bl=0):
+    return _lib.BurstDesc(n, h, w, pitch or w, ref, cfa, wl, bl)
+
+
+def test_workspace_size_queries(L):
+    d = desc()
+    ws_m = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), 16, 1, 1)
+    ws_a = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(d), 16, 1, 1)
+    hw = 128 * 128
+    # guide 8 B + sums 8 B + kernel 16 B + Rhat 4 B per half-res pixel per frame, plus base stats
+    assert ws_m >= 8 * hw * 36 + 16 * hw
+    assert ws_a >= 8 * hw * 2
+    assert L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), 16, 1, 2) == 0      # scale < 1
+    assert L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), 12, 1, 1) == 0      # unsupported tile
+    assert L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(desc(h=255)), 16, 1, 1) == 0
+    assert L.hmfsr_workspace_size(99, ctypes.byref(d), 16, 1, 1) == 0
+
+
+def _merge_call(L, d, params=None, snum=1, sden=1, burst=16, motion=16, rgb=16, ws=256, ws_bytes=1 << 40):
+    p = params or hm.MergeParams().c()
+    return L.hmfsr_merge(ctypes.c_void_p(burst) if burst else None, ctypes.byref(d) if d else None,
+                         ctypes.c_void_p(motion) if motion else None, ctypes.byref(p), snum, sden,
+                         ctypes.c_void_p(rgb) if rgb else None, None, ctypes.c_void_p(ws) if ws else None,
+                         ws_bytes, None)
+
+
+def test_merge_rejects_bad_arguments_on_host(L):
+    # every case returns before any launch, so fake (never dereferenced) pointers are safe
+    assert _merge_call(L, None) == -1
+    assert _merge_call(L, desc(h=7)) == -1
+    assert _merge_call(L, desc(ref=8)) == -1
+    assert _merge_call(L, desc(pitch=100)) == -1
+    assert _merge_call(L, desc(wl=9000)) == -1
+    assert _merge_call(L, desc(cfa=1)) == -2
+    assert _merge_call(L, desc(bl=64)) == -2
+    assert _merge_call(L, desc(), burst=0) == -1
+    assert _merge_call(L, desc(), burst=17) == -1          # misaligned burst pointer
+    assert _merge_call(L, desc(), rgb=0) == -1
+    assert _merge_call(L, desc(), snum=1, sden=2) == -1
+    assert _merge_call(L, desc(), snum=9, sden=1) == -1
+    bad = hm.MergeParams(k_detail=0.0).c()
+    assert _merge_call(L, desc(), params=bad) == -1
+    bad = hm.MergeParams(noise_a=float("nan")).c()
+    assert _merge_call(L, desc(), params=bad) == -1
+    bad = hm.MergeParams(tile=24).c()
+    assert _merge_call(L, desc(), params=bad) == -1
+    assert _merge_call(L, desc(), ws=0) == -3
+    assert _merge_call(L, desc(), ws=128) == -3             # misaligned workspace
+    assert _merge_call(L, desc(), ws_bytes=1000) == -3     # too small
+
+
+def test_align_rejects_bad_arguments_on_host(L):
+    d = desc()
+
+    def call(p, motion=16, ws_bytes=1 << 40):
+        pc = p.c()
+        return L.hmfsr_align(ctypes.c_void_p(16), ctypes.byref(d), ctypes.byref(pc),
+                             ctypes.c_void_p(motion) if motion else None, None, ctypes.c_void_p(256), ws_bytes, None)
+
+    assert call(hm.AlignParams(tile=12)) == -1
+    assert call(hm.AlignParams(n_levels=0)) == -1
+    assert call(hm.AlignParams(n_levels=5)) == -1
+    assert call(hm.AlignParams(radius=(1, 9, 4, 4))) == -1
+    assert call(hm.AlignParams(lk_iters=-1)) == -1
+    assert call(hm.AlignParams(), motion=0) == -1
+    assert call(hm.AlignParams(), ws_bytes=10) == -3
+
+
+def test_product_path_does_not_use_the_oracle():
+    src_dir = os.path.join(ROOT, "paper_1905_03277_gb300")
+    for fn in os.listdir(src_dir):
+        if fn.endswith(".py"):
+            txt = open(os.path.join(src_dir, fn)).read()
+            assert "import oracle" not in txt and "from oracle" not in txt, fn
+
+
+def test_load_fails_loudly_without_library(tmp_path):
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="libhmfsr.so not found"):
+            _lib.load(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved

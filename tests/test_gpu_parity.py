@@ -1,0 +1,230 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Bars (stated by the task and derived in the design notes):
+  * integer alignment (block-matching vectors): bit-exact;
+  * Lucas-Kanade motion: within 1e-3 px on well-conditioned tiles;
+  * merge: per channel, max |gpu - oracle| <= 1e-4 * WL and mean <= 1e-6 * WL, with both
+    sides given the same float32 motion field (the oracle's own alignment).
+"""
+import numpy as np
+import pytest
+import torch
+
+import burstgen
+import oracle
+import paper_1905_03277_gb300 as hm
+
+pytestmark = pytest.mark.gpu
+
+WL = 4095
+MAX_ABS = 1e-4 * WL
+MEAN_ABS = 1e-6 * WL
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hm.build()
+    return torch.device("cuda:0")
+
+
+def params_of(b, **kw):
+    return hm.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2, **kw)
+
+
+def oparams(p: hm.MergeParams) -> oracle.MergeParams:
+    return oracle.MergeParams(**{k: getattr(p, k) for k in oracle.MergeParams.__dataclass_fields__})
+
+
+def merge_errors(gpu, ref):
+    err = np.abs(gpu.astype(np.float64) - ref)
+    return err.reshape(3, -1).max(axis=1), err.reshape(3, -1).mean(axis=1)
+
+
+def assert_merge_close(gpu, ref, what=""):
+    assert np.isfinite(gpu).all(), what
+    mx, mn = merge_errors(gpu, ref)
+    assert (mx <= MAX_ABS).all() and (mn <= MEAN_ABS).all(), f"{what}: max {mx}, mean {mn}"
+
+
+def lk_conditioned(raw_np, ref, tile, floor=1e-6):
+    """Tiles whose level-0 normal matrix is well conditioned (lambda_min / lambda_max)."""
+    lq = oracle.luma(raw_np[ref]).astype(np.float64)
+    gx = np.zeros_like(lq)
+    gy = np.zeros_like(lq)
+    gx[:, 1:-1] = lq[:, 2:] - lq[:, :-2]
+    gx[:, 0] = lq[:, 1] - lq[:, 0]
+    gx[:, -1] = lq[:, -1] - lq[:, -2]
+    gy[1:-1] = lq[2:] - lq[:-2]
+    gy[0] = lq[1] - lq[0]
+    gy[-1] = lq[-1] - lq[-2]
+    t = tile // 2
+    H, W = lq.shape
+    ty, tx = -(-H // t), -(-W // t)
+    pad = lambda a: np.pad(a, ((0, ty * t - H), (0, tx * t - W)), mode="edge")
+    sxx = (pad(gx * gx)).reshape(ty, t, tx, t).sum(axis=(1, 3))
+    syy = (pad(gy * gy)).reshape(ty, t, tx, t).sum(axis=(1, 3))
+    sxy = (pad(gx * gy)).reshape(ty, t, tx, t).sum(axis=(1, 3))
+    tr = sxx + syy
+    det = sxx * syy - sxy * sxy
+    disc = np.sqrt(np.maximum(tr * tr / 4 - det, 0))
+    lmin, lmax = tr / 2 - disc, tr / 2 + disc
+    return lmin > floor * np.maximum(lmax, 1e-30) * 1e3
+
+
+def check_align(raw, dev, ref=0, tile=16, **kw):
+    raw_np = raw.numpy()
+    ap = hm.AlignParams(tile=tile, **kw)
+    g_motion, g_int = hm.align(raw.to(dev), ref, ap, with_int=True)
+    mi, mf, fl, _ = oracle.align(raw_np, ref=ref, tile=tile, n_levels=ap.n_levels, radius=ap.radius,
+                                 lk_iters=ap.lk_iters)
+    g_int = g_int.cpu().numpy()
+    g_motion = g_motion.cpu().numpy()
+    assert np.array_equal(g_int, mi), "integer block matching differs"
+    # skipped (ill-conditioned) tiles are exactly 2u on both sides
+    sk = fl.astype(bool)
+    assert np.array_equal(g_motion[sk], (2 * mi[sk]).astype(np.float32))
+    good = lk_conditioned(raw_np, ref, tile)[None].repeat(raw_np.shape[0], 0) & ~sk
+    err = np.abs(g_motion - mf).max(axis=-1)
+    assert err[good].max() <= 1e-3, f"LK max err {err[good].max()} on conditioned tiles"
+    return mf.astype(np.float32)
+
+
+# --------------------------------------------------------------------------------------
+# alignment
+# --------------------------------------------------------------------------------------
+def test_align_tiny(dev, tiny_burst):
+    check_align(tiny_burst["raw"], dev)
+
+
+def test_align_ragged_sizes_and_ref(dev):
+    b = burstgen.make_burst(dict(n=4, h=136, w=200, gain=1.0, read=2.0, motion="global", scale=(1, 1)), seed=21)
+    check_align(b["raw"], dev, ref=2)
+    check_align(b["raw"], dev, ref=0, tile=32, radius=(2, 3, 4, 4))
+    check_align(b["raw"], dev, ref=1, tile=8, n_levels=2, lk_iters=5)
+
+
+# --------------------------------------------------------------------------------------
+# merge stages
+# --------------------------------------------------------------------------------------
+def test_merge_stages_tiny(dev, tiny_burst):
+    raw = tiny_burst["raw"]
+    raw_np = raw.numpy()
+    _, mf, _, _ = oracle.align(raw_np)
+    mv = mf.astype(np.float32)
+    p = params_of(tiny_burst)
+    om, rh = hm.merge_stages(raw.to(dev), torch.from_numpy(mv).to(dev), p)
+    om = om.cpu().numpy()
+    rh = rh.cpu().numpy()
+    op = oparams(p)
+    for f in range(raw_np.shape[0]):
+        ref_om = oracle.omega_plane(raw_np[f], op)
+        scale = np.abs(ref_om[0]) + np.abs(ref_om[2])
+        assert (np.abs(om[f] - ref_om) <= 2e-6 * scale[None]).all(), f"Omega frame {f}"
+        if f == 0:
+            assert np.all(rh[f] == 1.0)
+            continue
+        _, ref_rh = oracle.robustness(raw_np[0], raw_np[f], mv[f], 16, op)
+        assert np.abs(rh[f] - ref_rh).max() <= 2e-5, f"Rhat frame {f}: {np.abs(rh[f] - ref_rh).max()}"
+
+
+def test_identical_frames_robustness_is_one(dev, tiny_burst):
+    raw = tiny_burst["raw"][:1].repeat(4, 1, 1).contiguous()
+    mv = torch.zeros((4, 16, 16, 2), dtype=torch.float32, device=dev)
+    _, rh = hm.merge_stages(raw.to(dev), mv, params_of(tiny_burst))
+    assert bool((rh == 1.0).all())
+
+
+# --------------------------------------------------------------------------------------
+# merge
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("scale", [(1, 1), (3, 2), (2, 1)])
+def test_merge_tiny(dev, tiny_burst, scale):
+    raw = tiny_burst["raw"]
+    raw_np = raw.numpy()
+    _, mf, _, _ = oracle.align(raw_np)
+    mv = mf.astype(np.float32)
+    p = params_of(tiny_burst)
+    rgb = hm.merge(raw.to(dev), torch.from_numpy(mv).to(dev), p, scale).cpu().numpy()
+    ref = oracle.merge(raw_np, mv, oparams(p), scale=scale)
+    assert rgb.shape == ref.shape
+    assert_merge_close(rgb, ref, f"scale {scale}")
+
+
+def test_merge_denominator(dev, tiny_burst):
+    raw = tiny_burst["raw"]
+    raw_np = raw.numpy()
+    _, mf, _, _ = oracle.align(raw_np)
+    mv = mf.astype(np.float32)
+    p = params_of(tiny_burst)
+    _, den = hm.merge(raw.to(dev), torch.from_numpy(mv).to(dev), p, (1, 1), with_den=True)
+    _, oden = oracle.merge(raw_np, mv, oparams(p), with_den=True)
+    assert np.abs(den.cpu().numpy() - np.log2(oden)).max() <= 1e-3
+
+
+def test_merge_edge_cases(dev):
+    b = burstgen.make_burst(dict(n=5, h=136, w=200, gain=2.0, read=4.0, motion="global", scale=(1, 1)), seed=22)
+    raw = b["raw"]
+    raw_np = raw.numpy()
+    p = params_of(b)
+    ty, tx = hm.n_tiles(136, 200, 16)
+    rng = np.random.default_rng(0)
+    # large and odd motion: windows partly or wholly outside the frame, some tiles rejected
+    mv = rng.uniform(-3, 3, size=(5, ty, tx, 2)).astype(np.float32)
+    mv[3, :3, :4] = (41.25, -37.5)
+    mv[4, -2:, -3:] = (-250.0, 180.0)
+    mv[2] = np.round(mv[2] * 4) / 4   # quarter-pixel values: exact window-centre ties
+    for ref in (0, 3):
+        for scale in [(1, 1), (3, 2), (2, 1)]:
+            rgb = hm.merge(raw.to(dev), torch.from_numpy(mv).to(dev), p, scale, ref=ref).cpu().numpy()
+            oref = oracle.merge(raw_np, mv, oparams(p), scale=scale, ref=ref)
+            assert_merge_close(rgb, oref, f"ref {ref} scale {scale}")
+    # a single frame
+    one = hm.merge(raw[:1].to(dev), torch.from_numpy(mv[:1]).to(dev), p, (2, 1)).cpu().numpy()
+    assert_merge_close(one, oracle.merge(raw_np[:1], mv[:1], oparams(p), scale=(2, 1)), "single frame")
+    # the smallest frame
+    small = raw[:3, :4, :6].contiguous()
+    smv = np.zeros((3, 1, 1, 2), np.float32)
+    smv[1] = (0.3, -0.7)
+    got = hm.merge(small.to(dev), torch.from_numpy(smv).to(dev), p, (3, 2)).cpu().numpy()
+    assert_merge_close(got, oracle.merge(small.numpy(), smv, oparams(p), scale=(3, 2)), "4x6 frame")
+
+
+def test_merge_rejects_bad_arguments(dev, tiny_burst):
+    raw = tiny_burst["raw"].to(dev)
+    mv = torch.zeros((8, 16, 16, 2), dtype=torch.float32, device=dev)
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        hm.merge(raw, mv, hm.MergeParams(k_detail=-1.0))
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        hm.merge(raw, mv, scale=(1, 2))
+
+
+# --------------------------------------------------------------------------------------
+# full-size workloads, sampled outputs
+# --------------------------------------------------------------------------------------
+def sample_pixels(ho, wo, k, seed):
+    rng = np.random.default_rng(seed)
+    xy = np.stack([rng.integers(0, wo, k), rng.integers(0, ho, k)], axis=1)
+    edge = [(0, 0), (wo - 1, 0), (0, ho - 1), (wo - 1, ho - 1), (wo // 2, 0), (0, ho // 2), (wo - 1, ho // 2),
+            (wo // 2, ho - 1)]
+    return np.concatenate([np.array(edge), xy]).astype(np.int32)
+
+
+@pytest.mark.parametrize("config,k", [("12mp", 3000), ("sr15", 1500)])
+def test_full_size_sampled(dev, config, k):
+    b = burstgen.make_burst(config, device=dev)
+    raw = b["raw"]
+    raw_np = raw.cpu().numpy()
+    mv = check_align(raw.cpu(), dev)          # bit-exact integer stage on every tile
+    p = params_of(b)
+    scale = b["scale"]
+    rgb = hm.merge(raw, torch.from_numpy(mv).to(dev), p, scale).cpu().numpy()
+    ho, wo = rgb.shape[1:]
+    xy = sample_pixels(ho, wo, k, seed=5)
+    ref = oracle.merge_pixels(raw_np, mv, oparams(p), xy, scale=scale)
+    got = rgb[:, xy[:, 1], xy[:, 0]].T
+    err = np.abs(got.astype(np.float64) - ref)
+    assert np.isfinite(got).all()
+    assert err.max(axis=0).max() <= MAX_ABS, f"max {err.max(axis=0)}"
+    assert (err.mean(axis=0) <= MEAN_ABS).all(), f"mean {err.mean(axis=0)}"
