@@ -730,8 +730,8 @@ static void tile_search(const level_img *Lr, const level_img *La, int t, int tx,
  * (clamped), H = sum g g^T over the tile, each iteration r(p) = I_alt(p + u + delta)
  * - I_ref(p) with bilinear sampling (clamped) and delta <- delta - H^-1 sum g r, delta
  * clamped to [-1, 1] per axis; the update is skipped when tr H == 0 or
- * det H <= 1e-9 tr(H)^2.  H is accumulated exactly in integers (64 H) so that this
- * guard is the same FP64 operation sequence in any implementation. */
+ * det H <= 1e-9 tr(H)^2.  H is accumulated exactly in integers (64 H) and the guard is
+ * evaluated exactly (128-bit integers), so any implementation takes the same decision. */
 static int lk_tile(const level_img *Lr, const level_img *La, int t, int tx, int ty, int ux, int uy, int iters,
                    double *ox, double *oy)
 {
@@ -745,11 +745,11 @@ static int lk_tile(const level_img *Lr, const level_img *La, int t, int tx, int 
         }
     /* g = (Lq difference) / 8 since I = Lq / 4 and central differences halve */
     double Hxx = (double)hxx, Hxy = (double)hxy, Hyy = (double)hyy;
-    double tr = Hxx + Hyy;
-    double det = Hxx * Hyy - Hxy * Hxy;
-    double trsq = tr * tr;
+    /* guard evaluated exactly: 10^9 det H <= tr(H)^2 in 128-bit integers */
+    __int128 det_i = (__int128)hxx * hyy - (__int128)hxy * hxy;
+    __int128 tr_i = (__int128)hxx + hyy;
     double dx = 0.0, dy = 0.0;
-    int skipped = (tr == 0.0) || (det <= 1e-9 * trsq);
+    int skipped = (tr_i == 0) || ((__int128)1000000000 * det_i <= tr_i * tr_i);
     if (!skipped) {
         for (int it = 0; it < iters; ++it) {
             double bx = 0.0, by = 0.0;
