@@ -146,17 +146,17 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
     if (i >= n * ty * tx) return;
     int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
     const float2 *mv = motion + (size_t)f * ty * tx;
-    double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+    // min / max are exact in FP32; the span, its length and the threshold are FP64
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
     for (int j = -1; j <= 1; ++j)
         for (int k = -1; k <= 1; ++k) {
             int yy = y + j, xx = x + k;
             if (yy < 0 || yy >= ty || xx < 0 || xx >= tx) continue;
             float2 v = mv[(size_t)yy * tx + xx];
-            double vx = (double)v.x, vy = (double)v.y;
-            mnx = fmin(mnx, vx); mxx = fmax(mxx, vx);
-            mny = fmin(mny, vy); mxy = fmax(mxy, vy);
+            mnx = fminf(mnx, v.x); mxx = fmaxf(mxx, v.x);
+            mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
         }
-    double Mx = __dsub_rn(mxx, mnx), My = __dsub_rn(mxy, mny);
+    double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
     double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
     s_tile[i] = (M > (double)m_th) ? s1 : s2;
 }
@@ -244,28 +244,57 @@ __global__ void __launch_bounds__(kRobW *kRobH) k_rob(const uint2 *__restrict__ 
 // --------------------------------------------------------------------------------------
 constexpr int kMergeW = 32, kMergeH = 4;
 
-template <bool kDen>
+// exact uint16 -> float on the FMA pipe (v < 2^23)
+__device__ __forceinline__ float u16f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
+
+// The 3x3 Bayer neighbourhood of frame sample rows around (kx, ky): raw values and the
+// weight exponents q' (log2 units) of the quadratic form; samples outside the frame get
+// q' = +inf.  kBorder selects the checked variant.
+template <bool kBorder>
+__device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int pitch, int h, int w, int kx, int ky,
+                                          const float (&Ax)[3], const float (&Ex)[3], const float (&Cy)[3],
+                                          const float (&dys)[3], float (&q)[3][3], float (&rv)[3][3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int yy = ky - 1 + j;
+        const bool yok = !kBorder || ((unsigned)yy < (unsigned)h);
+        const uint16_t *row = fr + (size_t)(kBorder ? clampi(yy, 0, h - 1) : yy) * pitch;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int xx = kx - 1 + i;
+            rv[j][i] = u16f(__ldg(row + (kBorder ? clampi(xx, 0, w - 1) : xx)));
+            const float qq = fmaf(Ex[i], dys[j], Ax[i] + Cy[j]);
+            if (kBorder) q[j][i] = (yok && (unsigned)xx < (unsigned)w) ? qq : INFINITY;
+            else q[j][i] = qq;
+        }
+    }
+}
+
+// SN/SD > 0: compile-time output scale SN/SD (constant divisors); 0: runtime snum/sden.
+template <bool kDen, int SN, int SD>
 __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__restrict__ burst,
                                                            const float2 *__restrict__ motion, Geom g,
                                                            const float4 *__restrict__ kern,
-                                                           const float *__restrict__ rhat_planes, int snum, int sden,
-                                                           int ho, int wo, float *__restrict__ rgb,
+                                                           const float *__restrict__ rhat_planes, int snum_rt,
+                                                           int sden_rt, int ho, int wo, float *__restrict__ rgb,
                                                            float *__restrict__ den_out) {
     const int X = blockIdx.x * kMergeW + threadIdx.x;
     const int Y = blockIdx.y * kMergeH + threadIdx.y;
     if (X >= wo || Y >= ho) return;
+    const int snum = SN > 0 ? SN : snum_rt, sden = SD > 0 ? SD : sden_rt;
     const int Q = 2 * snum, Q2 = 4 * snum;
     const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
     // output pixel centre x0 = Px / Q in raw px (exact rational)
     const int Px = 2 * sden * X + sden - snum, Py = 2 * sden * Y + sden - snum;
-    const int txi = clampi(floor_div(Px, Q * g.tile), 0, g.tx - 1);
-    const int tyi = clampi(floor_div(Py, Q * g.tile), 0, g.ty - 1);
+    const int txi = min(max(floor_div(Px, Q * g.tile), 0), g.tx - 1);
+    const int tyi = min(max(floor_div(Py, Q * g.tile), 0), g.ty - 1);
     const size_t hw = (size_t)g.hh * g.wh;
     // Rhat is sampled on the base half-res grid at (x0 - 1/2)/2 = (P - num) / 2Q
-    int rx = floor_div(Px - snum, Q2), ry = floor_div(Py - snum, Q2);
+    const int rx = floor_div(Px - snum, Q2), ry = floor_div(Py - snum, Q2);
     const float rfx = (float)(Px - snum - rx * Q2) * inv2Q, rfy = (float)(Py - snum - ry * Q2) * inv2Q;
     const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
     const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
+    const int r00 = ry0 * g.wh + rx0, r10 = ry0 * g.wh + rx1, r01 = ry1 * g.wh + rx0, r11 = ry1 * g.wh + rx1;
     const float rw00 = (1.f - rfx) * (1.f - rfy), rw10 = rfx * (1.f - rfy), rw01 = (1.f - rfx) * rfy, rw11 = rfx * rfy;
 
     float numR = 0.f, numG = 0.f, numB = 0.f, denR = 0.f, denG = 0.f, denB = 0.f;
@@ -276,10 +305,9 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         float vx = 0.f, vy = 0.f, rh = 1.f;
         if (f != g.ref) {
             const float *Rp = rhat_planes + (size_t)f * hw;
-            rh = rw00 * __ldg(Rp + (size_t)ry0 * g.wh + rx0) + rw10 * __ldg(Rp + (size_t)ry0 * g.wh + rx1) +
-                 rw01 * __ldg(Rp + (size_t)ry1 * g.wh + rx0) + rw11 * __ldg(Rp + (size_t)ry1 * g.wh + rx1);
+            rh = rw00 * __ldg(Rp + r00) + rw10 * __ldg(Rp + r10) + rw01 * __ldg(Rp + r01) + rw11 * __ldg(Rp + r11);
             if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
-            float2 mv = __ldg(motion + ((size_t)f * g.ty + tyi) * g.tx + txi);
+            const float2 mv = __ldg(motion + ((size_t)f * g.ty + tyi) * g.tx + txi);
             vx = mv.x;
             vy = mv.y;
         }
@@ -295,10 +323,10 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         const int ox = floor_div(gx, Q2), oy = floor_div(gy, Q2);
         const float ofx = ((float)(gx - ox * Q2) + zx) * inv2Q, ofy = ((float)(gy - oy * Q2) + zy) * inv2Q;
         const int ox0 = clampi(ox, 0, g.wh - 1), ox1 = clampi(ox + 1, 0, g.wh - 1);
-        const int oy0 = clampi(oy, 0, g.hh - 1), oy1 = clampi(oy + 1, 0, g.hh - 1);
+        const int oy0 = clampi(oy, 0, g.hh - 1) * g.wh, oy1 = clampi(oy + 1, 0, g.hh - 1) * g.wh;
         const float4 *K = kern + (size_t)f * hw;
-        const float4 t0 = __ldg(K + (size_t)oy0 * g.wh + ox0), t1 = __ldg(K + (size_t)oy0 * g.wh + ox1);
-        const float4 t2 = __ldg(K + (size_t)oy1 * g.wh + ox0), t3 = __ldg(K + (size_t)oy1 * g.wh + ox1);
+        const float4 t0 = __ldg(K + oy0 + ox0), t1 = __ldg(K + oy0 + ox1);
+        const float4 t2 = __ldg(K + oy1 + ox0), t3 = __ldg(K + oy1 + ox1);
         const float b0 = (1.f - ofx) * (1.f - ofy), b1 = ofx * (1.f - ofy), b2 = (1.f - ofx) * ofy, b3 = ofx * ofy;
         // Omega = a I + M, M = sum_k g_k u_k u_k^T;  adj(Omega) = a I + sum_k g_k u_k^perp u_k^perp^T
         const float a = b0 * t0.x + b1 * t1.x + b2 * t2.x + b3 * t3.x;
@@ -314,7 +342,7 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         const float detM = g0 * (g1 * c01 * c01 + g2 * c02 * c02 + g3 * c03 * c03) +
                            g1 * (g2 * c12 * c12 + g3 * c13 * c13) + g2 * g3 * c23 * c23;
         const float det = fmaf(a, a + Gs, detM);
-        const float sc = kHalfLog2e / det;
+        const float sc = __fdividef(kHalfLog2e, det);
         // q'(d) = (d^T adj(Omega) d) / det * log2(e)/2: weight = 2^-q'
         const float Bxx = (a + Nxx) * sc, Byy = (a + Nyy) * sc, Bxy2 = 2.f * Nxy * sc;
         const float dxs[3] = {dx0 - 1.f, dx0, dx0 + 1.f};
@@ -329,20 +357,10 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         // the 3x3 Bayer neighbourhood; samples outside the frame are left out
         const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
         float q[3][3], rv[3][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int yy = ky - 1 + j;
-            const bool yok = (yy >= 0) && (yy < g.h);
-            const uint16_t *row = fr + (size_t)clampi(yy, 0, g.h - 1) * g.pitch;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int xx = kx - 1 + i;
-                const bool ok = yok && (xx >= 0) && (xx < g.w);
-                rv[j][i] = (float)__ldg(row + clampi(xx, 0, g.w - 1));
-                const float qq = fmaf(Ex[i], dys[j], Ax[i] + Cy[j]);
-                q[j][i] = ok ? qq : INFINITY;
-            }
-        }
+        if ((unsigned)(kx - 1) < (unsigned)(g.w - 2) && (unsigned)(ky - 1) < (unsigned)(g.h - 2))
+            gather3x3<false>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
+        else
+            gather3x3<true>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
         // per-class minima: C = centre, H = (+-1, 0), V = (0, +-1), K = corners
         const float qC = q[1][1];
         const float mH = fminf(q[1][0], q[1][2]), mV = fminf(q[0][1], q[2][1]);
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         const float sC = cg ? mG : mS1, sK = cg ? mG : mS2, sH = cg ? mS1 : mG, sV = cg ? mS2 : mG;
         float w;
         w = fast_exp2(sC - q[1][1]);
-        float nC = w * rv[1][1], dC = w;
+        const float nC = w * rv[1][1], dC = w;
         w = fast_exp2(sH - q[1][0]);
         float nH = w * rv[1][0], dH = w;
         w = fast_exp2(sH - q[1][2]);
@@ -396,6 +414,20 @@ __global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__re
         den_out[po + o] = log2f(denG) - mG;
         den_out[2 * po + o] = log2f(denB) - mB;
     }
+}
+
+template <bool kDen>
+static void launch_k_merge(dim3 grid, cudaStream_t s, const uint16_t *burst, const float2 *mv, const Geom &g,
+                           const MergePlanes &P, int snum, int sden, int ho, int wo, float *rgb, float *den) {
+    const dim3 block(kMergeW, kMergeH);
+    if (snum == 1 && sden == 1)
+        k_merge<kDen, 1, 1><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
+    else if (snum == 3 && sden == 2)
+        k_merge<kDen, 3, 2><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
+    else if (snum == 2 && sden == 1)
+        k_merge<kDen, 2, 1><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
+    else
+        k_merge<kDen, 0, 0><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
 }
 
 // --------------------------------------------------------------------------------------
@@ -441,10 +473,9 @@ cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const
     dim3 grid(div_up(wo, kMergeW), div_up(ho, kMergeH));
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     if (den)
-        k_merge<true><<<grid, dim3(kMergeW, kMergeH), 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
+        launch_k_merge<true>(grid, s, burst, mv, g, P, snum, sden, ho, wo, rgb, den);
     else
-        k_merge<false><<<grid, dim3(kMergeW, kMergeH), 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb,
-                                                               nullptr);
+        launch_k_merge<false>(grid, s, burst, mv, g, P, snum, sden, ho, wo, rgb, nullptr);
     return cudaGetLastError();
 }
 

@@ -103,6 +103,8 @@ def test_align_ragged_sizes_and_ref(dev):
     check_align(b["raw"], dev, ref=2)
     check_align(b["raw"], dev, ref=0, tile=32, radius=(2, 3, 4, 4))
     check_align(b["raw"], dev, ref=1, tile=8, n_levels=2, lk_iters=5)
+    check_align(b["raw"], dev, ref=3, tile=64, n_levels=3, radius=(0, 7, 5, 4), lk_iters=1)
+    check_align(b["raw"], dev, ref=0, radius=(3, 6, 2, 0), lk_iters=0)
 
 
 # --------------------------------------------------------------------------------------
