@@ -119,6 +119,23 @@ hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_des
                                 const hmfsr_merge_params *params, float *omega_dev, float *rhat_dev,
                                 void *ws, size_t ws_bytes, void *stream);
 
+/* hmfsr_merge without a workspace argument, for callers that cannot allocate device
+ * memory where they merge (inside another framework's memory pool, on a real-time
+ * capture path where cudaMalloc could stall other streams, or behind a plugin interface
+ * that passes only input and output buffers).  The paper has no counterpart; this is a
+ * deployment convenience.  The call allocates nothing: its scratch is one fixed 32 MiB
+ * array inside the library (held by every GPU that loads the library, until the process
+ * exits).  Bursts whose merge needs more scratch than that, as hmfsr_workspace_size
+ * (HMFSR_OP_MERGE, ...) reports, are rejected with HMFSR_ERR_WORKSPACE before any launch
+ * (8 frames of 768 x 512 fit).  The first call on a device looks up the array's device
+ * address; make that first call before capturing a stream into a CUDA graph.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Arguments and results are otherwise those
+ * of hmfsr_merge. */
+hmfsr_status hmfsr_merge_static(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
+                                float *den_dev, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *hmfsr_status_string(hmfsr_status s);
 

@@ -237,3 +237,20 @@ def launches_per_call(n_frames: int, h: int, w: int, n_levels_max: int = 4) -> d
     """Kernel launches made by one hmfsr_align / hmfsr_merge_prepare / accumulate call."""
     nl = pyramid_levels(h, w, n_levels_max)
     return {"align": 1 + (nl - 1) + nl + 1, "merge_prepare": 4 + (n_frames - 1), "merge_accumulate": 1}
+
+
+def merge_static(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1),
+                 ref: int = 0, white_level: int = 4095, stream=None) -> torch.Tensor:
+    """`merge` through hmfsr_merge_static: the library's fixed in-module scratch instead
+    of a workspace (for callers that cannot allocate; small bursts only, and calls that
+    overlap on the GPU race)."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ho, wo = out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_static(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
+                                    _ptr(rgb), None, _stream(burst.device, stream)), "hmfsr_merge_static")
+    return rgb
