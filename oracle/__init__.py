@@ -78,8 +78,12 @@ def lib():
         L.orc_merge_pixels.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci, i32p, ci,
                                        f64p, ci]
         L.orc_align.argtypes = [u16p, ci, ci, ci, ci, ci, ci, i32p, ci, i32p, f64p, i32p, ci]
+        L.orc_merge_backward.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci, f64p, f64p, f64p, ci]
+        L.orc_merge_fingerprint.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci]
+        L.orc_merge_fingerprint.restype = ctypes.c_ulonglong
         for name in ("orc_luma", "orc_structure_tensor", "orc_kernel_from_tensor", "orc_omega_plane",
-                     "orc_tile_strength", "orc_robustness", "orc_merge_rows", "orc_merge_pixels", "orc_align"):
+                     "orc_tile_strength", "orc_robustness", "orc_merge_rows", "orc_merge_pixels", "orc_align",
+                     "orc_merge_backward"):
             getattr(L, name).restype = ci
         _lib = L
     return _lib
@@ -220,3 +224,35 @@ def align(burst, ref: int = 0, tile: int = 16, n_levels: int = 4, radius=(1, 4, 
                                 _ptr(rad, ctypes.c_int32), lk_iters, _ptr(mi, ctypes.c_int32),
                                 _ptr(mf, ctypes.c_double), _ptr(fl, ctypes.c_int32), n_threads), "align")
     return mi, mf, fl, nl
+
+
+PARAM_NAMES = ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink", "s2", "t")
+
+
+def merge_backward(burst, motion, params: MergeParams, grad_out, scale=(1, 1), ref: int = 0, tile: int = 16,
+                   wl: int = 4095, n_threads: int = 0):
+    """Oracle adjoint: (dL/dparams double [8] in PARAM_NAMES order, dL/dmotion double
+    [n, ty, tx, 2]) for the upstream gradient grad_out = dL/dC (double [3, Ho, Wo])."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    mv = np.ascontiguousarray(motion, dtype=np.float32)
+    ty, tx = n_tiles(h, w, tile)
+    g = np.ascontiguousarray(grad_out, dtype=np.float64)
+    gp = np.zeros(8, np.float64)
+    gm = np.zeros((n, ty, tx, 2), np.float64)
+    p = params.c()
+    _check(lib().orc_merge_backward(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
+                                    ctypes.byref(p), wl, scale[0], scale[1], _ptr(g, ctypes.c_double),
+                                    _ptr(gp, ctypes.c_double), _ptr(gm, ctypes.c_double), n_threads), "merge_backward")
+    return gp, gm
+
+
+def merge_fingerprint(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: int = 16,
+                      wl: int = 4095) -> int:
+    """Hash of every discrete decision of the merge (equal hashes: same branches)."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    mv = np.ascontiguousarray(motion, dtype=np.float32)
+    p = params.c()
+    return int(lib().orc_merge_fingerprint(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float),
+                                           tile, ctypes.byref(p), wl, scale[0], scale[1]))

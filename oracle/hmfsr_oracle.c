@@ -855,3 +855,350 @@ int orc_align(const uint16_t *burst, int n, int h, int w, int ref, int tile, int
     for (int l = 0; l < 4; ++l) free(ref_lv[l].px);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Adjoint of the merge (reverse mode of Eq. 1-9 and the supplement's heuristics)        */
+/* ------------------------------------------------------------------------------------ */
+/* Differentiable parameters, in this order: k_detail, k_denoise, D_th, D_tr, k_stretch,
+ * k_shrink, s (the robustness scale s2 of Eq. 8 used where the motion prior does not
+ * fire; s1 stays fixed) and t.  Discrete decisions (window centres, tiles, s1/s2
+ * selection, clamps, the 5x5 argmin, bilinear cells) carry no gradient: at such a point
+ * the one-sided derivatives differ and the value used is that of the branch taken.
+ *
+ * Kernel shape derivative: d Omega / d p = (d k_across / d p) e1 e1^T + (d k_along / d p) e2 e2^T. */
+static void kernel_param_grad(int64_t a, int64_t b, int64_t c, const orc_params *p, int wl, double dOm[6][3])
+{
+    double k[11];
+    kernel_from_tensor(a, b, c, p, wl, k);
+    double A = k[5], cs = k[9], sn = k[10];
+    double l1 = k[3];
+    double rl = sqrt(l1 / (4.0 * (8.0 * wl) * (8.0 * wl)));
+    double Draw = 1.0 - rl / p->d_tr + p->d_th;
+    double D = clampd(Draw, 0.0, 1.0);
+    int inside = Draw > 0.0 && Draw < 1.0;
+    double dD2 = inside ? 1.0 : 0.0, dD3 = inside ? rl / (p->d_tr * p->d_tr) : 0.0;
+    double kh_al = p->k_detail * p->k_stretch * A, kh_ac = p->k_detail / (p->k_shrink * A);
+    double kd = p->k_detail * p->k_denoise;
+    double s_al = (1.0 - D) * kh_al + D * kd, s_ac = (1.0 - D) * kh_ac + D * kd;
+    double ds_al[6] = { (1.0 - D) * p->k_stretch * A + D * p->k_denoise, D * p->k_detail,
+                        (kd - kh_al) * dD2, (kd - kh_al) * dD3, (1.0 - D) * p->k_detail * A, 0.0 };
+    double ds_ac[6] = { (1.0 - D) / (p->k_shrink * A) + D * p->k_denoise, D * p->k_detail,
+                        (kd - kh_ac) * dD2, (kd - kh_ac) * dD3, 0.0,
+                        -(1.0 - D) * p->k_detail / (p->k_shrink * p->k_shrink * A) };
+    double e1xx = 0.5 * (1.0 + cs), e1xy = 0.5 * sn, e1yy = 0.5 * (1.0 - cs);
+    for (int q = 0; q < 6; ++q) {
+        double dal = 2.0 * s_al * ds_al[q], dac = 2.0 * s_ac * ds_ac[q];
+        dOm[q][0] = dac * e1xx + dal * (1.0 - e1xx);
+        dOm[q][1] = dac * e1xy - dal * e1xy;
+        dOm[q][2] = dac * e1yy + dal * (1.0 - e1yy);
+    }
+}
+
+/* Robustness R at base half-res (u,v) for frame `alt` with its partial derivatives:
+ * dR[0] = dR/dvx, dR[1] = dR/dvy (the tile's vector), dR[2] = dR/ds2, dR[3] = dR/dt.
+ * Same arithmetic as robustness_at. */
+static double robustness_grad_at(const uint16_t *base, const uint16_t *alt, const float *motion_alt,
+                                 const double *s_tile, const rob_geom *g, int u, int v, double dR[4])
+{
+    const orc_params *p = g->p;
+    int tyi = clampi((2 * v) / g->tile, 0, g->ty - 1);
+    int txi = clampi((2 * u) / g->tile, 0, g->tx - 1);
+    const float *mv = motion_alt + ((size_t)tyi * g->tx + txi) * 2;
+    double fx = (double)u + 0.5 * (double)mv[0];
+    double fy = (double)v + 0.5 * (double)mv[1];
+    double x0 = floor(fx), y0 = floor(fy);
+    double ax = fx - x0, ay = fy - y0;
+    int ix = (int)x0, iy = (int)y0;
+    double dd = 0.0, ss = 0.0, ddd_dvx = 0.0, ddd_dvy = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double s1 = (double)box_sum(base, g->h, g->w, u, v, c, 0);
+        double s2 = (double)box_sum(base, g->h, g->w, u, v, c, 1);
+        double gs = (c == 1) ? 2.0 : 1.0;
+        double mu = s1 / (9.0 * gs);
+        double var_ms = (9.0 * s2 - s1 * s1) / (81.0 * gs * gs);
+        if (var_ms < 0.0) var_ms = 0.0;
+        double sigma_ms = sqrt(var_ms);
+        double m00 = box_mean(alt, g->h, g->w, ix, iy, c), m10 = box_mean(alt, g->h, g->w, ix + 1, iy, c);
+        double m01 = box_mean(alt, g->h, g->w, ix, iy + 1, c), m11 = box_mean(alt, g->h, g->w, ix + 1, iy + 1, c);
+        double mu_n = (1.0 - ay) * ((1.0 - ax) * m00 + ax * m10) + ay * ((1.0 - ax) * m01 + ax * m11);
+        double dmu_dfx = (1.0 - ay) * (m10 - m00) + ay * (m11 - m01);
+        double dmu_dfy = (1.0 - ax) * (m01 - m00) + ax * (m11 - m10);
+        double d_ms = mu - mu_n;
+        double var_md = (p->noise_a * clampd(mu, 0.0, (double)g->wl) + p->noise_b) / gs;
+        if (var_md < 0.0) var_md = 0.0;
+        double sigma_md = sqrt(var_md);
+        double m = 2.0 * var_md / 9.0;
+        double sigma = sigma_ms > sigma_md ? sigma_ms : sigma_md;
+        double den = d_ms * d_ms + m;
+        double d = den > 0.0 ? d_ms * (d_ms * d_ms) / den : 0.0;
+        double dd_dms = den > 0.0 ? (d_ms * d_ms * d_ms * d_ms + 3.0 * m * d_ms * d_ms) / (den * den) : 0.0;
+        dd += d * d;
+        ss += sigma * sigma;
+        /* d(d^2)/d v = 2 d dd/dd_ms * (-dmu_n/dpos) * 1/2 */
+        ddd_dvx += 2.0 * d * dd_dms * (-dmu_dfx) * 0.5;
+        ddd_dvy += 2.0 * d * dd_dms * (-dmu_dfy) * 0.5;
+    }
+    double eps = 1e-12 * (double)g->wl * (double)g->wl;
+    double S = ss > eps ? ss : eps;
+    double ratio = dd / S;
+    double s = s_tile[(size_t)tyi * g->tx + txi];
+    double e = exp(-ratio);
+    double raw = s * e - p->t;
+    double R = clampd(raw, 0.0, 1.0);
+    if (raw > 0.0 && raw < 1.0) {
+        dR[0] = -s * e * ddd_dvx / S;
+        dR[1] = -s * e * ddd_dvy / S;
+        dR[2] = (tile_M(motion_alt, g->ty, g->tx, tyi, txi) > p->m_th) ? 0.0 : e;   /* s = s2 here */
+        dR[3] = -1.0;
+    } else {
+        dR[0] = dR[1] = dR[2] = dR[3] = 0.0;
+    }
+    return R;
+}
+
+int orc_merge_backward(const uint16_t *burst, int n, int h, int w, int ref, const float *motion, int tile,
+                       const orc_params *p, int wl, int snum, int sden, const double *grad_out,
+                       double *grad_params, double *grad_motion, int n_threads)
+{
+    if (!grad_out || !grad_params || !grad_motion || snum < 1 || sden < 1) return -1;
+    set_threads(n_threads);
+    merge_ctx m;
+    int rc = init_ctx(&m, burst, n, h, w, ref, motion, tile, p, wl);
+    int ho = (int)(((long long)h * snum) / sden), wo = (int)(((long long)w * snum) / sden);
+    if (rc == 0) rc = precompute_rows(&m, snum, sden, 0, ho);
+    if (rc != 0) { free_ctx(&m); return rc; }
+    const int hh = h / 2, wh = w / 2;
+    const size_t hw = (size_t)hh * wh;
+    rob_geom g = { h, w, tile, m.ty, m.tx, wl, p };
+    /* per-frame accumulators: Omega-bar per texel, Rhat-bar per base texel */
+    double *om_bar = (double *)calloc((size_t)n * 3 * hw, sizeof(double));
+    double *rh_bar = (double *)calloc((size_t)n * hw, sizeof(double));
+    memset(grad_params, 0, 8 * sizeof(double));
+    memset(grad_motion, 0, sizeof(double) * (size_t)n * m.ty * m.tx * 2);
+    if (!om_bar || !rh_bar) { free(om_bar); free(rh_bar); free_ctx(&m); return -2; }
+    const long long Q = 2LL * snum;
+    for (int Y = 0; Y < ho; ++Y)
+        for (int X = 0; X < wo; ++X) {
+            double C[3], den[3];
+            merge_pixel(&m, snum, sden, X, Y, C, den);
+            const long long Px = 2LL * sden * X + sden - snum, Py = 2LL * sden * Y + sden - snum;
+            const double x0 = (double)Px / (double)Q, y0 = (double)Py / (double)Q;
+            int txi = clampi((int)floor_div(Px, Q * tile), 0, m.tx - 1);
+            int tyi = clampi((int)floor_div(Py, Q * tile), 0, m.ty - 1);
+            double gc[3];
+            for (int c = 0; c < 3; ++c) gc[c] = grad_out[(size_t)c * ho * wo + (size_t)Y * wo + X];
+            for (int f = 0; f < n; ++f) {
+                double vx = 0.0, vy = 0.0;
+                if (f != ref) {
+                    const float *mv = motion_ptr(&m, f) + ((size_t)tyi * m.tx + txi) * 2;
+                    vx = (double)mv[0];
+                    vy = (double)mv[1];
+                }
+                long long kx = floor_div(Px + Q / 2 + (long long)floor((double)Q * vx), Q);
+                long long ky = floor_div(Py + Q / 2 + (long long)floor((double)Q * vy), Q);
+                double px = x0 + vx, py = y0 + vy;
+                double hx = (px - 0.5) / 2.0, hy = (py - 0.5) / 2.0;
+                double fx0 = floor(hx), fy0 = floor(hy);
+                double ax = hx - fx0, ay = hy - fy0;
+                int ix = (int)fx0, iy = (int)fy0;
+                int tx_[4] = { clampi(ix, 0, wh - 1), clampi(ix + 1, 0, wh - 1), clampi(ix, 0, wh - 1), clampi(ix + 1, 0, wh - 1) };
+                int ty_[4] = { clampi(iy, 0, hh - 1), clampi(iy, 0, hh - 1), clampi(iy + 1, 0, hh - 1), clampi(iy + 1, 0, hh - 1) };
+                double beta[4] = { (1 - ax) * (1 - ay), ax * (1 - ay), (1 - ax) * ay, ax * ay };
+                double dbx[4] = { -(1 - ay), (1 - ay), -ay, ay };     /* d beta / d ax */
+                double dby[4] = { -(1 - ax), -ax, (1 - ax), ax };     /* d beta / d ay */
+                double ok[4][3], om[3] = { 0, 0, 0 };
+                for (int k = 0; k < 4; ++k) {
+                    omega_get(&m, f, tx_[k], ty_[k], ok[k]);
+                    for (int e = 0; e < 3; ++e) om[e] += beta[k] * ok[k][e];
+                }
+                double det = om[0] * om[2] - om[1] * om[1];
+                double ixx = om[2] / det, ixy = -om[1] / det, iyy = om[0] / det;
+                double rhat = 1.0, gam[4] = { 0, 0, 0, 0 };
+                int gx_[4] = { 0, 0, 0, 0 }, gy_[4] = { 0, 0, 0, 0 };
+                if (f != ref) {
+                    double gx = (x0 - 0.5) / 2.0, gy = (y0 - 0.5) / 2.0;
+                    double gx0 = floor(gx), gy0 = floor(gy);
+                    double bx = gx - gx0, by = gy - gy0;
+                    int jx = (int)gx0, jy = (int)gy0;
+                    gx_[0] = clampi(jx, 0, wh - 1); gx_[1] = clampi(jx + 1, 0, wh - 1); gx_[2] = gx_[0]; gx_[3] = gx_[1];
+                    gy_[0] = clampi(jy, 0, hh - 1); gy_[1] = gy_[0]; gy_[2] = clampi(jy + 1, 0, hh - 1); gy_[3] = gy_[2];
+                    gam[0] = (1 - bx) * (1 - by); gam[1] = bx * (1 - by); gam[2] = (1 - bx) * by; gam[3] = bx * by;
+                    rhat = 0.0;
+                    for (int k = 0; k < 4; ++k) rhat += gam[k] * rhat_get(&m, f, gx_[k], gy_[k]);
+                }
+                const uint16_t *fr = frame_ptr(&m, f);
+                double om_b[3] = { 0, 0, 0 }, v_b[2] = { 0, 0 }, rh_b = 0.0;
+                for (int j = -1; j <= 1; ++j)
+                    for (int i = -1; i <= 1; ++i) {
+                        long long qx = kx + i, qy = ky + j;
+                        if (qx < 0 || qx >= w || qy < 0 || qy >= h) continue;
+                        double dx = (double)qx - px, dy = (double)qy - py;
+                        double Pxv = ixx * dx + ixy * dy, Pyv = ixy * dx + iyy * dy;   /* Omega^-1 d */
+                        double qf = dx * Pxv + dy * Pyv;
+                        double wgt = exp(-0.5 * qf);
+                        int c = cfa_channel((int)qx, (int)qy);
+                        double cval = (double)fr[(size_t)qy * w + qx];
+                        double gwr = gc[c] * (cval - C[c]) / den[c];   /* dL / d(w Rhat) */
+                        rh_b += gwr * wgt;
+                        double q_b = gwr * rhat * (-0.5 * wgt);           /* dL / dq */
+                        /* q = d^T Omega^-1 d: dq/dd = 2 Omega^-1 d, dq/dv = -dq/dd */
+                        v_b[0] += -2.0 * q_b * Pxv;
+                        v_b[1] += -2.0 * q_b * Pyv;
+                        /* dq/dOmega = -(Omega^-1 d)(Omega^-1 d)^T; Oxy counted twice */
+                        om_b[0] += -q_b * Pxv * Pxv;
+                        om_b[1] += -2.0 * q_b * Pxv * Pyv;
+                        om_b[2] += -q_b * Pyv * Pyv;
+                    }
+                /* Omega position: h = (x0 + v - 1/2)/2, so d(ax)/d(vx) = 1/2 */
+                for (int k = 0; k < 4; ++k) {
+                    double dot = om_b[0] * ok[k][0] + om_b[1] * ok[k][1] + om_b[2] * ok[k][2];
+                    v_b[0] += 0.5 * dbx[k] * dot;
+                    v_b[1] += 0.5 * dby[k] * dot;
+                    for (int e = 0; e < 3; ++e)
+                        om_bar[((size_t)f * 3 + e) * hw + (size_t)ty_[k] * wh + tx_[k]] += beta[k] * om_b[e];
+                }
+                if (f != ref) {
+                    double *gm = grad_motion + ((size_t)f * m.ty * m.tx + (size_t)tyi * m.tx + txi) * 2;
+                    gm[0] += v_b[0];
+                    gm[1] += v_b[1];
+                    for (int k = 0; k < 4; ++k) rh_bar[(size_t)f * hw + (size_t)gy_[k] * wh + gx_[k]] += gam[k] * rh_b;
+                }
+            }
+        }
+    /* texels: Omega-bar -> kernel parameters */
+    for (int f = 0; f < n; ++f)
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double ob[3];
+                for (int e = 0; e < 3; ++e) ob[e] = om_bar[((size_t)f * 3 + e) * hw + (size_t)v * wh + u];
+                if (ob[0] == 0.0 && ob[1] == 0.0 && ob[2] == 0.0) continue;
+                int64_t a, b, c;
+                tensor_at(frame_ptr(&m, f), h, w, u, v, &a, &b, &c);
+                double dOm[6][3];
+                kernel_param_grad(a, b, c, p, wl, dOm);
+                for (int q = 0; q < 6; ++q) grad_params[q] += ob[0] * dOm[q][0] + ob[1] * dOm[q][1] + ob[2] * dOm[q][2];
+            }
+    /* Rhat-bar -> argmin R -> s, t and the motion of the R pixel's tile */
+    double *Rpl = (double *)malloc(sizeof(double) * hw);
+    double *dRpl = (double *)malloc(sizeof(double) * hw * 4);
+    double *Rbar = (double *)malloc(sizeof(double) * hw);
+    if (!Rpl || !dRpl || !Rbar) { free(Rpl); free(dRpl); free(Rbar); free(om_bar); free(rh_bar); free_ctx(&m); return -2; }
+    for (int f = 0; f < n; ++f) {
+        if (f == ref) continue;
+        const uint16_t *base = frame_ptr(&m, ref), *alt = frame_ptr(&m, f);
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u)
+                Rpl[(size_t)v * wh + u] = robustness_grad_at(base, alt, motion_ptr(&m, f), m.s_tile[f], &g, u, v,
+                                                             &dRpl[((size_t)v * wh + u) * 4]);
+        memset(Rbar, 0, sizeof(double) * hw);
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double rb = rh_bar[(size_t)f * hw + (size_t)v * wh + u];
+                if (rb == 0.0) continue;
+                /* first minimum of the 5x5 window in scan order */
+                double best = INFINITY;
+                int bu = u, bv = v;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int uu = u + i, vv = v + j;
+                        if (uu < 0 || uu >= wh || vv < 0 || vv >= hh) continue;
+                        double r = Rpl[(size_t)vv * wh + uu];
+                        if (r < best) { best = r; bu = uu; bv = vv; }
+                    }
+                Rbar[(size_t)bv * wh + bu] += rb;
+            }
+        const float *mva = motion_ptr(&m, f);
+        (void)mva;
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double rb = Rbar[(size_t)v * wh + u];
+                if (rb == 0.0) continue;
+                const double *dR = &dRpl[((size_t)v * wh + u) * 4];
+                int tyi = clampi((2 * v) / tile, 0, m.ty - 1), txi = clampi((2 * u) / tile, 0, m.tx - 1);
+                double *gm = grad_motion + ((size_t)f * m.ty * m.tx + (size_t)tyi * m.tx + txi) * 2;
+                gm[0] += rb * dR[0];
+                gm[1] += rb * dR[1];
+                grad_params[6] += rb * dR[2];
+                grad_params[7] += rb * dR[3];
+            }
+    }
+    free(Rpl); free(dRpl); free(Rbar); free(om_bar); free(rh_bar);
+    free_ctx(&m);
+    return 0;
+}
+
+/* A fingerprint of every discrete decision of the merge at these arguments (window
+ * centres, motion-prior selections, clamp states of D and R, 5x5 argmins).  Finite
+ * differences are only meaningful between points with equal fingerprints. */
+unsigned long long orc_merge_fingerprint(const uint16_t *burst, int n, int h, int w, int ref, const float *motion,
+                                         int tile, const orc_params *p, int wl, int snum, int sden)
+{
+    merge_ctx m;
+    if (init_ctx(&m, burst, n, h, w, ref, motion, tile, p, wl) != 0) { free_ctx(&m); return 0; }
+    unsigned long long hsh = 1469598103934665603ULL;
+#define MIX(x) do { hsh ^= (unsigned long long)(x); hsh *= 1099511628211ULL; } while (0)
+    int ho = (int)(((long long)h * snum) / sden), wo = (int)(((long long)w * snum) / sden);
+    const long long Q = 2LL * snum;
+    const int hh = h / 2, wh = w / 2;
+    for (int Y = 0; Y < ho; ++Y)
+        for (int X = 0; X < wo; ++X) {
+            const long long Px = 2LL * sden * X + sden - snum, Py = 2LL * sden * Y + sden - snum;
+            int txi = clampi((int)floor_div(Px, Q * tile), 0, m.tx - 1);
+            int tyi = clampi((int)floor_div(Py, Q * tile), 0, m.ty - 1);
+            for (int f = 0; f < n; ++f) {
+                double vx = 0.0, vy = 0.0;
+                if (f != ref) {
+                    const float *mv = motion_ptr(&m, f) + ((size_t)tyi * m.tx + txi) * 2;
+                    vx = mv[0]; vy = mv[1];
+                }
+                MIX(floor_div(Px + Q / 2 + (long long)floor((double)Q * vx), Q));
+                MIX(floor_div(Py + Q / 2 + (long long)floor((double)Q * vy), Q));
+                MIX((long long)floor(((double)Px / Q + vx - 0.5) / 2.0));
+                MIX((long long)floor(((double)Py / Q + vy - 0.5) / 2.0));
+            }
+        }
+    rob_geom g = { h, w, tile, m.ty, m.tx, wl, p };
+    double *Rpl = (double *)malloc(sizeof(double) * (size_t)hh * wh);
+    for (int f = 0; f < n && Rpl; ++f) {
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                int64_t a, b, c;
+                double k[11];
+                tensor_at(frame_ptr(&m, f), h, w, u, v, &a, &b, &c);
+                kernel_from_tensor(a, b, c, p, wl, k);
+                double rl = sqrt(k[3] / (4.0 * (8.0 * wl) * (8.0 * wl)));
+                double Draw = 1.0 - rl / p->d_tr + p->d_th;
+                MIX(Draw <= 0.0 ? 0 : (Draw >= 1.0 ? 2 : 1));
+            }
+        if (f == ref) continue;
+        for (int t = 0; t < m.ty * m.tx; ++t) MIX(m.s_tile[f][t] == p->s1);
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double dR[4];
+                Rpl[(size_t)v * wh + u] = robustness_grad_at(frame_ptr(&m, ref), frame_ptr(&m, f), motion_ptr(&m, f),
+                                                             m.s_tile[f], &g, u, v, dR);
+                MIX(dR[3] != 0.0);
+                int tyi = clampi((2 * v) / tile, 0, m.ty - 1), txi = clampi((2 * u) / tile, 0, m.tx - 1);
+                const float *mv = motion_ptr(&m, f) + ((size_t)tyi * m.tx + txi) * 2;
+                MIX((long long)floor(u + 0.5 * mv[0]));
+                MIX((long long)floor(v + 0.5 * mv[1]));
+            }
+        for (int v = 0; v < hh; ++v)
+            for (int u = 0; u < wh; ++u) {
+                double best = INFINITY;
+                int bi = 0;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int uu = u + i, vv = v + j;
+                        if (uu < 0 || uu >= wh || vv < 0 || vv >= hh) continue;
+                        double r = Rpl[(size_t)vv * wh + uu];
+                        if (r < best) { best = r; bi = (j + 2) * 5 + i + 2; }
+                    }
+                MIX(bi);
+            }
+    }
+#undef MIX
+    free(Rpl);
+    free_ctx(&m);
+    return hsh;
+}

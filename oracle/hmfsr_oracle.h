@@ -78,6 +78,17 @@ int orc_align(const uint16_t *burst, int n, int h, int w, int ref, int tile, int
               const int *radius, int lk_iters, int32_t *motion_int, double *motion,
               int32_t *lk_flags, int n_threads);
 
+/* Adjoint of the merge: given dL/dC (double [3][ho][wo]) returns dL/dparams (double [8]:
+ * k_detail, k_denoise, d_th, d_tr, k_stretch, k_shrink, s2, t) and dL/dmotion (double
+ * [n][ty][tx][2]; zero for the base frame). */
+int orc_merge_backward(const uint16_t *burst, int n, int h, int w, int ref, const float *motion, int tile,
+                       const orc_params *p, int wl, int snum, int sden, const double *grad_out,
+                       double *grad_params, double *grad_motion, int n_threads);
+
+/* Fingerprint of the discrete decisions of the merge (for finite-difference checks). */
+unsigned long long orc_merge_fingerprint(const uint16_t *burst, int n, int h, int w, int ref, const float *motion,
+                                         int tile, const orc_params *p, int wl, int snum, int sden);
+
 #ifdef __cplusplus
 }
 #endif
