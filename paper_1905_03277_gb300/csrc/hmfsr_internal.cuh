@@ -34,6 +34,13 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// sqrt on the SFU (sqrt.approx, flush-to-zero): relative error ~2^-23.
+__device__ __forceinline__ float fast_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------------------
 // geometry of one burst
 // ---------------------------------------------------------------------------------------
@@ -78,5 +85,25 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
                                int snum, int sden, float *rgb, float *den, cudaStream_t s);
 cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *omega, float *rhat, cudaStream_t s);
+
+// adjoint of the merge: buffers beyond the forward planes
+struct BwdPlanes {
+    float4 *shape;          // [n][hh*wh] {A, sqrt(l1_norm), cos 2t, sin 2t}
+    float4 *rb;             // [n][hh*wh] {R, dR/dvx, dR/dvy, dR/ds2}
+    unsigned char *flags;   // [n][hh*wh] bit 7: R unclamped; bits 0-4: argmin of the 5x5 window
+    float *rhbar_tex;       // [n][hh*wh] dL/dRhat on base texels
+    float2 *vbar_tex;       // [n][hh*wh] motion contributions through R
+    float2 *vbar_pix;       // [n][ho*wo] motion contributions through the weights
+    float *rhbar_pix;       // [n][ho*wo] dL/dRhat at output pixels
+    double *part6;          // [n_bwd_blocks][6] kernel-parameter partial sums
+    double *part2;          // [n_rp_blocks][2] (s2, t) partial sums
+    unsigned char *sel;     // [n][ty*tx] 1 where the motion prior chose s2
+    int n_bwd_blocks, n_rp_blocks;
+};
+size_t carve_backward(void *ws, const Geom &g, int ho, int wo, size_t fwd_bytes, BwdPlanes *B);
+cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                                  const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
+                                  const float *lden, const float *grad_rgb, float *grad_params, float *grad_motion,
+                                  cudaStream_t s);
 
 }  // namespace hmfsr

@@ -64,13 +64,14 @@ __global__ void k_box(const ushort4 *__restrict__ guide, int hh, int wh, int ref
     float sig2 = 0.f, dmd2[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        float gs = (ch == 1) ? 2.f : 1.f;  // green guide = (G1 + G2) / 2
+        // green guide = (G1 + G2) / 2
         long long num = 9LL * (long long)S2[ch] - (long long)S1[ch] * (long long)S1[ch];
-        float var_ms = fmaxf((float)num / (81.f * gs * gs), 0.f);
-        float mu = (float)S1[ch] / (9.f * gs);
-        float var_md = fmaxf((c.noise_a * fminf(fmaxf(mu, 0.f), (float)wl) + c.noise_b) / gs, 0.f);
+        const float igs = (ch == 1) ? 0.5f : 1.f;
+        float var_ms = fmaxf((float)num * (igs * igs * (1.f / 81.f)), 0.f);
+        float mu = (float)S1[ch] * (igs * (1.f / 9.f));
+        float var_md = fmaxf((c.noise_a * fminf(fmaxf(mu, 0.f), (float)wl) + c.noise_b) * igs, 0.f);
         sig2 += fmaxf(var_ms, var_md);
-        dmd2[ch] = 2.f * var_md / 9.f;
+        dmd2[ch] = var_md * (2.f / 9.f);
     }
     float eps = 1e-12f * (float)wl * (float)wl;
     base_stats[idx] = make_float4(fmaxf(sig2, eps), dmd2[0], dmd2[1], dmd2[2]);
@@ -111,23 +112,23 @@ __global__ void k_cov(const ushort4 *__restrict__ guide, int hh, int wh, MergeCo
     // cos 2theta = (a-c)/r, sin 2theta = 2b/r (theta = 0 when the tensor is isotropic)
     float tr = (float)(ta + tc);
     float amc = (float)(ta - tc), b2 = 2.f * (float)tb;
-    float r = sqrtf(amc * amc + b2 * b2);
+    float r = fast_sqrt(amc * amc + b2 * b2);
     float cs = 1.f, sn = 0.f;
-    if (!(ta == tc && tb == 0)) { cs = amc / r; sn = b2 / r; }
+    if (!(ta == tc && tb == 0)) { const float ir = __fdividef(1.f, r); cs = amc * ir; sn = b2 * ir; }
     float l1 = 0.5f * (tr + r);
-    float A = (ta + tc == 0) ? 1.f : 1.f + sqrtf(r / tr);
+    float A = (ta + tc == 0) ? 1.f : 1.f + fast_sqrt(__fdividef(r, tr));
     // lambda in units of luminance normalised to [0,1]: sqrt(l1_norm) = sqrt(l1) / (16 WL)
-    float D = fminf(fmaxf(1.f - (sqrtf(l1) / (16.f * (float)wl)) / c.d_tr + c.d_th, 0.f), 1.f);
+    float D = fminf(fmaxf(1.f - fast_sqrt(l1) * __fdividef(1.f, 16.f * (float)wl * c.d_tr) + c.d_th, 0.f), 1.f);
     float kh_al = c.k_detail * (c.k_stretch * A);
-    float kh_ac = c.k_detail / (c.k_shrink * A);
+    float kh_ac = __fdividef(c.k_detail, c.k_shrink * A);
     float kd = c.k_detail * c.k_denoise;
     float s_al = (1.f - D) * kh_al + D * kd;   // standard deviations before squaring
     float s_ac = (1.f - D) * kh_ac + D * kd;
     float k_al = s_al * s_al, k_ac = s_ac * s_ac;
     // half-angle unit vector e1 = (cos theta, sin theta), without cancellation
     float e1x, e1y;
-    if (cs >= 0.f) { e1x = sqrtf(0.5f * (1.f + cs)); e1y = sn / (2.f * e1x); }
-    else { e1y = sqrtf(0.5f * (1.f - cs)); e1x = sn / (2.f * e1y); }
+    if (cs >= 0.f) { e1x = fast_sqrt(0.5f * (1.f + cs)); e1y = __fdividef(sn, 2.f * e1x); }
+    else { e1y = fast_sqrt(0.5f * (1.f - cs)); e1x = __fdividef(sn, 2.f * e1y); }
     // Omega = k_across e1 e1^T + k_along e2 e2^T (stretch along the edge, e2)
     //       = min I + |k_along - k_across| u u^T with u = e2 if k_along >= k_across else e1
     float dh = (1.f - D) * (kh_al - kh_ac) * (s_al + s_ac);  // k_along - k_across, no cancellation
@@ -211,20 +212,20 @@ __global__ void __launch_bounds__(kRobW *kRobH) k_rob(const uint2 *__restrict__ 
             float dd = 0.f;
             {
                 float d2 = dR * dR, den = d2 + st.y;
-                float d = den > 0.f ? dR * d2 / den : 0.f;  // Wiener shrinkage (Eq. 6)
+                float d = den > 0.f ? __fdividef(dR * d2, den) : 0.f;  // Wiener shrinkage (Eq. 6)
                 dd += d * d;
             }
             {
                 float d2 = dG * dG, den = d2 + st.z;
-                float d = den > 0.f ? dG * d2 / den : 0.f;
+                float d = den > 0.f ? __fdividef(dG * d2, den) : 0.f;
                 dd += d * d;
             }
             {
                 float d2 = dB * dB, den = d2 + st.w;
-                float d = den > 0.f ? dB * d2 / den : 0.f;
+                float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
                 dd += d * d;
             }
-            R = fminf(fmaxf(s * expf(-dd / st.x) - t_thr, 0.f), 1.f);  // Eq. 5
+            R = fminf(fmaxf(s * expf(-__fdividef(dd, st.x)) - t_thr, 0.f), 1.f);  // Eq. 5
         }
         Rs[ly][lx] = R;
     }
@@ -272,7 +273,7 @@ __device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int p
 
 // SN/SD > 0: compile-time output scale SN/SD (constant divisors); 0: runtime snum/sden.
 template <bool kDen, int SN, int SD>
-__global__ void __launch_bounds__(kMergeW *kMergeH) k_merge(const uint16_t *__restrict__ burst,
+__global__ void __launch_bounds__(kMergeW *kMergeH, 8) k_merge(const uint16_t *__restrict__ burst,
                                                            const float2 *__restrict__ motion, Geom g,
                                                            const float4 *__restrict__ kern,
                                                            const float *__restrict__ rhat_planes, int snum_rt,
