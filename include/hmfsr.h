@@ -72,7 +72,7 @@ typedef struct {
     int tile;                       /* raw px of the motion field's tiles: 8, 16, 32, 64 */
 } hmfsr_merge_params;
 
-enum { HMFSR_OP_ALIGN = 0, HMFSR_OP_MERGE = 1, HMFSR_OP_MERGE_STAGES = 2 };
+enum { HMFSR_OP_ALIGN = 0, HMFSR_OP_MERGE = 1, HMFSR_OP_MERGE_STAGES = 2, HMFSR_OP_MERGE_BACKWARD = 3 };
 
 /* Bytes of scratch the op needs for this burst (0 on invalid arguments).  For
  * HMFSR_OP_ALIGN, `tile` is the alignment tile; scale_num/scale_den are ignored.  For the
@@ -118,6 +118,23 @@ hmfsr_status hmfsr_merge_accumulate(const uint16_t *burst_dev, const hmfsr_burst
 hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
                                 const hmfsr_merge_params *params, float *omega_dev, float *rhat_dev,
                                 void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint of hmfsr_merge (reverse mode of Eq. 1-9 and the supplement's heuristics S.1)
+ * for fitting the tuning parameters and the motion by gradient descent.  Given the
+ * forward's outputs rgb_dev and den_dev (hmfsr_merge with den_dev, same arguments) and
+ * grad_rgb_dev = dL/drgb (float32 [3][Ho][Wo]), writes
+ *   grad_params_dev  float32 [8]: dL/d{k_detail, k_denoise, d_th, d_tr, k_stretch,
+ *                    k_shrink, s2, t} (s2 is the robustness scale of Eq. 8 where the
+ *                    motion prior does not fire; s1 is not differentiated);
+ *   grad_motion_dev  float32 [n_frames][TY][TX][2]: dL/dmotion (0 for the base frame).
+ * Discrete decisions (window centres, tiles, s1/s2 selection, clamps, the 5x5 argmin)
+ * carry no gradient.  The forward is recomputed from the burst; the reduction order is
+ * fixed, so results are deterministic.  Workspace: HMFSR_OP_MERGE_BACKWARD. */
+hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                  const hmfsr_merge_params *params, int scale_num, int scale_den,
+                                  const float *rgb_dev, const float *den_dev, const float *grad_rgb_dev,
+                                  float *grad_params_dev, float *grad_motion_dev, void *ws, size_t ws_bytes,
+                                  void *stream);
 
 /* hmfsr_merge without a workspace argument, for callers that cannot allocate device
  * memory where they merge (inside another framework's memory pool, on a real-time

@@ -254,3 +254,51 @@ def merge_static(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams 
     _lib.check(L.hmfsr_merge_static(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
                                     _ptr(rgb), None, _stream(burst.device, stream)), "hmfsr_merge_static")
     return rgb
+
+
+PARAM_NAMES = ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink", "s2", "t")
+
+
+def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams, rgb: torch.Tensor,
+                   den: torch.Tensor, grad_rgb: torch.Tensor, scale=(1, 1), ref: int = 0, white_level: int = 4095,
+                   stream=None):
+    """Adjoint of `merge` (hmfsr_merge_backward): (dL/dparams float32 [8] in PARAM_NAMES
+    order, dL/dmotion float32 [n, TY, TX, 2]) for grad_rgb = dL/drgb, given the forward's
+    rgb and den (merge(..., with_den=True))."""
+    L = _lib.load()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ty, tx = n_tiles(h, w, params.tile)
+    gp = torch.empty(8, dtype=torch.float32, device=burst.device)
+    gm = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
+    grad_rgb = grad_rgb.contiguous().float()
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_BACKWARD, ctypes.byref(d), params.tile, scale[0], scale[1])
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_backward(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0],
+                                      scale[1], _ptr(rgb), _ptr(den), _ptr(grad_rgb), _ptr(gp), _ptr(gm), _ptr(ws),
+                                      ws.numel(), _stream(burst.device, stream)), "hmfsr_merge_backward")
+    return gp, gm
+
+
+class MergeFn(torch.autograd.Function):
+    """rgb = merge(burst, motion, params) as a differentiable function of the eight tuning
+    parameters (a float tensor in PARAM_NAMES order) and of the motion field; gradients
+    come from the hand-written adjoint (hmfsr_merge_backward)."""
+
+    @staticmethod
+    def forward(ctx, theta, motion, burst, base: MergeParams, scale=(1, 1), ref: int = 0):
+        vals = [float(x) for x in theta.detach().cpu().tolist()]
+        p = MergeParams(**{**base.__dict__, **dict(zip(PARAM_NAMES, vals))})
+        motion_c = motion.detach().contiguous()
+        rgb, den = merge(burst, motion_c, p, scale, ref, with_den=True)
+        ctx.save_for_backward(motion_c, rgb, den)
+        ctx.burst, ctx.p, ctx.scale, ctx.ref = burst, p, scale, ref
+        ctx.theta_device = theta.device
+        return rgb
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        motion_c, rgb, den = ctx.saved_tensors
+        gp, gm = merge_backward(ctx.burst, motion_c, ctx.p, rgb, den, grad_rgb, ctx.scale, ctx.ref)
+        return gp.to(ctx.theta_device), gm, None, None, None, None

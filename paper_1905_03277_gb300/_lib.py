@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libhmfsr.so")
-SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_static.cu")
+SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "merge_static.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -77,9 +77,10 @@ class MergeParamsC(ctypes.Structure):
         ("tile", ctypes.c_int)]
 
 
-OP_ALIGN, OP_MERGE, OP_MERGE_STAGES = 0, 1, 2
+OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD = 0, 1, 2, 3
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
-           "hmfsr_merge_stages", "hmfsr_merge_static", "hmfsr_status_string", "hmfsr_version")
+           "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_status_string",
+           "hmfsr_version")
 
 _lib = None
 
@@ -107,6 +108,8 @@ def load(path: str | None = None):
     L.hmfsr_merge_accumulate.restype = ci
     L.hmfsr_merge_stages.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, vp, vp, sz, vp]
     L.hmfsr_merge_stages.restype = ci
+    L.hmfsr_merge_backward.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.hmfsr_merge_backward.restype = ci
     L.hmfsr_merge_static.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp]
     L.hmfsr_merge_static.restype = ci
     L.hmfsr_status_string.argtypes = [ci]

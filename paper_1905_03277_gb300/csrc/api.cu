@@ -143,6 +143,14 @@ size_t hmfsr_workspace_size(int op, const hmfsr_burst_desc *desc, int tile, int 
         MergePlanes P;
         return carve_merge(nullptr, g, &P);
     }
+    if (op == HMFSR_OP_MERGE_BACKWARD) {
+        if (!valid_scale(scale_num, scale_den)) return 0;
+        MergePlanes P;
+        BwdPlanes B;
+        const int ho = (int)(((long long)desc->height * scale_num) / scale_den);
+        const int wo = (int)(((long long)desc->width * scale_num) / scale_den);
+        return carve_backward(nullptr, g, ho, wo, carve_merge(nullptr, g, &P), &B);
+    }
     return 0;
 }
 
@@ -227,6 +235,33 @@ hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_des
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, consts_of(params), P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_export_stages(g, P, omega_dev, rhat_dev, s));
+}
+
+hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                  const hmfsr_merge_params *params, int scale_num, int scale_den,
+                                  const float *rgb_dev, const float *den_dev, const float *grad_rgb_dev,
+                                  float *grad_params_dev, float *grad_motion_dev, void *ws, size_t ws_bytes,
+                                  void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !rgb_dev || !den_dev || !grad_rgb_dev || !grad_params_dev || !grad_motion_dev ||
+        !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params) || !valid_scale(scale_num, scale_den))
+        return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    BwdPlanes B;
+    const int ho = (int)(((long long)desc->height * scale_num) / scale_den);
+    const int wo = (int)(((long long)desc->width * scale_num) / scale_den);
+    const size_t fwd = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, carve_backward(nullptr, g, ho, wo, fwd, &B));
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    carve_backward(ws, g, ho, wo, fwd, &B);
+    cudaStream_t s = (cudaStream_t)stream;
+    const MergeConsts c = consts_of(params);
+    if (launch_merge_prep(burst_dev, motion_dev, g, c, P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
+    return cuda_status(launch_merge_backward(burst_dev, motion_dev, g, c, P, B, scale_num, scale_den, rgb_dev, den_dev,
+                                             grad_rgb_dev, grad_params_dev, grad_motion_dev, s));
 }
 
 const char *hmfsr_status_string(hmfsr_status s) {

@@ -1,0 +1,549 @@
+// Adjoint of the merge (reverse mode of Eq. 1-9 and the supplement's kernel heuristics).
+//
+// Differentiable inputs: the kernel parameters k_detail, k_denoise, D_th, D_tr,
+// k_stretch, k_shrink, the robustness scale s (s2 of Eq. 8; s1 stays fixed) and the
+// threshold t, and every tile's motion vector.  Discrete decisions (window centres,
+// tiles, s1/s2 selection, clamps, the 5x5 argmin, bilinear cells) carry no gradient.
+// The forward is recomputed from the burst; the forward's normalised colour C and
+// log2 of its weight sum are read back, so each sample's normalised weight is
+// 2^-(q' + log2 den).  All reductions are deterministic: per-pixel and per-texel
+// contributions go to buffers and are summed in a fixed order in FP64.
+#include "hmfsr_internal.cuh"
+
+namespace hmfsr {
+namespace {
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+constexpr int kBwdW = 32, kBwdH = 4, kBwdThreads = kBwdW * kBwdH;
+
+// ---------------------------------------------------------------------------------------
+// per texel: what the kernel-shape derivative needs {A, sqrt(l1_norm), cos 2t, sin 2t}
+// ---------------------------------------------------------------------------------------
+__global__ void k_shape(const ushort4 *__restrict__ guide, int hh, int wh, int wl, float4 *__restrict__ shape) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    if (u >= wh) return;
+    const ushort4 *G = guide + (size_t)f * hh * wh;
+    int L[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            L[j][i] = G[(size_t)clampi(v - 1 + j, 0, hh - 1) * wh + clampi(u - 1 + i, 0, wh - 1)].w;
+    long long ta = 0, tb = 0, tc = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int gx = (L[j][i + 1] - L[j][i]) + (L[j + 1][i + 1] - L[j + 1][i]);
+            const int gy = (L[j + 1][i] - L[j][i]) + (L[j + 1][i + 1] - L[j][i + 1]);
+            ta += (long long)gx * gx;
+            tb += (long long)gx * gy;
+            tc += (long long)gy * gy;
+        }
+    const float tr = (float)(ta + tc), amc = (float)(ta - tc), b2 = 2.f * (float)tb;
+    const float r = sqrtf(amc * amc + b2 * b2);
+    float cs = 1.f, sn = 0.f;
+    if (!(ta == tc && tb == 0)) { cs = amc / r; sn = b2 / r; }
+    const float A = (ta + tc == 0) ? 1.f : 1.f + sqrtf(r / tr);
+    const float rl = sqrtf(0.5f * (tr + r)) / (16.f * (float)wl);
+    shape[((size_t)f * hh + v) * wh + u] = make_float4(A, rl, cs, sn);
+}
+
+// d k_across / d p and d k_along / d p for the six kernel parameters at one texel
+struct KGrad {
+    float dac[6], dal[6];
+};
+
+__device__ __forceinline__ void kernel_grad(const float4 sh, const MergeConsts &c, KGrad &kg) {
+    const float A = sh.x, rl = sh.y;
+    const float Draw = 1.f - rl / c.d_tr + c.d_th;
+    const float D = fminf(fmaxf(Draw, 0.f), 1.f);
+    const bool inside = Draw > 0.f && Draw < 1.f;
+    const float dD2 = inside ? 1.f : 0.f, dD3 = inside ? rl / (c.d_tr * c.d_tr) : 0.f;
+    const float kh_al = c.k_detail * c.k_stretch * A, kh_ac = c.k_detail / (c.k_shrink * A);
+    const float kd = c.k_detail * c.k_denoise;
+    const float s_al = (1.f - D) * kh_al + D * kd, s_ac = (1.f - D) * kh_ac + D * kd;
+    const float al[6] = {(1.f - D) * c.k_stretch * A + D * c.k_denoise, D * c.k_detail, (kd - kh_al) * dD2,
+                         (kd - kh_al) * dD3, (1.f - D) * c.k_detail * A, 0.f};
+    const float ac[6] = {(1.f - D) / (c.k_shrink * A) + D * c.k_denoise, D * c.k_detail, (kd - kh_ac) * dD2,
+                         (kd - kh_ac) * dD3, 0.f, -(1.f - D) * c.k_detail / (c.k_shrink * c.k_shrink * A)};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        kg.dal[q] = 2.f * s_al * al[q];
+        kg.dac[q] = 2.f * s_ac * ac[q];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// per tile: 1 where the motion prior (Eq. 7-8) chose s2, the same FP64 decision as the
+// forward's
+// ---------------------------------------------------------------------------------------
+__global__ void k_sel(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th,
+                      unsigned char *__restrict__ sel) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * ty * tx) return;
+    const int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
+    const float2 *mv = motion + (size_t)f * ty * tx;
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    for (int j = -1; j <= 1; ++j)
+        for (int k = -1; k <= 1; ++k) {
+            const int yy = y + j, xx = x + k;
+            if (yy < 0 || yy >= ty || xx < 0 || xx >= tx) continue;
+            const float2 v = mv[(size_t)yy * tx + xx];
+            mnx = fminf(mnx, v.x); mxx = fmaxf(mxx, v.x);
+            mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
+        }
+    const double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
+    const double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
+    sel[i] = (M > (double)m_th) ? 0 : 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// per base texel of frame f != ref: R with its partial derivatives
+// ---------------------------------------------------------------------------------------
+__global__ void k_rback(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
+                        const float2 *__restrict__ motion, const float *__restrict__ s_tile,
+                        const unsigned char *__restrict__ sel, Geom g, MergeConsts c, float4 *__restrict__ rb,
+                        unsigned char *__restrict__ flags) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    if (u >= g.wh || f == g.ref) return;
+    const size_t hw = (size_t)g.hh * g.wh;
+    const int half_tile = g.tile / 2;
+    const int txi = min(u / half_tile, g.tx - 1), tyi = min(v / half_tile, g.ty - 1);
+    const float2 mv = motion[((size_t)f * g.ty + tyi) * g.tx + txi];
+    const float s = s_tile[((size_t)f * g.ty + tyi) * g.tx + txi];
+    const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
+    const float flx = floorf(hx), fly = floorf(hy);
+    const float fx = hx - flx, fy = hy - fly;
+    const int ix = u + (int)flx, iy = v + (int)fly;
+    const int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
+    const int y0 = clampi(iy, 0, g.hh - 1), y1 = clampi(iy + 1, 0, g.hh - 1);
+    const uint2 *Sb = s1 + (size_t)g.ref * hw, *Sn = s1 + (size_t)f * hw;
+    const uint2 sb = Sb[(size_t)v * g.wh + u];
+    const uint2 n00 = Sn[(size_t)y0 * g.wh + x0], n10 = Sn[(size_t)y0 * g.wh + x1];
+    const uint2 n01 = Sn[(size_t)y1 * g.wh + x0], n11 = Sn[(size_t)y1 * g.wh + x1];
+    const float4 st = base_stats[(size_t)v * g.wh + u];
+    const float b00 = (1.f - fx) * (1.f - fy), b10 = fx * (1.f - fy), b01 = (1.f - fx) * fy, b11 = fx * fy;
+    float dd = 0.f, gvx = 0.f, gvy = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        int sbv, m00, m10, m01, m11;
+        float inv, dmd2;
+        if (ch == 0) {
+            sbv = sb.x & 0xffff; m00 = n00.x & 0xffff; m10 = n10.x & 0xffff; m01 = n01.x & 0xffff; m11 = n11.x & 0xffff;
+            inv = 1.f / 9.f; dmd2 = st.y;
+        } else if (ch == 1) {
+            sbv = sb.y; m00 = n00.y; m10 = n10.y; m01 = n01.y; m11 = n11.y;
+            inv = 1.f / 18.f; dmd2 = st.z;
+        } else {
+            sbv = sb.x >> 16; m00 = n00.x >> 16; m10 = n10.x >> 16; m01 = n01.x >> 16; m11 = n11.x >> 16;
+            inv = 1.f / 9.f; dmd2 = st.w;
+        }
+        const float dms = inv * (b00 * (float)(sbv - m00) + b10 * (float)(sbv - m10) + b01 * (float)(sbv - m01) +
+                                 b11 * (float)(sbv - m11));
+        // d mu_aligned / d position (in mean units)
+        const float dmx = inv * ((1.f - fy) * (float)(m10 - m00) + fy * (float)(m11 - m01));
+        const float dmy = inv * ((1.f - fx) * (float)(m01 - m00) + fx * (float)(m11 - m10));
+        const float d2 = dms * dms, den = d2 + dmd2;
+        const float d = den > 0.f ? dms * d2 / den : 0.f;
+        const float dd_dms = den > 0.f ? (d2 * d2 + 3.f * dmd2 * d2) / (den * den) : 0.f;
+        dd += d * d;
+        gvx += 2.f * d * dd_dms * (-dmx) * 0.5f;
+        gvy += 2.f * d * dd_dms * (-dmy) * 0.5f;
+    }
+    const float e = expf(-dd / st.x);
+    const float raw = s * e - c.t;
+    const float R = fminf(fmaxf(raw, 0.f), 1.f);
+    const bool unclamped = raw > 0.f && raw < 1.f;
+    float4 out = make_float4(R, 0.f, 0.f, 0.f);
+    if (unclamped) {
+        out.y = -s * e * gvx / st.x;
+        out.z = -s * e * gvy / st.x;
+        out.w = sel[((size_t)f * g.ty + tyi) * g.tx + txi] ? e : 0.f;
+    }
+    const size_t o = (size_t)f * hw + (size_t)v * g.wh + u;
+    rb[o] = out;
+    flags[o] = unclamped ? 0x80 : 0;
+}
+
+// first minimum of R over the 5x5 window of valid pixels (scan order), offset 0..24
+__global__ void k_argmin(const float4 *__restrict__ rb, Geom g, unsigned char *__restrict__ flags) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    if (u >= g.wh || f == g.ref) return;
+    const size_t hw = (size_t)g.hh * g.wh;
+    const float4 *Rp = rb + (size_t)f * hw;
+    float best = INFINITY;
+    int bi = 12;
+    for (int j = -2; j <= 2; ++j)
+        for (int i = -2; i <= 2; ++i) {
+            const int uu = u + i, vv = v + j;
+            if (uu < 0 || uu >= g.wh || vv < 0 || vv >= g.hh) continue;
+            const float r = Rp[(size_t)vv * g.wh + uu].x;
+            if (r < best) { best = r; bi = (j + 2) * 5 + (i + 2); }
+        }
+    const size_t o = (size_t)f * hw + (size_t)v * g.wh + u;
+    flags[o] = (unsigned char)((flags[o] & 0x80) | bi);
+}
+
+// ---------------------------------------------------------------------------------------
+// per output pixel: recompute the frame loop and emit the adjoint contributions
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBwdThreads) k_merge_bwd(
+    const uint16_t *__restrict__ burst, const float2 *__restrict__ motion, Geom g, MergeConsts c,
+    const float4 *__restrict__ kern, const float4 *__restrict__ shape, const float *__restrict__ rhat_planes,
+    int snum, int sden, int ho, int wo, const float *__restrict__ rgb, const float *__restrict__ lden,
+    const float *__restrict__ grad_rgb, float2 *__restrict__ vbar_pix, float *__restrict__ rhbar_pix,
+    double *__restrict__ partials) {
+    __shared__ double s_red[kBwdThreads];
+    const int X = blockIdx.x * kBwdW + threadIdx.x;
+    const int Y = blockIdx.y * kBwdH + threadIdx.y;
+    const int tid = threadIdx.y * kBwdW + threadIdx.x;
+    const bool active = X < wo && Y < ho;
+    float pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (active) {
+        const int Q = 2 * snum, Q2 = 4 * snum;
+        const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
+        const int Px = 2 * sden * X + sden - snum, Py = 2 * sden * Y + sden - snum;
+        const int txi = clampi(floor_div(Px, Q * g.tile), 0, g.tx - 1);
+        const int tyi = clampi(floor_div(Py, Q * g.tile), 0, g.ty - 1);
+        const size_t hw = (size_t)g.hh * g.wh, po = (size_t)ho * wo, op = (size_t)Y * wo + X;
+        const int rx = floor_div(Px - snum, Q2), ry = floor_div(Py - snum, Q2);
+        const float rfx = (float)(Px - snum - rx * Q2) * inv2Q, rfy = (float)(Py - snum - ry * Q2) * inv2Q;
+        const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
+        const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
+        const float rw00 = (1.f - rfx) * (1.f - rfy), rw10 = rfx * (1.f - rfy), rw01 = (1.f - rfx) * rfy,
+                    rw11 = rfx * rfy;
+        const float Cc[3] = {rgb[op], rgb[po + op], rgb[2 * po + op]};
+        const float Lc[3] = {lden[op], lden[po + op], lden[2 * po + op]};
+        const float gc[3] = {grad_rgb[op], grad_rgb[po + op], grad_rgb[2 * po + op]};
+        for (int f = 0; f < g.n; ++f) {
+            float vx = 0.f, vy = 0.f, rh = 1.f;
+            if (f != g.ref) {
+                const float *Rp = rhat_planes + (size_t)f * hw;
+                rh = rw00 * Rp[(size_t)ry0 * g.wh + rx0] + rw10 * Rp[(size_t)ry0 * g.wh + rx1] +
+                     rw01 * Rp[(size_t)ry1 * g.wh + rx0] + rw11 * Rp[(size_t)ry1 * g.wh + rx1];
+                const float2 mv = motion[((size_t)f * g.ty + tyi) * g.tx + txi];
+                vx = mv.x;
+                vy = mv.y;
+            }
+            const int FX = floor_mul(Q, vx), FY = floor_mul(Q, vy);
+            const int kx = floor_div(Px + snum + FX, Q), ky = floor_div(Py + snum + FY, Q);
+            const float dx0 = fmaf(-fQ, vx, (float)(kx * Q - Px)) * invQ;
+            const float dy0 = fmaf(-fQ, vy, (float)(ky * Q - Py)) * invQ;
+            const float zx = fmaf(fQ, vx, -(float)FX), zy = fmaf(fQ, vy, -(float)FY);
+            const int gx = Px - snum + FX, gy = Py - snum + FY;
+            const int ox = floor_div(gx, Q2), oy = floor_div(gy, Q2);
+            const float ax = ((float)(gx - ox * Q2) + zx) * inv2Q, ay = ((float)(gy - oy * Q2) + zy) * inv2Q;
+            const int tx_[4] = {clampi(ox, 0, g.wh - 1), clampi(ox + 1, 0, g.wh - 1), clampi(ox, 0, g.wh - 1),
+                                clampi(ox + 1, 0, g.wh - 1)};
+            const int ty_[4] = {clampi(oy, 0, g.hh - 1), clampi(oy, 0, g.hh - 1), clampi(oy + 1, 0, g.hh - 1),
+                                clampi(oy + 1, 0, g.hh - 1)};
+            const float beta[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
+            const float dbx[4] = {-(1.f - ay), 1.f - ay, -ay, ay};
+            const float dby[4] = {-(1.f - ax), -ax, 1.f - ax, ax};
+            float4 t[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] = kern[(size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]];
+            // Omega = a I + sum g_k u u^T with the accurate (Cauchy-Binet) determinant
+            float a = 0.f, G = 0.f, Oxx = 0.f, Oxy = 0.f, Oyy = 0.f, gk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                gk[k] = beta[k] * t[k].y;
+                a += beta[k] * t[k].x;
+                G += gk[k];
+                Oxx += gk[k] * t[k].z * t[k].z;
+                Oxy += gk[k] * t[k].z * t[k].w;
+                Oyy += gk[k] * t[k].w * t[k].w;
+            }
+            float detM = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int l = k + 1; l < 4; ++l) {
+                    const float cr = t[k].z * t[l].w - t[k].w * t[l].z;
+                    detM += gk[k] * gk[l] * cr * cr;
+                }
+            const float det = fmaf(a, a + G, detM);
+            const float invdet = 1.f / det;
+            // adj(Omega) = a I + [[Oyy, -Oxy], [-Oxy, Oxx]] of M
+            const float Axx = a + Oyy, Ayy = a + Oxx, Axy = -Oxy;
+            const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
+            float ob0 = 0.f, ob1 = 0.f, ob2 = 0.f, vbx = 0.f, vby = 0.f, rhb = 0.f;
+#pragma unroll
+            for (int j = -1; j <= 1; ++j)
+#pragma unroll
+                for (int i = -1; i <= 1; ++i) {
+                    const int qx = kx + i, qy = ky + j;
+                    if (qx < 0 || qx >= g.w || qy < 0 || qy >= g.h) continue;
+                    const float dx = dx0 + (float)i, dy = dy0 + (float)j;
+                    const float Pxv = (Axx * dx + Axy * dy) * invdet, Pyv = (Axy * dx + Ayy * dy) * invdet;
+                    const float qq = dx * Pxv + dy * Pyv;  // d^T Omega^-1 d
+                    const int ch = (qx & 1) + (qy & 1);
+                    const float wn = fast_exp2(-(kHalfLog2e * qq + Lc[ch]));  // w / den
+                    const float cv = (float)fr[(size_t)qy * g.pitch + qx];
+                    const float e = gc[ch] * (cv - Cc[ch]) * wn;  // dL/d(w Rhat) * w
+                    rhb += e;
+                    const float qb = -0.5f * rh * e;  // dL/dq
+                    vbx -= 2.f * qb * Pxv;
+                    vby -= 2.f * qb * Pyv;
+                    ob0 -= qb * Pxv * Pxv;
+                    ob1 -= 2.f * qb * Pxv * Pyv;
+                    ob2 -= qb * Pyv * Pyv;
+                }
+            // Omega sampling position (x0 + v - 1/2)/2 and the texel parameters
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float ux = t[k].z, uy = t[k].w;
+                const float okx = t[k].x + t[k].y * ux * ux, oky = t[k].y * ux * uy, okz = t[k].x + t[k].y * uy * uy;
+                const float dot = ob0 * okx + ob1 * oky + ob2 * okz;
+                vbx += 0.5f * dbx[k] * dot;
+                vby += 0.5f * dby[k] * dot;
+                const float4 sh = shape[(size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]];
+                KGrad kg;
+                kernel_grad(sh, c, kg);
+                const float e1xx = 0.5f * (1.f + sh.z), e1xy = 0.5f * sh.w, e1yy = 0.5f * (1.f - sh.z);
+                const float oE1 = ob0 * e1xx + ob1 * e1xy + ob2 * e1yy;
+                const float oE2 = (ob0 + ob2) - oE1;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) pb[q] += beta[k] * (kg.dac[q] * oE1 + kg.dal[q] * oE2);
+            }
+            const size_t of = (size_t)f * po + op;
+            vbar_pix[of] = (f == g.ref) ? make_float2(0.f, 0.f) : make_float2(vbx, vby);
+            rhbar_pix[of] = (f == g.ref) ? 0.f : rhb;
+        }
+    }
+    // block sums of the six kernel-parameter gradients, in FP64 and a fixed order
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll 1
+    for (int q = 0; q < 6; ++q) {
+        s_red[tid] = (double)pb[q];
+        __syncthreads();
+        for (int sstep = kBwdThreads / 2; sstep > 0; sstep >>= 1) {
+            if (tid < sstep) s_red[tid] += s_red[tid + sstep];
+            __syncthreads();
+        }
+        if (tid == 0) partials[(size_t)bid * 6 + q] = s_red[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Rhat-bar gathered onto base texels, then through the 5x5 argmin into R's parameters
+// ---------------------------------------------------------------------------------------
+__global__ void k_rhat_gather(const float *__restrict__ rhbar_pix, Geom g, int snum, int sden, int ho, int wo,
+                              float *__restrict__ rhbar_tex) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    if (u >= g.wh || f == g.ref) return;
+    const int Q2 = 4 * snum;
+    const float inv2Q = 0.25f / (float)snum;
+    // output pixels whose bilinear taps (clamped) reach texel u: x0 within (2u - 1.5, 2u + 2.5)
+    // plus, at the border, every pixel clamped onto it
+    auto xrange = [&](int t, int nt, int nout, int &lo, int &hi) {
+        lo = (int)floorf(((2.f * t - 1.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) - 1;
+        hi = (int)ceilf(((2.f * t + 2.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) + 1;
+        if (t == 0) lo = 0;
+        if (t == nt - 1) hi = nout - 1;
+        lo = max(lo, 0);
+        hi = min(hi, nout - 1);
+    };
+    int xlo, xhi, ylo, yhi;
+    xrange(u, g.wh, wo, xlo, xhi);
+    xrange(v, g.hh, ho, ylo, yhi);
+    const size_t po = (size_t)ho * wo;
+    float acc = 0.f;
+    for (int Y = ylo; Y <= yhi; ++Y) {
+        const int Py = 2 * sden * Y + sden - snum;
+        const int ry = floor_div(Py - snum, Q2);
+        const float fy = (float)(Py - snum - ry * Q2) * inv2Q;
+        const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
+        const float wy = (ry0 == v ? 1.f - fy : 0.f) + (ry1 == v ? fy : 0.f);
+        if (wy == 0.f) continue;
+        for (int X = xlo; X <= xhi; ++X) {
+            const int Px = 2 * sden * X + sden - snum;
+            const int rx = floor_div(Px - snum, Q2);
+            const float fx = (float)(Px - snum - rx * Q2) * inv2Q;
+            const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
+            const float wx = (rx0 == u ? 1.f - fx : 0.f) + (rx1 == u ? fx : 0.f);
+            if (wx == 0.f) continue;
+            acc += wx * wy * rhbar_pix[(size_t)f * po + (size_t)Y * wo + X];
+        }
+    }
+    rhbar_tex[(size_t)f * g.hh * g.wh + (size_t)v * g.wh + u] = acc;
+}
+
+constexpr int kRpThreads = 128;
+
+__global__ void __launch_bounds__(kRpThreads) k_rpath(const float *__restrict__ rhbar_tex,
+                                                      const unsigned char *__restrict__ flags,
+                                                      const float4 *__restrict__ rb, Geom g,
+                                                      float2 *__restrict__ vbar_tex, double *__restrict__ partials) {
+    __shared__ double s_red[2][kRpThreads];
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    const size_t hw = (size_t)g.hh * g.wh;
+    float pt = 0.f, ps = 0.f;
+    if (u < g.wh && f != g.ref) {
+        // R-bar(u,v) = sum of Rhat-bar over the 5x5 windows whose argmin is (u,v)
+        float rbar = 0.f;
+        for (int j = -2; j <= 2; ++j)
+            for (int i = -2; i <= 2; ++i) {
+                const int uu = u + i, vv = v + j;
+                if (uu < 0 || uu >= g.wh || vv < 0 || vv >= g.hh) continue;
+                const size_t o = (size_t)f * hw + (size_t)vv * g.wh + uu;
+                const int bi = flags[o] & 0x1f;
+                // window of (uu,vv) picked offset bi = (dj+2)*5 + (di+2): the pixel (uu+di, vv+dj)
+                if (uu + (bi % 5 - 2) == u && vv + (bi / 5 - 2) == v) rbar += rhbar_tex[o];
+            }
+        const size_t o = (size_t)f * hw + (size_t)v * g.wh + u;
+        const bool unclamped = (flags[o] & 0x80) != 0;
+        const float4 d = rb[o];
+        vbar_tex[o] = unclamped ? make_float2(rbar * d.y, rbar * d.z) : make_float2(0.f, 0.f);
+        if (unclamped) {
+            ps = rbar * d.w;
+            pt = -rbar;
+        }
+    }
+    const int tid = threadIdx.x;
+    s_red[0][tid] = (double)ps;
+    s_red[1][tid] = (double)pt;
+    __syncthreads();
+    for (int sstep = kRpThreads / 2; sstep > 0; sstep >>= 1) {
+        if (tid < sstep) {
+            s_red[0][tid] += s_red[0][tid + sstep];
+            s_red[1][tid] += s_red[1][tid + sstep];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[bid * 2] = s_red[0][0];
+        partials[bid * 2 + 1] = s_red[1][0];
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// deterministic final sums
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int tile_first(int k, int ntiles, int nout, int snum, int sden, int tile) {
+    if (k <= 0) return 0;
+    if (k >= ntiles) return nout;
+    const int a = k * 2 * snum * tile - sden + snum, b = 2 * sden;
+    return min((a + b - 1) / b, nout);
+}
+
+constexpr int kRedThreads = 128;
+
+// one block per (frame, tile): output-pixel and texel contributions of that tile
+__global__ void __launch_bounds__(kRedThreads) k_motion_reduce(const float2 *__restrict__ vbar_pix,
+                                                               const float2 *__restrict__ vbar_tex, Geom g, int snum,
+                                                               int sden, int ho, int wo, float *__restrict__ grad_motion) {
+    __shared__ double s_red[2][kRedThreads];
+    const int txi = blockIdx.x, tyi = blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
+    double sx = 0.0, sy = 0.0;
+    if (f != g.ref) {
+        const int X0 = tile_first(txi, g.tx, wo, snum, sden, g.tile), X1 = tile_first(txi + 1, g.tx, wo, snum, sden, g.tile);
+        const int Y0 = tile_first(tyi, g.ty, ho, snum, sden, g.tile), Y1 = tile_first(tyi + 1, g.ty, ho, snum, sden, g.tile);
+        const int tw = X1 - X0, npix = tw * (Y1 - Y0);
+        const size_t po = (size_t)ho * wo;
+        for (int k = tid; k < npix; k += kRedThreads) {
+            const float2 vb = vbar_pix[(size_t)f * po + (size_t)(Y0 + k / tw) * wo + X0 + k % tw];
+            sx += vb.x;
+            sy += vb.y;
+        }
+        const int ht = g.tile / 2;
+        const int u0 = txi * ht, v0 = tyi * ht;
+        const int u1 = (txi == g.tx - 1) ? g.wh : min(u0 + ht, g.wh), v1 = (tyi == g.ty - 1) ? g.hh : min(v0 + ht, g.hh);
+        const int twt = u1 - u0, nt = twt * (v1 - v0);
+        const size_t hw = (size_t)g.hh * g.wh;
+        for (int k = tid; k < nt; k += kRedThreads) {
+            const float2 vb = vbar_tex[(size_t)f * hw + (size_t)(v0 + k / twt) * g.wh + u0 + k % twt];
+            sx += vb.x;
+            sy += vb.y;
+        }
+    }
+    s_red[0][tid] = sx;
+    s_red[1][tid] = sy;
+    __syncthreads();
+    for (int sstep = kRedThreads / 2; sstep > 0; sstep >>= 1) {
+        if (tid < sstep) {
+            s_red[0][tid] += s_red[0][tid + sstep];
+            s_red[1][tid] += s_red[1][tid + sstep];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const size_t o = (((size_t)f * g.ty + tyi) * g.tx + txi) * 2;
+        grad_motion[o] = (float)s_red[0][0];
+        grad_motion[o + 1] = (float)s_red[1][0];
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_param_reduce(const double *__restrict__ p6, int n6,
+                                                              const double *__restrict__ p2, int n2,
+                                                              float *__restrict__ grad_params) {
+    __shared__ double s_red[kRedThreads];
+    const int q = blockIdx.x, tid = threadIdx.x;  // q = 0..7
+    double acc = 0.0;
+    if (q < 6)
+        for (int k = tid; k < n6; k += kRedThreads) acc += p6[(size_t)k * 6 + q];
+    else
+        for (int k = tid; k < n2; k += kRedThreads) acc += p2[(size_t)k * 2 + (q - 6)];
+    s_red[tid] = acc;
+    __syncthreads();
+    for (int sstep = kRedThreads / 2; sstep > 0; sstep >>= 1) {
+        if (tid < sstep) s_red[tid] += s_red[tid + sstep];
+        __syncthreads();
+    }
+    if (tid == 0) grad_params[q] = (float)s_red[0];
+}
+
+}  // namespace
+
+// workspace of the adjoint beyond the forward planes
+size_t carve_backward(void *ws, const Geom &g, int ho, int wo, size_t fwd_bytes, BwdPlanes *B) {
+    char *base = static_cast<char *>(ws);
+    size_t off = fwd_bytes;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return base ? (void *)(base + o) : nullptr;
+    };
+    const size_t hw = (size_t)g.hh * g.wh, npx = (size_t)ho * wo;
+    B->shape = (float4 *)take(sizeof(float4) * g.n * hw);
+    B->rb = (float4 *)take(sizeof(float4) * g.n * hw);
+    B->flags = (unsigned char *)take(g.n * hw);
+    B->rhbar_tex = (float *)take(sizeof(float) * g.n * hw);
+    B->vbar_tex = (float2 *)take(sizeof(float2) * g.n * hw);
+    B->vbar_pix = (float2 *)take(sizeof(float2) * g.n * npx);
+    B->rhbar_pix = (float *)take(sizeof(float) * g.n * npx);
+    B->n_bwd_blocks = div_up(wo, kBwdW) * div_up(ho, kBwdH);
+    B->n_rp_blocks = div_up(g.wh, kRpThreads) * g.hh * g.n;
+    B->part6 = (double *)take(sizeof(double) * 6 * (size_t)B->n_bwd_blocks);
+    B->part2 = (double *)take(sizeof(double) * 2 * (size_t)B->n_rp_blocks);
+    B->sel = (unsigned char *)take((size_t)g.n * g.ty * g.tx);
+    return off;
+}
+
+cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                                  const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
+                                  const float *lden, const float *grad_rgb, float *grad_params, float *grad_motion,
+                                  cudaStream_t s) {
+    const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
+    const float2 *mv = reinterpret_cast<const float2 *>(motion);
+    const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
+    k_shape<<<tex_grid, 128, 0, s>>>(P.guide, g.hh, g.wh, g.wl, B.shape);
+    k_sel<<<div_up(g.n * g.ty * g.tx, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, B.sel);
+    k_rback<<<tex_grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, B.sel, g, c, B.rb, B.flags);
+    k_argmin<<<tex_grid, 128, 0, s>>>(B.rb, g, B.flags);
+    k_merge_bwd<<<dim3(div_up(wo, kBwdW), div_up(ho, kBwdH)), dim3(kBwdW, kBwdH), 0, s>>>(
+        burst, mv, g, c, P.kern, B.shape, P.rhat, snum, sden, ho, wo, rgb, lden, grad_rgb, B.vbar_pix, B.rhbar_pix,
+        B.part6);
+    k_rhat_gather<<<tex_grid, 128, 0, s>>>(B.rhbar_pix, g, snum, sden, ho, wo, B.rhbar_tex);
+    k_rpath<<<dim3(div_up(g.wh, kRpThreads), g.hh, g.n), kRpThreads, 0, s>>>(B.rhbar_tex, B.flags, B.rb, g,
+                                                                           B.vbar_tex, B.part2);
+    k_motion_reduce<<<dim3(g.tx, g.ty, g.n), kRedThreads, 0, s>>>(B.vbar_pix, B.vbar_tex, g, snum, sden, ho, wo,
+                                                                  grad_motion);
+    k_param_reduce<<<8, kRedThreads, 0, s>>>(B.part6, B.n_bwd_blocks, B.part2, B.n_rp_blocks, grad_params);
+    return cudaGetLastError();
+}
+
+}  // namespace hmfsr

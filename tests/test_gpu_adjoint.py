@@ -1,0 +1,72 @@
+"""CUDA adjoint of the merge vs the FP64 oracle adjoint (itself pinned by central finite
+differences), through the C-ABI; 1e-3 relative."""
+import numpy as np
+import pytest
+import torch
+
+import burstgen
+import oracle
+import paper_1905_03277_gb300 as hm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    hm.build()
+    return torch.device("cuda:0")
+
+
+def case(seed, h, w, n, scale, robust=True):
+    b = burstgen.make_burst(dict(n=n, h=h, w=w, gain=1.0, read=3.0, motion="global", scale=(1, 1)), seed=seed)
+    raw = b["raw"].numpy()
+    _, mf, _, _ = oracle.align(raw)
+    mv = mf.astype(np.float32)
+    mv[min(2, n - 1), 1, 2] += np.float32(0.9)
+    p = hm.MergeParams(k_detail=0.3, k_denoise=3.0, d_th=0.004, d_tr=0.05, k_stretch=3.0, k_shrink=1.8, t=0.12,
+                       s1=12.0, s2=1.1 if robust else 2.0, m_th=3.0, noise_a=0.02, noise_b=0.5)
+    ho, wo = hm.out_size(h, w, scale)
+    g = np.random.default_rng(seed).normal(size=(3, ho, wo))
+    return raw, mv, p, g
+
+
+def oparams(p):
+    return oracle.MergeParams(**{k: getattr(p, k) for k in oracle.MergeParams.__dataclass_fields__})
+
+
+@pytest.mark.parametrize("scale,ref", [((1, 1), 0), ((3, 2), 1), ((2, 1), 0)])
+def test_adjoint_matches_oracle(dev, scale, ref):
+    raw, mv, p, g = case(51, 64, 96, 4, scale)
+    burst = torch.from_numpy(raw).to(dev)
+    motion = torch.from_numpy(mv).to(dev)
+    rgb, den = hm.merge(burst, motion, p, scale, ref, with_den=True)
+    gp, gm = hm.merge_backward(burst, motion, p, rgb, den, torch.from_numpy(g).float().to(dev), scale, ref)
+    ogp, ogm = oracle.merge_backward(raw, mv, oparams(p), g, scale=scale, ref=ref)
+    gp = gp.cpu().numpy().astype(np.float64)
+    gm = gm.cpu().numpy().astype(np.float64)
+    assert np.isfinite(gp).all() and np.isfinite(gm).all()
+    for k, name in enumerate(hm.PARAM_NAMES):
+        assert gp[k] == pytest.approx(ogp[k], rel=1e-3, abs=1e-3 * np.abs(ogp).max()), (name, gp[k], ogp[k])
+    scale_m = np.abs(ogm).max()
+    assert np.abs(gm - ogm).max() <= 1e-3 * scale_m, np.abs(gm - ogm).max() / scale_m
+    assert np.all(gm[ref] == 0)
+
+
+def test_autograd_function_and_descent(dev):
+    raw, mv, p, _ = case(52, 64, 64, 4, (1, 1))
+    burst = torch.from_numpy(raw).to(dev)
+    motion = torch.from_numpy(mv).to(dev).requires_grad_(True)
+    theta = torch.tensor([getattr(p, k) for k in hm.PARAM_NAMES], dtype=torch.float32, requires_grad=True)
+    target = hm.merge(burst, motion.detach(), p).detach() * 0.98
+    rgb = hm.MergeFn.apply(theta, motion, burst, p, (1, 1), 0)
+    loss = ((rgb - target) ** 2).mean()
+    loss.backward()
+    assert theta.grad is not None and motion.grad is not None
+    assert torch.isfinite(theta.grad).all() and torch.isfinite(motion.grad).all()
+    # a small step against the gradient lowers the loss
+    with torch.no_grad():
+        theta2 = theta - 1e-4 * theta.grad / theta.grad.abs().max()
+        rgb2 = hm.MergeFn.apply(theta2, motion.detach(), burst, p, (1, 1), 0)
+        assert ((rgb2 - target) ** 2).mean() < loss
