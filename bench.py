@@ -288,6 +288,27 @@ def run_gpu(args):
         e2e_ms = float(t.item())
     e2e_value = world * mp / (e2e_ms / 1e3)
 
+    # adjoint (fitting workload: 8 x 1024x1024 at 1.5x): forward with den, then backward
+    fb = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 3 + 1000 * rank, device=dev)
+    fraw = fb["raw"]
+    fp = hm.MergeParams(noise_a=fb["gain"], noise_b=fb["read"] ** 2)
+    fmotion = hm.align(fraw, 0, ap)
+    fscale = fb["scale"]
+    fho, fwo = hm.out_size(fraw.shape[1], fraw.shape[2], fscale)
+    gup = torch.randn((3, fho, fwo), device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+    fev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd_ms, bwd_ms = [], []
+    for i in range(8):
+        fev[0].record(stream)
+        frgb, fden = hm.merge(fraw, fmotion, fp, fscale, with_den=True)
+        fev[1].record(stream)
+        hm.merge_backward(fraw, fmotion, fp, frgb, fden, gup, fscale)
+        fev[2].record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            fwd_ms.append(fev[0].elapsed_time(fev[1]))
+            bwd_ms.append(fev[1].elapsed_time(fev[2]))
+
     if rank == 0:
         units = ho * wo * n
         acc_s = statistics.median(acc_ms) / 1e3
@@ -327,10 +348,47 @@ def run_gpu(args):
                 "gpu_launches": launches, "launches_per_step": per_call, "clocks": clocks,
                 "breakdown_ms": {"align": statistics.median(align_ms), "merge_prepare": statistics.median(prep_ms),
                                  "merge_accumulate": statistics.median(acc_ms)},
-                "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)}
+                "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
+                "adjoint": {"workload": "fit: 8 x 1024x1024 RGGB, 1.5x output", "forward_ms": statistics.median(fwd_ms),
+                            "backward_ms": statistics.median(bwd_ms),
+                            "backward_over_forward": statistics.median(bwd_ms) / statistics.median(fwd_ms)}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_fit(args):
+    """Adjoint workload: fit the eight tuning parameters (and the motion) of 16 bursts of
+    8 x 1024x1024 (1.5x ground truth) with Adam; prints one JSON line."""
+    import math
+
+    import torch
+
+    import burstgen
+    import paper_1905_03277_gb300 as hm
+    from paper_1905_03277_gb300.fit import fit
+
+    dev = torch.device("cuda", 0)
+    hm.build()
+    bursts, gts = [], []
+    for k in range(args.fit_bursts):
+        b = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 3 + k, device=dev, with_gt=True)
+        bursts.append(b["raw"])
+        gts.append(b["gt"])
+    base = hm.MergeParams(noise_a=1.0, noise_b=9.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    params, hist, _ = fit(bursts, gts, base, steps=args.fit_steps, scale=(3, 2))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    psnr = lambda mse: 10 * math.log10(4095.0 ** 2 / mse)
+    print(json.dumps({"workload": f"fit: {args.fit_bursts} bursts x 8 x 1024x1024 RGGB, 1.5x ground truth, "
+                                  f"{args.fit_steps} Adam steps (parameters and motion)",
+                      "seconds": dt, "ms_per_step": 1000 * dt / args.fit_steps,
+                      "loss_first": hist[0], "loss_last": hist[-1], "psnr_first_db": psnr(hist[0]),
+                      "psnr_last_db": psnr(hist[-1]), "start": {k: getattr(base, k) for k in hm.PARAM_NAMES},
+                      "fitted": {k: getattr(params, k) for k in hm.PARAM_NAMES}}), flush=True)
     return 0
 
 
@@ -341,11 +399,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("hmfsr", "reference"), default="hmfsr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fit", action="store_true", help="run the parameter-fitting workload instead")
+    ap.add_argument("--fit-steps", type=int, default=200)
+    ap.add_argument("--fit-bursts", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.fit:
+        return run_fit(args)
     return run_gpu(args)
 
 

@@ -70,3 +70,17 @@ def test_autograd_function_and_descent(dev):
         theta2 = theta - 1e-4 * theta.grad / theta.grad.abs().max()
         rgb2 = hm.MergeFn.apply(theta2, motion.detach(), burst, p, (1, 1), 0)
         assert ((rgb2 - target) ** 2).mean() < loss
+
+
+def test_fit_lowers_loss_against_ground_truth(dev):
+    from paper_1905_03277_gb300.fit import fit
+    bursts, gts = [], []
+    for k in range(2):
+        b = burstgen.make_burst(dict(n=4, h=128, w=128, gain=1.0, read=3.0, motion="global", scale=(3, 2)),
+                                seed=60 + k, device=dev, with_gt=True)
+        bursts.append(b["raw"])
+        gts.append(b["gt"])
+    base = hm.MergeParams(noise_a=1.0, noise_b=9.0)
+    params, hist, motions = fit(bursts, gts, base, steps=15, scale=(3, 2))
+    assert hist[-1] < hist[0]
+    assert all(getattr(params, k) > 0 for k in hm.PARAM_NAMES)
