@@ -270,7 +270,7 @@ def make_burst(config: str | dict, seed: int | None = None, device: str | torch.
     gen.manual_seed(seed)
     raw = torch.empty((n, h, w), dtype=torch.uint16, device=device)
     for i in range(n):
-        clean = _render_frame(sc, ms[i], objects, i, n, h, w, device)
+        clean = _render_frame(sc, ms[i], objects, i, n, h, w, device, ss=int(cfg.get("ss", 4)))
         raw[i] = _add_noise(clean, float(cfg["gain"]), float(cfg["read"]), gen)
     out = dict(raw=raw, ref=0, white_level=WHITE_LEVEL, gain=float(cfg["gain"]),
                read=float(cfg["read"]), scale=tuple(cfg.get("scale", (1, 1))), motions=ms,
@@ -303,9 +303,10 @@ def render_gt(sc: Scene, h: int, w: int, scale: tuple, device, ss: int = 8) -> t
 
 
 def make_ragged_batch(n_bursts: int = 64, seed: int | None = None, device="cpu",
-                      mp_range=(0.5, 12.0), max_frames: int = 15) -> list:
+                      mp_range=(0.5, 12.0), max_frames: int = 15, ss: int = 4) -> list:
     """Ragged batch: per burst MP ~ U[mp_range], aspect 4:3 or 16:9 (sides even),
-    frame count ~ U{4..max_frames}, scale in {1, 1.5, 2}, gain ~ U[0.5, 8]."""
+    frame count ~ U{4..max_frames}, scale in {1, 1.5, 2}, gain ~ U[0.5, 8]; `ss` is
+    the per-axis supersampling of the rendering."""
     if seed is None:
         seed = SEED_BASE + 4
     rng = _rng(seed)
@@ -319,7 +320,7 @@ def make_ragged_batch(n_bursts: int = 64, seed: int | None = None, device="cpu",
         n = int(rng.integers(4, max_frames + 1))
         scale = [(1, 1), (3, 2), (2, 1)][int(rng.integers(0, 3))]
         gain = float(rng.uniform(0.5, 8.0))
-        cfg = dict(index=4, n=n, h=h, w=w, gain=gain, read=2.0 + gain, motion="global", scale=scale)
+        cfg = dict(index=4, n=n, h=h, w=w, gain=gain, read=2.0 + gain, motion="global", scale=scale, ss=ss)
         out.append(make_burst(cfg, seed=seed * 1000 + b, device=device))
     return out
 

@@ -153,6 +153,62 @@ hmfsr_status hmfsr_merge_static(const uint16_t *burst_dev, const hmfsr_burst_des
                                 const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
                                 float *den_dev, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Ragged batches: many bursts (any sizes, frame counts and output scales) aligned and
+ * merged by ONE persistent kernel launch, captured in a CUDA graph and replayed.
+ * Results are bit-identical to hmfsr_align + hmfsr_merge on each burst.
+ * Batched bursts use tile 16 and search radii 1..4 at every level.
+ * --------------------------------------------------------------------------------- */
+typedef struct hmfsr_batch_plan_t *hmfsr_batch_plan;
+
+/* Plan a batch (host work only; the plan is host memory owned by the library, released
+ * by hmfsr_batch_free).  Per burst b: descs[b], mparams[b], aparams[b] and the output
+ * scale scale_num[b] / scale_den[b]. */
+hmfsr_status hmfsr_batch_plan_create(const hmfsr_burst_desc *descs, int n_bursts, const hmfsr_merge_params *mparams,
+                                     const hmfsr_align_params *aparams, const int *scale_num, const int *scale_den,
+                                     hmfsr_batch_plan *out);
+
+/* Bytes of workspace (256-byte aligned) a run of this plan needs. */
+size_t hmfsr_batch_workspace_size(hmfsr_batch_plan plan);
+
+/* Run the batch on `stream`: bursts_dev[b] (uint16, layout of desc b), rgb_dev[b]
+ * (float32 [3][Ho][Wo], written) and optionally motion_dev[b] (float32 [n][TY][TX][2],
+ * written; NULL array or entries: kept in the workspace).  Host arrays of device
+ * pointers.  The first run, or a run with a different workspace, stream or grid,
+ * captures and instantiates the CUDA graph; later runs replay it.  The call returns
+ * after enqueueing; hmfsr_batch_wait reports the outcome. */
+hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *bursts_dev, float *const *motion_dev,
+                             float *const *rgb_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Wait for the stream and return the batch's device status: HMFSR_OK, or
+ * HMFSR_ERR_TIMEOUT if a block's bounded wait for a dependency ran out (the kernel then
+ * stops early and the outputs are incomplete; the device stays usable). */
+hmfsr_status hmfsr_batch_wait(hmfsr_batch_plan plan, void *ws, void *stream);
+
+/* Settings: accumulation work item of merge_tile_w x (128 / merge_tile_w) output pixels
+ * (merge_tile_w divides 128), ctas_per_sm persistent blocks per SM (0 = as many as fit),
+ * regs_variant (kernel build with 0: 128, 1: 80, 2: 64 registers per thread),
+ * queue_order (0: stage-major, 1: burst-major, 2: wavefront), spin_limit polls per dependency wait
+ * before HMFSR_ERR_TIMEOUT, and inject_stall != 0 to add a dependency nothing satisfies
+ * (for testing the timeout path). */
+hmfsr_status hmfsr_batch_configure(hmfsr_batch_plan plan, int merge_tile_w, int ctas_per_sm, int regs_variant,
+                                   int queue_order, int spin_limit, int inject_stall);
+
+/* Execution mode: 0 = the one persistent kernel (default); k > 0 = a CUDA graph of every
+ * burst's own kernel sequence (the per-burst path) spread over k parallel branches. */
+hmfsr_status hmfsr_batch_set_mode(hmfsr_batch_plan plan, int streams);
+
+/* Autotuner: times the batch on the given buffers for 8 candidates -- the persistent
+ * kernel with accumulation tiles 32x4 / 16x8, register budgets 64 / 80 and stage-major or
+ * wavefront queues, and the per-burst graph on 1, 2, 4 and 8 branches -- keeps the
+ * fastest in the plan and returns its time (ms) in *best_ms and every candidate's time
+ * in tune_log[8] (both nullable).  Overwrites the outputs. */
+hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *bursts_dev, float *const *motion_dev,
+                              float *const *rgb_dev, void *ws, size_t ws_bytes, void *stream, float *best_ms,
+                              float *tune_log);
+
+void hmfsr_batch_free(hmfsr_batch_plan plan);
+
 /* Human-readable name of a status code (static string). */
 const char *hmfsr_status_string(hmfsr_status s);
 

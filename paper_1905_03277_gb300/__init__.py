@@ -302,3 +302,97 @@ class MergeFn(torch.autograd.Function):
         motion_c, rgb, den = ctx.saved_tensors
         gp, gm = merge_backward(ctx.burst, motion_c, ctx.p, rgb, den, grad_rgb, ctx.scale, ctx.ref)
         return gp.to(ctx.theta_device), gm, None, None, None, None
+
+
+class BatchPlan:
+    """A ragged batch of bursts aligned and merged by one persistent, graph-captured
+    launch (hmfsr_batch_*).  `shapes`: list of (n_frames, height, width); `params`,
+    `scales`, `refs`: per burst (or one value for all)."""
+
+    def __init__(self, shapes, params=None, scales=(1, 1), refs=0, align_params: AlignParams | None = None,
+                 white_level: int = 4095):
+        L = _lib.load()
+        nb = len(shapes)
+        params = params if isinstance(params, (list, tuple)) else [params or MergeParams()] * nb
+        scales = scales if (isinstance(scales, (list, tuple)) and isinstance(scales[0], (list, tuple))) else [scales] * nb
+        refs = refs if isinstance(refs, (list, tuple)) else [refs] * nb
+        ap = align_params or AlignParams()
+        self.shapes, self.scales = [tuple(s) for s in shapes], [tuple(s) for s in scales]
+        self._descs = (_lib.BurstDesc * nb)(*[_lib.BurstDesc(n, h, w, w, r, 0, white_level, 0)
+                                             for (n, h, w), r in zip(shapes, refs)])
+        self._mp = (_lib.MergeParamsC * nb)(*[p.c() for p in params])
+        self._ap = (_lib.AlignParamsC * nb)(*[ap.c() for _ in range(nb)])
+        self._num = (ctypes.c_int * nb)(*[s[0] for s in scales])
+        self._den = (ctypes.c_int * nb)(*[s[1] for s in scales])
+        h = ctypes.c_void_p()
+        _lib.check(L.hmfsr_batch_plan_create(self._descs, nb, self._mp, self._ap, self._num, self._den,
+                                             ctypes.byref(h)), "hmfsr_batch_plan_create")
+        self._h = h
+        self._L = L
+        self.n = nb
+        self.ws_bytes = int(L.hmfsr_batch_workspace_size(h))
+        self.ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.hmfsr_batch_free(h)
+            self._h = None
+
+    def outputs(self, device):
+        return [torch.empty((3,) + out_size(h, w, sc), dtype=torch.float32, device=device)
+                for (n, h, w), sc in zip(self.shapes, self.scales)]
+
+    def _arrays(self, bursts, rgbs, motions):
+        VP = ctypes.c_void_p * self.n
+        b = VP(*[t.data_ptr() for t in bursts])
+        r = VP(*[t.data_ptr() for t in rgbs])
+        m = VP(*[t.data_ptr() for t in motions]) if motions is not None else None
+        return b, m, r
+
+    def _workspace(self, device):
+        if self.ws is None or self.ws.device != device:
+            buf = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=device)
+            off = (-buf.data_ptr()) % 256
+            self._ws_buf, self.ws = buf, buf[off:off + self.ws_bytes]
+        return self.ws
+
+    def run(self, bursts, rgbs, motions=None, stream=None, wait: bool = False):
+        """Enqueue the whole batch; with `wait`, synchronise and raise on a device error."""
+        dev = bursts[0].device
+        ws = self._workspace(dev)
+        b, m, r = self._arrays(bursts, rgbs, motions)
+        st = _stream(dev, stream)
+        _lib.check(self._L.hmfsr_batch_run(self._h, b, m, r, _ptr(ws), ws.numel(), st), "hmfsr_batch_run")
+        if wait:
+            self.wait(stream)
+        return rgbs
+
+    def wait(self, stream=None) -> int:
+        st = self._L.hmfsr_batch_wait(self._h, _ptr(self.ws), _stream(self.ws.device, stream))
+        _lib.check(st, "batch")
+        return st
+
+    def configure(self, merge_tile_w: int = 32, ctas_per_sm: int = 0, regs_variant: int = 1, queue_order: int = 0,
+                  spin_limit: int = 1 << 22, inject_stall: bool = False):
+        _lib.check(self._L.hmfsr_batch_configure(self._h, merge_tile_w, ctas_per_sm, regs_variant, queue_order,
+                                                 spin_limit, int(inject_stall)), "hmfsr_batch_configure")
+
+    TUNE_CANDIDATES = ("persistent 32x4 64reg", "persistent 16x8 64reg", "persistent 32x4 80reg",
+                       "persistent 32x4 64reg wavefront", "graph 1 branch", "graph 2 branches", "graph 4 branches",
+                       "graph 8 branches")
+
+    def set_mode(self, streams: int):
+        """0: the one persistent kernel; k > 0: graph of per-burst kernels on k branches."""
+        _lib.check(self._L.hmfsr_batch_set_mode(self._h, streams), "hmfsr_batch_set_mode")
+
+    def tune(self, bursts, rgbs, motions=None, stream=None):
+        """Autotune on these buffers; returns (best ms, {candidate: ms})."""
+        dev = bursts[0].device
+        ws = self._workspace(dev)
+        b, m, r = self._arrays(bursts, rgbs, motions)
+        best = ctypes.c_float()
+        log = (ctypes.c_float * 8)()
+        _lib.check(self._L.hmfsr_batch_tune(self._h, b, m, r, _ptr(ws), ws.numel(), _stream(dev, stream),
+                                            ctypes.byref(best), log), "hmfsr_batch_tune")
+        return float(best.value), dict(zip(self.TUNE_CANDIDATES, [float(x) for x in log]))

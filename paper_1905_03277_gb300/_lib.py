@@ -12,9 +12,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libhmfsr.so")
-SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "merge_static.cu")
+SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+# -fmad=false: no automatic FMA contraction, so a device function gives the same bits in
+# every kernel it is inlined into (fused multiply-adds are written out with fmaf)
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
 
 def _nvcc() -> str:
@@ -25,7 +27,8 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "hmfsr_internal.cuh"), os.path.join(INCLUDE, "hmfsr.h")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return files
 
 
@@ -79,8 +82,9 @@ class MergeParamsC(ctypes.Structure):
 
 OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD = 0, 1, 2, 3
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
-           "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_status_string",
-           "hmfsr_version")
+           "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
+           "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_configure",
+           "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
 
@@ -112,6 +116,23 @@ def load(path: str | None = None):
     L.hmfsr_merge_backward.restype = ci
     L.hmfsr_merge_static.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp]
     L.hmfsr_merge_static.restype = ci
+    pp = P(vp)
+    L.hmfsr_batch_plan_create.argtypes = [P(BurstDesc), ci, P(MergeParamsC), P(AlignParamsC), P(ci), P(ci), pp]
+    L.hmfsr_batch_plan_create.restype = ci
+    L.hmfsr_batch_workspace_size.argtypes = [vp]
+    L.hmfsr_batch_workspace_size.restype = sz
+    L.hmfsr_batch_run.argtypes = [vp, pp, pp, pp, vp, sz, vp]
+    L.hmfsr_batch_run.restype = ci
+    L.hmfsr_batch_wait.argtypes = [vp, vp, vp]
+    L.hmfsr_batch_wait.restype = ci
+    L.hmfsr_batch_configure.argtypes = [vp, ci, ci, ci, ci, ci, ci]
+    L.hmfsr_batch_configure.restype = ci
+    L.hmfsr_batch_tune.argtypes = [vp, pp, pp, pp, vp, sz, vp, P(ctypes.c_float), P(ctypes.c_float)]
+    L.hmfsr_batch_set_mode.argtypes = [vp, ci]
+    L.hmfsr_batch_set_mode.restype = ci
+    L.hmfsr_batch_tune.restype = ci
+    L.hmfsr_batch_free.argtypes = [vp]
+    L.hmfsr_batch_free.restype = None
     L.hmfsr_status_string.argtypes = [ci]
     L.hmfsr_status_string.restype = ctypes.c_char_p
     L.hmfsr_version.argtypes = []

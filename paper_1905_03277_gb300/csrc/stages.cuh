@@ -1,0 +1,607 @@
+// Per-item bodies of every stage of the path (alignment, merge preparation, merge),
+// shared by the per-burst kernels and the batched persistent kernel so that both run
+// exactly the same arithmetic.  Each function handles the work of one thread (or, where
+// stated, one warp or one 32 x 4 block) given its decoded indices.
+#pragma once
+
+#include "hmfsr_internal.cuh"
+
+namespace hmfsr {
+namespace stage {
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+constexpr float kBig = 1.0e30f;
+
+// ======================================================================================
+// alignment (Sec. 3.2)
+// ======================================================================================
+// Level 0 = half-res luminance Lq: sum of the four Bayer samples of each quad (Sec. 5.1.2).
+__device__ __forceinline__ void luma0(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
+                                      uint16_t *__restrict__ out, int u, int v, int f) {
+    if (u >= wh) return;
+    const uint16_t *r0 = burst + ((size_t)f * h + 2 * v) * pitch + 2 * u;
+    uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
+    uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch));
+    uint32_t s = (a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16);
+    out[((size_t)f * hh + v) * wh + u] = (uint16_t)s;
+}
+
+// Next level: integer floor mean of f x f blocks.
+__device__ __forceinline__ void down(const uint16_t *__restrict__ src, int sh, int sw, uint16_t *__restrict__ dst,
+                                     int dh, int dw, int fct, int x, int y, int f) {
+    if (x >= dw) return;
+    const uint16_t *p = src + (size_t)f * sh * sw + (size_t)(y * fct) * sw + x * fct;
+    uint32_t s = 0;
+    for (int j = 0; j < fct; ++j)
+        for (int i = 0; i < fct; ++i) s += p[(size_t)j * sw + i];
+    dst[((size_t)f * dh + y) * dw + x] = (uint16_t)(s / (uint32_t)(fct * fct));
+}
+
+constexpr int kMaxRad = 7;
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One thread per tile of one level: exhaustive integer SSD over offsets |d| <= RAD
+// around the candidate (the parent's vector times the level factor).  For each dy the
+// thread streams the tile's rows (L1-cached reads, clamped at the border) and keeps the
+// 2 RAD + 1 candidate sums of that row of offsets in registers.  Ties: smallest SSD,
+// then smallest |dx| + |dy|, then smaller dy, then smaller dx -- one 64-bit key whose
+// minimum decides.
+template <int T, int RAD>
+__device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                    const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                    int2 *__restrict__ vec, int tile, int f) {
+    constexpr int kW = 2 * RAD + 1;
+    if (tile >= lty * ltx) return;
+    const int ty = tile / ltx, tx = tile - ty * ltx;
+    int2 *out = vec + (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        *out = make_int2(0, 0);
+        return;
+    }
+    int cx = 0, cy = 0;
+    if (parent) {  // level factor 1 << fsh
+        const int px = min(((tx * T + T / 2) >> fsh) / T, ptx - 1);
+        const int py = min(((ty * T + T / 2) >> fsh) / T, pty - 1);
+        const int2 pv = __ldg(parent + (size_t)f * pty * ptx + (size_t)py * ptx + px);
+        cx = pv.x << fsh;
+        cy = pv.y << fsh;
+    }
+    const uint16_t *R = img + (size_t)ref * lh * lw;
+    const uint16_t *A = img + (size_t)f * lh * lw;
+    const int x0 = tx * T, y0 = ty * T;
+    unsigned long long best = ~0ull;
+    for (int dy = -RAD; dy <= RAD; ++dy) {
+        unsigned long long acc[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) acc[k] = 0;
+        for (int j = 0; j < T; ++j) {
+            const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
+            const uint16_t *arow = A + (size_t)clampi(y0 + j + cy + dy, 0, lh - 1) * lw;
+            int rv[T], av[T + 2 * RAD];
+#pragma unroll
+            for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
+#pragma unroll
+            for (int i = 0; i < T + 2 * RAD; ++i) av[i] = __ldg(arow + clampi(x0 + cx - RAD + i, 0, lw - 1));
+#pragma unroll
+            for (int k = 0; k < kW; ++k) {
+#pragma unroll
+                for (int i0 = 0; i0 < T; i0 += 8) {
+                    unsigned int part = 0;  // 8 squared 14-bit differences fit 32 bits
+#pragma unroll
+                    for (int i = i0; i < i0 + 8 && i < T; ++i) {
+                        const int d = rv[i] - av[i + k];
+                        part += (unsigned int)(d * d);
+                    }
+                    acc[k] += part;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            const int dx = k - RAD;
+            const unsigned long long key = (acc[k] << 12) | ((unsigned long long)(abs(dx) + abs(dy)) << 8) |
+                                           ((unsigned long long)(dy + 7) << 4) | (unsigned long long)(dx + 7);
+            best = key < best ? key : best;
+        }
+    }
+    const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
+    *out = make_int2(cx + bdx, cy + bdy);
+}
+
+// Lucas-Kanade refinement (Sec. 3.2) of one level-0 tile per warp, on I = Lq / 4.  Each
+// lane owns pixels lane + 32 m of the tile.  Gradients of the base frame by central
+// differences around the clamped pixel; H = sum g g^T is summed exactly in integers, so
+// the conditioning guard (tr H == 0 or det H <= 1e-9 tr(H)^2) is an exact 128-bit integer
+// test; each iteration accumulates sum g r in FP32 (warp shuffles) and solves the 2x2
+// system.
+template <int T>
+__device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                   const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
+                                   int32_t *__restrict__ motion_int, int warp, int lane, int f) {
+    constexpr int t = T, npx = T * T, nper = (npx + 31) / 32;
+    if (warp >= lty * ltx) return;
+    const int ty = warp / ltx, tx = warp % ltx;
+    const size_t o = (size_t)f * lty * ltx + warp;
+    if (f == ref) {
+        if (lane == 0) {
+            motion[2 * o] = 0.f;
+            motion[2 * o + 1] = 0.f;
+            if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+        }
+        return;
+    }
+    const uint16_t *R = L0 + (size_t)ref * lh * lw;
+    const uint16_t *A = L0 + (size_t)f * lh * lw;
+    const int2 u = vec0[o];
+    int gxs[nper], gys[nper], pxs[nper], pys[nper], rv[nper];
+    long long hxx = 0, hxy = 0, hyy = 0;
+#pragma unroll
+    for (int m = 0; m < nper; ++m) {
+        const int k = lane + 32 * m;
+        if (k >= npx) { gxs[m] = gys[m] = 0; pxs[m] = pys[m] = 0; rv[m] = 0; continue; }
+        const int x = min(tx * t + k % t, lw - 1), y = min(ty * t + k / t, lh - 1);
+        const uint16_t *row = R + (size_t)y * lw;
+        const int gx = (int)__ldg(row + min(x + 1, lw - 1)) - (int)__ldg(row + max(x - 1, 0));
+        const int gy = (int)__ldg(R + (size_t)min(y + 1, lh - 1) * lw + x) - (int)__ldg(R + (size_t)max(y - 1, 0) * lw + x);
+        gxs[m] = gx; gys[m] = gy; pxs[m] = x; pys[m] = y;
+        rv[m] = __ldg(row + x);
+        hxx += (long long)(gx * gx);
+        hxy += (long long)(gx * gy);
+        hyy += (long long)(gy * gy);
+    }
+    hxx = warp_sum_ll(hxx);
+    hxy = warp_sum_ll(hxy);
+    hyy = warp_sum_ll(hyy);
+    // conditioning guard, exact: skip when tr H == 0 or 10^9 det H <= tr(H)^2
+    const __int128 det_i = (__int128)hxx * hyy - (__int128)hxy * hxy;
+    const __int128 tr_i = (__int128)hxx + hyy;
+    const bool skip = (tr_i == 0) || ((__int128)1000000000 * det_i <= tr_i * tr_i);
+    float dx = 0.f, dy = 0.f;
+    if (!skip) {
+        // H in units of g = (Lq difference) / 8 is H_int / 64
+        const float Hxx = (float)hxx, Hxy = (float)hxy, Hyy = (float)hyy;
+        const float inv = 64.f / fmaf(Hxx, Hyy, -Hxy * Hxy);
+        for (int it = 0; it < iters; ++it) {
+            const float fdx = floorf(dx), fdy = floorf(dy);
+            const float ax = dx - fdx, ay = dy - fdy;
+            const int ox = u.x + (int)fdx, oy = u.y + (int)fdy;
+            float bx = 0.f, by = 0.f;
+#pragma unroll
+            for (int m = 0; m < nper; ++m) {
+                if (lane + 32 * m >= npx) continue;
+                const int ix = pxs[m] + ox, iy = pys[m] + oy;
+                const int x0 = clampi(ix, 0, lw - 1), x1 = clampi(ix + 1, 0, lw - 1);
+                const uint16_t *a0 = A + (size_t)clampi(iy, 0, lh - 1) * lw;
+                const uint16_t *a1 = A + (size_t)clampi(iy + 1, 0, lh - 1) * lw;
+                const float i00 = __ldg(a0 + x0), i10 = __ldg(a0 + x1), i01 = __ldg(a1 + x0), i11 = __ldg(a1 + x1);
+                const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
+                const float ia = fmaf(ay, bot, (1.f - ay) * top);
+                const float r = (ia - (float)rv[m]) * 0.25f;
+                bx = fmaf((float)gxs[m] * 0.125f, r, bx);
+                by = fmaf((float)gys[m] * 0.125f, r, by);
+            }
+            bx = warp_sum_f(bx);
+            by = warp_sum_f(by);
+            const float sx = -(Hyy * bx - Hxy * by) * inv;
+            const float sy = -(Hxx * by - Hxy * bx) * inv;
+            dx = fminf(fmaxf(dx + sx, -1.f), 1.f);
+            dy = fminf(fmaxf(dy + sy, -1.f), 1.f);
+        }
+    }
+    if (lane == 0) {
+        motion[2 * o] = 2.f * ((float)u.x + dx);
+        motion[2 * o + 1] = 2.f * ((float)u.y + dy);
+        if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+    }
+}
+
+// ======================================================================================
+// merge preparation (Sec. 5.1.2, 5.2)
+// ======================================================================================
+// --------------------------------------------------------------------------------------
+// guide image + luminance (Sec. 5.1.2, Sec. 5.2.2): one texel per Bayer quad
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void guide_px(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
+                                         ushort4 *__restrict__ guide, int u, int v, int f) {
+    if (u >= wh) return;
+    const uint16_t *r0 = burst + ((size_t)f * h + 2 * v) * pitch + 2 * u;
+    uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
+    uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch));
+    uint32_t R = a & 0xffffu, G1 = a >> 16, G2 = b & 0xffffu, B = b >> 16;
+    guide[((size_t)f * hh + v) * wh + u] = make_ushort4((unsigned short)R, (unsigned short)(G1 + G2),
+                                                        (unsigned short)B, (unsigned short)(R + G1 + G2 + B));
+}
+
+// --------------------------------------------------------------------------------------
+// 3x3 guide sums of every frame; for the base frame also the noise-corrected statistics
+// that do not depend on the other frame (Eq. 6, closed-form noise model)
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void box_px(const ushort4 *__restrict__ guide, int hh, int wh, int ref, const MergeConsts &c,
+                                       int wl, uint2 *__restrict__ s1, float4 *__restrict__ base_stats, int u, int v, int f) {
+    if (u >= wh) return;
+    const ushort4 *G = guide + (size_t)f * hh * wh;
+    uint32_t sr = 0, sg = 0, sb = 0;
+    uint32_t qr = 0, qg = 0, qb = 0;
+    for (int j = -1; j <= 1; ++j) {
+        int vv = clampi(v + j, 0, hh - 1);
+        for (int i = -1; i <= 1; ++i) {
+            ushort4 q = G[(size_t)vv * wh + clampi(u + i, 0, wh - 1)];
+            sr += q.x; sg += q.y; sb += q.z;
+            qr += (uint32_t)q.x * q.x; qg += (uint32_t)q.y * q.y; qb += (uint32_t)q.z * q.z;
+        }
+    }
+    size_t idx = (size_t)v * wh + u;
+    s1[(size_t)f * hh * wh + idx] = make_uint2(sr | (sb << 16), sg);
+    if (f != ref) return;
+    const uint32_t S1[3] = {sr, sg, sb}, S2[3] = {qr, qg, qb};
+    float sig2 = 0.f, dmd2[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        // green guide = (G1 + G2) / 2
+        long long num = 9LL * (long long)S2[ch] - (long long)S1[ch] * (long long)S1[ch];
+        const float igs = (ch == 1) ? 0.5f : 1.f;
+        float var_ms = fmaxf((float)num * (igs * igs * (1.f / 81.f)), 0.f);
+        float mu = (float)S1[ch] * (igs * (1.f / 9.f));
+        float var_md = fmaxf(fmaf(c.noise_a, fminf(fmaxf(mu, 0.f), (float)wl), c.noise_b) * igs, 0.f);
+        sig2 += fmaxf(var_ms, var_md);
+        dmd2[ch] = var_md * (2.f / 9.f);
+    }
+    float eps = 1e-12f * (float)wl * (float)wl;
+    base_stats[idx] = make_float4(fmaxf(sig2, eps), dmd2[0], dmd2[1], dmd2[2]);
+}
+
+// --------------------------------------------------------------------------------------
+// structure tensor -> kernel covariance (Eq. 3, Eq. 4, supplement S.1)
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ int lq_at(const ushort4 *G, int hh, int wh, int u, int v) {
+    return G[(size_t)clampi(v, 0, hh - 1) * wh + clampi(u, 0, wh - 1)].w;
+}
+
+__device__ __forceinline__ void cov_px(const ushort4 *__restrict__ guide, int hh, int wh, const MergeConsts &c, int wl,
+                                       float4 *__restrict__ kern, int u, int v, int f) {
+    if (u >= wh) return;
+    const ushort4 *G = guide + (size_t)f * hh * wh;
+    // four 2x2 sub-squares of the 3x3 window, forward differences, exact integer tensor
+    int L[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) L[j][i] = lq_at(G, hh, wh, u - 1 + i, v - 1 + j);
+    long long ta = 0, tb = 0, tc = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int gx = (L[j][i + 1] - L[j][i]) + (L[j + 1][i + 1] - L[j + 1][i]);
+            int gy = (L[j + 1][i] - L[j][i]) + (L[j + 1][i + 1] - L[j][i + 1]);
+            ta += (long long)gx * gx;
+            tb += (long long)gx * gy;
+            tc += (long long)gy * gy;
+        }
+    // eigen-analysis: lambda1 = (tr + r)/2, dominant direction at angle theta with
+    // cos 2theta = (a-c)/r, sin 2theta = 2b/r (theta = 0 when the tensor is isotropic)
+    float tr = (float)(ta + tc);
+    float amc = (float)(ta - tc), b2 = 2.f * (float)tb;
+    float r = fast_sqrt(fmaf(amc, amc, b2 * b2));
+    float cs = 1.f, sn = 0.f;
+    if (!(ta == tc && tb == 0)) { const float ir = __fdividef(1.f, r); cs = amc * ir; sn = b2 * ir; }
+    float l1 = 0.5f * (tr + r);
+    float A = (ta + tc == 0) ? 1.f : 1.f + fast_sqrt(__fdividef(r, tr));
+    // lambda in units of luminance normalised to [0,1]: sqrt(l1_norm) = sqrt(l1) / (16 WL)
+    float D = fminf(fmaxf(fmaf(-fast_sqrt(l1), __fdividef(1.f, 16.f * (float)wl * c.d_tr), 1.f) + c.d_th, 0.f), 1.f);
+    float kh_al = c.k_detail * (c.k_stretch * A);
+    float kh_ac = __fdividef(c.k_detail, c.k_shrink * A);
+    float kd = c.k_detail * c.k_denoise;
+    float s_al = fmaf(1.f - D, kh_al, D * kd);   // standard deviations before squaring
+    float s_ac = fmaf(1.f - D, kh_ac, D * kd);
+    float k_al = s_al * s_al, k_ac = s_ac * s_ac;
+    // half-angle unit vector e1 = (cos theta, sin theta), without cancellation
+    float e1x, e1y;
+    if (cs >= 0.f) { e1x = fast_sqrt(fmaf(0.5f, cs, 0.5f)); e1y = __fdividef(sn, 2.f * e1x); }
+    else { e1y = fast_sqrt(fmaf(-0.5f, cs, 0.5f)); e1x = __fdividef(sn, 2.f * e1y); }
+    // Omega = k_across e1 e1^T + k_along e2 e2^T (stretch along the edge, e2)
+    //       = min I + |k_along - k_across| u u^T with u = e2 if k_along >= k_across else e1
+    float dh = (1.f - D) * (kh_al - kh_ac) * (s_al + s_ac);  // k_along - k_across, no cancellation
+    float4 out;
+    if (dh >= 0.f) out = make_float4(k_ac, dh, -e1y, e1x);
+    else out = make_float4(k_al, -dh, e1x, e1y);
+    kern[((size_t)f * hh + v) * wh + u] = out;
+}
+
+// --------------------------------------------------------------------------------------
+// motion prior (Eq. 7-8): robustness scale per tile, decided in exact FP64
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1,
+                                         float s2, float *__restrict__ s_tile, int i) {
+    if (i >= n * ty * tx) return;
+    int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
+    const float2 *mv = motion + (size_t)f * ty * tx;
+    // min / max are exact in FP32; the span, its length and the threshold are FP64
+    float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+    for (int j = -1; j <= 1; ++j)
+        for (int k = -1; k <= 1; ++k) {
+            int yy = y + j, xx = x + k;
+            if (yy < 0 || yy >= ty || xx < 0 || xx >= tx) continue;
+            float2 v = mv[(size_t)yy * tx + xx];
+            mnx = fminf(mnx, v.x); mxx = fmaxf(mxx, v.x);
+            mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
+        }
+    double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
+    double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
+    s_tile[i] = (M > (double)m_th) ? s1 : s2;
+}
+
+// --------------------------------------------------------------------------------------
+// robustness (Eq. 5, 6) on a 32x8 base tile with a 2-px halo, then the 5x5 minimum (Eq. 9)
+// --------------------------------------------------------------------------------------
+constexpr int kRobW = 32, kRobH = 4;
+
+// Rs: (kRobH + 4) x (kRobW + 4) floats of shared memory; every thread of the 32 x 4
+// block calls this with the same block coordinates (it synchronises the block).
+__device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
+                                          const float2 *__restrict__ motion, const float *__restrict__ s_tile,
+                                          const Geom &g, float t_thr, int frame, float *__restrict__ rhat,
+                                          float (*Rs)[kRobW + 4], int bx, int by, int tx, int ty) {
+    const int u0 = bx * kRobW - 2, v0 = by * kRobH - 2;
+    const size_t hw = (size_t)g.hh * g.wh;
+    const uint2 *S1b = s1 + (size_t)g.ref * hw;
+    const uint2 *S1n = s1 + (size_t)frame * hw;
+    const float2 *mvf = motion + (size_t)frame * g.ty * g.tx;
+    const float *stf = s_tile + (size_t)frame * g.ty * g.tx;
+    const int half_tile = g.tile / 2;
+    for (int k = ty * kRobW + tx; k < (kRobH + 4) * (kRobW + 4); k += kRobW * kRobH) {
+        int ly = k / (kRobW + 4), lx = k % (kRobW + 4);
+        int u = u0 + lx, v = v0 + ly;
+        float R = kBig;
+        if (u >= 0 && u < g.wh && v >= 0 && v < g.hh) {
+            int txi = min(u / half_tile, g.tx - 1), tyi = min(v / half_tile, g.ty - 1);
+            float2 mv = mvf[(size_t)tyi * g.tx + txi];
+            float s = stf[(size_t)tyi * g.tx + txi];
+            // aligned position (u, v) + v/2 split into an exact integer part and fraction
+            float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
+            float flx = floorf(hx), fly = floorf(hy);
+            float fx = hx - flx, fy = hy - fly;
+            int ix = u + (int)flx, iy = v + (int)fly;
+            int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
+            int y0 = clampi(iy, 0, g.hh - 1), y1 = clampi(iy + 1, 0, g.hh - 1);
+            uint2 sb = S1b[(size_t)v * g.wh + u];
+            uint2 n00 = S1n[(size_t)y0 * g.wh + x0], n10 = S1n[(size_t)y0 * g.wh + x1];
+            uint2 n01 = S1n[(size_t)y1 * g.wh + x0], n11 = S1n[(size_t)y1 * g.wh + x1];
+            float b00 = (1.f - fx) * (1.f - fy), b10 = fx * (1.f - fy), b01 = (1.f - fx) * fy, b11 = fx * fy;
+            // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9 (exact differences)
+            int rb = sb.x & 0xffff, bb = sb.x >> 16, gb = sb.y;
+            float dR = fmaf(b00, (float)(rb - (int)(n00.x & 0xffff)), fmaf(b10, (float)(rb - (int)(n10.x & 0xffff)),
+                       fmaf(b01, (float)(rb - (int)(n01.x & 0xffff)), b11 * (float)(rb - (int)(n11.x & 0xffff)))));
+            float dB = fmaf(b00, (float)(bb - (int)(n00.x >> 16)), fmaf(b10, (float)(bb - (int)(n10.x >> 16)),
+                       fmaf(b01, (float)(bb - (int)(n01.x >> 16)), b11 * (float)(bb - (int)(n11.x >> 16)))));
+            float dG = fmaf(b00, (float)(gb - (int)n00.y), fmaf(b10, (float)(gb - (int)n10.y),
+                       fmaf(b01, (float)(gb - (int)n01.y), b11 * (float)(gb - (int)n11.y))));
+            dR *= (1.f / 9.f);
+            dB *= (1.f / 9.f);
+            dG *= (1.f / 18.f);
+            float4 st = base_stats[(size_t)v * g.wh + u];
+            float dd = 0.f;
+            {
+                float d2 = dR * dR, den = d2 + st.y;
+                float d = den > 0.f ? __fdividef(dR * d2, den) : 0.f;  // Wiener shrinkage (Eq. 6)
+                dd = fmaf(d, d, dd);
+            }
+            {
+                float d2 = dG * dG, den = d2 + st.z;
+                float d = den > 0.f ? __fdividef(dG * d2, den) : 0.f;
+                dd = fmaf(d, d, dd);
+            }
+            {
+                float d2 = dB * dB, den = d2 + st.w;
+                float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
+                dd = fmaf(d, d, dd);
+            }
+            R = fminf(fmaxf(fmaf(s, expf(-__fdividef(dd, st.x)), -t_thr), 0.f), 1.f);  // Eq. 5
+        }
+        Rs[ly][lx] = R;
+    }
+    __syncthreads();
+    int u = bx * kRobW + tx, v = by * kRobH + ty;
+    if (u >= g.wh || v >= g.hh) return;
+    float m = kBig;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) m = fminf(m, Rs[ty + j][tx + i]);
+    rhat[(size_t)frame * hw + (size_t)v * g.wh + u] = m;
+}
+
+// ======================================================================================
+// accumulation (Eq. 1-2)
+// ======================================================================================
+// --------------------------------------------------------------------------------------
+// accumulation (Eq. 1-2): one thread per output pixel, all frames, registers only
+// --------------------------------------------------------------------------------------
+constexpr int kMergeW = 32, kMergeH = 4;
+
+// exact uint16 -> float on the FMA pipe (v < 2^23)
+__device__ __forceinline__ float u16f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
+
+// The 3x3 Bayer neighbourhood of frame sample rows around (kx, ky): raw values and the
+// weight exponents q' (log2 units) of the quadratic form; samples outside the frame get
+// q' = +inf.  kBorder selects the checked variant.
+template <bool kBorder>
+__device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int pitch, int h, int w, int kx, int ky,
+                                          const float (&Ax)[3], const float (&Ex)[3], const float (&Cy)[3],
+                                          const float (&dys)[3], float (&q)[3][3], float (&rv)[3][3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int yy = ky - 1 + j;
+        const bool yok = !kBorder || ((unsigned)yy < (unsigned)h);
+        const uint16_t *row = fr + (size_t)(kBorder ? clampi(yy, 0, h - 1) : yy) * pitch;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int xx = kx - 1 + i;
+            rv[j][i] = u16f(__ldg(row + (kBorder ? clampi(xx, 0, w - 1) : xx)));
+            const float qq = fmaf(Ex[i], dys[j], Ax[i] + Cy[j]);
+            if (kBorder) q[j][i] = (yok && (unsigned)xx < (unsigned)w) ? qq : INFINITY;
+            else q[j][i] = qq;
+        }
+    }
+}
+
+// SN/SD > 0: compile-time output scale SN/SD (constant divisors); 0: runtime snum/sden.
+template <bool kDen, int SN, int SD>
+__device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, const float2 *__restrict__ motion,
+                                         const Geom &g, const float4 *__restrict__ kern,
+                                         const float *__restrict__ rhat_planes, int snum_rt, int sden_rt, int ho, int wo,
+                                         float *__restrict__ rgb, float *__restrict__ den_out, int X, int Y) {
+    if (X >= wo || Y >= ho) return;
+    const int snum = SN > 0 ? SN : snum_rt, sden = SD > 0 ? SD : sden_rt;
+    const int Q = 2 * snum, Q2 = 4 * snum;
+    const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
+    // output pixel centre x0 = Px / Q in raw px (exact rational)
+    const int Px = 2 * sden * X + sden - snum, Py = 2 * sden * Y + sden - snum;
+    const int txi = min(max(floor_div(Px, Q * g.tile), 0), g.tx - 1);
+    const int tyi = min(max(floor_div(Py, Q * g.tile), 0), g.ty - 1);
+    const size_t hw = (size_t)g.hh * g.wh;
+    // Rhat is sampled on the base half-res grid at (x0 - 1/2)/2 = (P - num) / 2Q
+    const int rx = floor_div(Px - snum, Q2), ry = floor_div(Py - snum, Q2);
+    const float rfx = (float)(Px - snum - rx * Q2) * inv2Q, rfy = (float)(Py - snum - ry * Q2) * inv2Q;
+    const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
+    const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
+    const int r00 = ry0 * g.wh + rx0, r10 = ry0 * g.wh + rx1, r01 = ry1 * g.wh + rx0, r11 = ry1 * g.wh + rx1;
+    const float rw00 = (1.f - rfx) * (1.f - rfy), rw10 = rfx * (1.f - rfy), rw01 = (1.f - rfx) * rfy, rw11 = rfx * rfy;
+
+    float numR = 0.f, numG = 0.f, numB = 0.f, denR = 0.f, denG = 0.f, denB = 0.f;
+    float mR = kBig, mG = kBig, mB = kBig;  // per-channel exponent shifts (log2 units)
+
+    for (int it = 0; it < g.n; ++it) {
+        const int f = (it == 0) ? g.ref : (it <= g.ref ? it - 1 : it);
+        float vx = 0.f, vy = 0.f, rh = 1.f;
+        if (f != g.ref) {
+            const float *Rp = rhat_planes + (size_t)f * hw;
+            rh = fmaf(rw00, __ldg(Rp + r00), fmaf(rw10, __ldg(Rp + r10), fmaf(rw01, __ldg(Rp + r01), rw11 * __ldg(Rp + r11))));
+            if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
+            const float2 mv = __ldg(motion + ((size_t)f * g.ty + tyi) * g.tx + txi);
+            vx = mv.x;
+            vy = mv.y;
+        }
+        // window centre k = round(x0 + v) (ties up), exactly
+        const int FX = floor_mul(Q, vx), FY = floor_mul(Q, vy);
+        const int kx = floor_div(Px + snum + FX, Q), ky = floor_div(Py + snum + FY, Q);
+        // offset of the centre sample from x0 + v: (kx Q - Px - Q v) / Q
+        const float dx0 = fmaf(-fQ, vx, (float)(kx * Q - Px)) * invQ;
+        const float dy0 = fmaf(-fQ, vy, (float)(ky * Q - Py)) * invQ;
+        // Omega is sampled on frame f's half-res grid at (x0 + v - 1/2)/2
+        const float zx = fmaf(fQ, vx, -(float)FX), zy = fmaf(fQ, vy, -(float)FY);
+        const int gx = Px - snum + FX, gy = Py - snum + FY;
+        const int ox = floor_div(gx, Q2), oy = floor_div(gy, Q2);
+        const float ofx = ((float)(gx - ox * Q2) + zx) * inv2Q, ofy = ((float)(gy - oy * Q2) + zy) * inv2Q;
+        const int ox0 = clampi(ox, 0, g.wh - 1), ox1 = clampi(ox + 1, 0, g.wh - 1);
+        const int oy0 = clampi(oy, 0, g.hh - 1) * g.wh, oy1 = clampi(oy + 1, 0, g.hh - 1) * g.wh;
+        const float4 *K = kern + (size_t)f * hw;
+        const float4 t0 = __ldg(K + oy0 + ox0), t1 = __ldg(K + oy0 + ox1);
+        const float4 t2 = __ldg(K + oy1 + ox0), t3 = __ldg(K + oy1 + ox1);
+        const float b0 = (1.f - ofx) * (1.f - ofy), b1 = ofx * (1.f - ofy), b2 = (1.f - ofx) * ofy, b3 = ofx * ofy;
+        // Omega = a I + M, M = sum_k g_k u_k u_k^T;  adj(Omega) = a I + sum_k g_k u_k^perp u_k^perp^T
+        // (the library is built without automatic FMA contraction; the fused
+        // multiply-adds below are written out so the arithmetic is the same wherever this
+        // function is inlined)
+        const float a = fmaf(b0, t0.x, fmaf(b1, t1.x, fmaf(b2, t2.x, b3 * t3.x)));
+        const float g0 = b0 * t0.y, g1 = b1 * t1.y, g2 = b2 * t2.y, g3 = b3 * t3.y;
+        const float gw0 = g0 * t0.w, gw1 = g1 * t1.w, gw2 = g2 * t2.w, gw3 = g3 * t3.w;
+        const float gz0 = g0 * t0.z, gz1 = g1 * t1.z, gz2 = g2 * t2.z, gz3 = g3 * t3.z;
+        const float Nxx = fmaf(gw0, t0.w, fmaf(gw1, t1.w, fmaf(gw2, t2.w, gw3 * t3.w)));
+        const float Nyy = fmaf(gz0, t0.z, fmaf(gz1, t1.z, fmaf(gz2, t2.z, gz3 * t3.z)));
+        const float Nxy = -fmaf(gw0, t0.z, fmaf(gw1, t1.z, fmaf(gw2, t2.z, gw3 * t3.z)));
+        const float Gs = (g0 + g1) + (g2 + g3);
+        // det(M) = sum_{k<l} g_k g_l (u_k x u_l)^2 (Cauchy-Binet: all terms >= 0)
+        const float c01 = fmaf(t0.z, t1.w, -(t0.w * t1.z)), c02 = fmaf(t0.z, t2.w, -(t0.w * t2.z));
+        const float c03 = fmaf(t0.z, t3.w, -(t0.w * t3.z)), c12 = fmaf(t1.z, t2.w, -(t1.w * t2.z));
+        const float c13 = fmaf(t1.z, t3.w, -(t1.w * t3.z)), c23 = fmaf(t2.z, t3.w, -(t2.w * t3.z));
+        const float s0 = fmaf(g1 * c01, c01, fmaf(g2 * c02, c02, (g3 * c03) * c03));
+        const float s1 = fmaf(g2 * c12, c12, (g3 * c13) * c13);
+        const float detM = fmaf(g0, s0, fmaf(g1, s1, (g2 * g3) * (c23 * c23)));
+        const float det = fmaf(a, a + Gs, detM);
+        const float sc = __fdividef(kHalfLog2e, det);
+        // q'(d) = (d^T adj(Omega) d) / det * log2(e)/2: weight = 2^-q'
+        const float Bxx = (a + Nxx) * sc, Byy = (a + Nyy) * sc, Bxy2 = 2.f * Nxy * sc;
+        const float dxs[3] = {dx0 - 1.f, dx0, dx0 + 1.f};
+        const float dys[3] = {dy0 - 1.f, dy0, dy0 + 1.f};
+        float Ax[3], Ex[3], Cy[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            Ax[i] = Bxx * dxs[i] * dxs[i];
+            Ex[i] = Bxy2 * dxs[i];
+            Cy[i] = Byy * dys[i] * dys[i];
+        }
+        // the 3x3 Bayer neighbourhood; samples outside the frame are left out
+        const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
+        float q[3][3], rv[3][3];
+        if ((unsigned)(kx - 1) < (unsigned)(g.w - 2) && (unsigned)(ky - 1) < (unsigned)(g.h - 2))
+            gather3x3<false>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
+        else
+            gather3x3<true>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
+        // per-class minima: C = centre, H = (+-1, 0), V = (0, +-1), K = corners
+        const float qC = q[1][1];
+        const float mH = fminf(q[1][0], q[1][2]), mV = fminf(q[0][1], q[2][1]);
+        const float mK = fminf(fminf(q[0][0], q[0][2]), fminf(q[2][0], q[2][2]));
+        // CFA mapping: cg = centre is green; sw = centre row is odd
+        const bool cg = ((kx ^ ky) & 1) != 0, sw = (ky & 1) != 0;
+        const float f1 = cg ? mH : qC, f2 = cg ? mV : mK, fG = cg ? fminf(qC, mK) : fminf(mH, mV);
+        const float fR = sw ? f2 : f1, fB = sw ? f1 : f2;
+        if (fR < mR - 64.f || fG < mG - 64.f || fB < mB - 64.f) {
+            // move a channel's shift down to this frame's minimum (rare after the base frame)
+            if (fR < mR - 64.f) { const float s = fast_exp2(fR - mR); numR *= s; denR *= s; mR = fR; }
+            if (fG < mG - 64.f) { const float s = fast_exp2(fG - mG); numG *= s; denG *= s; mG = fG; }
+            if (fB < mB - 64.f) { const float s = fast_exp2(fB - mB); numB *= s; denB *= s; mB = fB; }
+        }
+        const float mS1 = sw ? mB : mR, mS2 = sw ? mR : mB;
+        const float sC = cg ? mG : mS1, sK = cg ? mG : mS2, sH = cg ? mS1 : mG, sV = cg ? mS2 : mG;
+        float w;
+        w = fast_exp2(sC - q[1][1]);
+        const float nC = w * rv[1][1], dC = w;
+        w = fast_exp2(sH - q[1][0]);
+        float nH = w * rv[1][0], dH = w;
+        w = fast_exp2(sH - q[1][2]);
+        nH = fmaf(w, rv[1][2], nH); dH += w;
+        w = fast_exp2(sV - q[0][1]);
+        float nV = w * rv[0][1], dV = w;
+        w = fast_exp2(sV - q[2][1]);
+        nV = fmaf(w, rv[2][1], nV); dV += w;
+        w = fast_exp2(sK - q[0][0]);
+        float nK = w * rv[0][0], dK = w;
+        w = fast_exp2(sK - q[0][2]);
+        nK = fmaf(w, rv[0][2], nK); dK += w;
+        w = fast_exp2(sK - q[2][0]);
+        nK = fmaf(w, rv[2][0], nK); dK += w;
+        w = fast_exp2(sK - q[2][2]);
+        nK = fmaf(w, rv[2][2], nK); dK += w;
+        const float n1 = cg ? nH : nC, n2 = cg ? nV : nK, nG = cg ? nC + nK : nH + nV;
+        const float d1 = cg ? dH : dC, d2 = cg ? dV : dK, dG = cg ? dC + dK : dH + dV;
+        numR = fmaf(rh, sw ? n2 : n1, numR);
+        denR = fmaf(rh, sw ? d2 : d1, denR);
+        numB = fmaf(rh, sw ? n1 : n2, numB);
+        denB = fmaf(rh, sw ? d1 : d2, denB);
+        numG = fmaf(rh, nG, numG);
+        denG = fmaf(rh, dG, denG);
+    }
+    const size_t po = (size_t)ho * wo, o = (size_t)Y * wo + X;
+    rgb[o] = numR / denR;
+    rgb[po + o] = numG / denG;
+    rgb[2 * po + o] = numB / denB;
+    if (kDen) {
+        den_out[o] = log2f(denR) - mR;
+        den_out[po + o] = log2f(denG) - mG;
+        den_out[2 * po + o] = log2f(denB) - mB;
+    }
+}
+
+}  // namespace stage
+}  // namespace hmfsr

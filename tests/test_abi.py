@@ -126,3 +126,17 @@ def test_load_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
     finally:
         _lib._lib = saved
+
+
+def test_batch_plan_validation_on_host(L):
+    # plan creation is host work only
+    p = hm.BatchPlan([(4, 64, 96), (3, 128, 128)], hm.MergeParams(), [(1, 1), (3, 2)], [0, 2])
+    assert p.ws_bytes > 0
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        hm.BatchPlan([(4, 63, 96)])                       # odd height
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        hm.BatchPlan([(4, 64, 96)], hm.MergeParams(tile=32))  # batches use tile 16
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        hm.BatchPlan([(4, 64, 96)], refs=4)                # ref out of range
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        p.configure(merge_tile_w=48)                       # must divide 128
