@@ -5,9 +5,9 @@
 namespace hmfsr {
 namespace {
 
-__global__ void k_luma0(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
+__global__ void k_luma0(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh,
                         uint16_t *__restrict__ out) {
-    stage::luma0(burst, h, w, pitch, hh, wh, out, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+    stage::luma0(burst, h, pitch, hh, wh, out, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
 __global__ void k_down(const uint16_t *__restrict__ src, int sh, int sw, uint16_t *__restrict__ dst, int dh, int dw,
@@ -21,6 +21,14 @@ __global__ void __launch_bounds__(64) k_ssd(const uint16_t *__restrict__ img, in
                                             int2 *__restrict__ vec) {
     stage::ssd<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, blockIdx.x * blockDim.x + threadIdx.x,
                        blockIdx.y);
+}
+
+template <int T>
+__global__ void k_lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                           const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
+                           int32_t *__restrict__ motion_int) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    stage::lk_group<T>(L0, lh, lw, lty, ltx, vec0, ref, iters, motion, motion_int, t / T, threadIdx.x & 31, blockIdx.y);
 }
 
 template <int T>
@@ -62,14 +70,18 @@ static void run_search(const Geom &g, const hmfsr_align_params &p, const AlignLe
         }
     }
     const int tiles0 = L.lty[0] * L.ltx[0];
-    k_lk<T><<<dim3(div_up(tiles0 * 32, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0], L.vec[0],
-                                                       g.ref, p.lk_iters, motion, motion_int);
+    if constexpr (T <= 8)
+        k_lk_group<T><<<dim3(div_up(tiles0 * T, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
+                                                                   L.vec[0], g.ref, p.lk_iters, motion, motion_int);
+    else
+        k_lk<T><<<dim3(div_up(tiles0 * 32, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
+                                                           L.vec[0], g.ref, p.lk_iters, motion, motion_int);
 }
 
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s) {
     const int n = g.n;
-    k_luma0<<<dim3(div_up(g.wh, 128), g.hh, n), 128, 0, s>>>(burst, g.h, g.w, g.pitch, g.hh, g.wh, L.img[0]);
+    k_luma0<<<dim3(div_up(g.wh, 4 * 128), g.hh, n), 128, 0, s>>>(burst, g.h, g.pitch, g.hh, g.wh, L.img[0]);
     for (int l = 1; l < L.n_levels; ++l)
         k_down<<<dim3(div_up(L.lw[l], 128), L.lh[l], n), 128, 0, s>>>(L.img[l - 1], L.lh[l - 1], L.lw[l - 1],
                                                                        L.img[l], L.lh[l], L.lw[l], kFactors[l - 1]);

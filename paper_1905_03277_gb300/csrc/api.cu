@@ -98,7 +98,6 @@ size_t carve_align(void *ws, const Geom &g, int tile, int n_levels_max, AlignLev
 size_t carve_merge(void *ws, const Geom &g, MergePlanes *P) {
     Carver c(ws);
     size_t hw = (size_t)g.hh * g.wh;
-    P->guide = c.take<ushort4>(g.n * hw);
     P->s1 = c.take<uint2>(g.n * hw);
     P->base_stats = c.take<float4>(hw);
     P->kern = c.take<float4>(g.n * hw);

@@ -25,14 +25,15 @@ namespace hmfsr {
 namespace {
 
 enum Stage {
-    S_LUMA = 0, S_GUIDE, S_DOWN1, S_BOX, S_DOWN2, S_COV, S_DOWN3, S_SSD3, S_SSD2, S_SSD1, S_SSD0, S_LK, S_STRENGTH,
-    S_ROB, S_MERGE, S_PHANTOM, S_COUNT
+    S_LUMA = 0, S_PREP, S_DOWN1, S_DOWN2, S_DOWN3, S_SSD3, S_SSD2, S_SSD1, S_SSD0, S_LK, S_STRENGTH, S_ROB, S_MERGE,
+    S_PHANTOM, S_COUNT
 };
 constexpr int kBatchThreads = 128;
 constexpr int kMaxDeps = 6;
 // queue order: every stage after the stages it depends on
-constexpr int kOrder[] = {S_LUMA, S_GUIDE, S_DOWN1, S_BOX, S_DOWN2, S_COV, S_DOWN3, S_SSD3, S_SSD2, S_SSD1, S_SSD0,
+constexpr int kOrder[] = {S_LUMA, S_PREP, S_DOWN1, S_DOWN2, S_DOWN3, S_SSD3, S_SSD2, S_SSD1, S_SSD0,
                           S_LK, S_STRENGTH, S_ROB, S_MERGE};
+constexpr int kLkTiles = kBatchThreads / 8;  // Lucas-Kanade tiles per sub-item (8 lanes per tile)
 
 struct BatchBurst {
     const uint16_t *burst;
@@ -67,11 +68,9 @@ __device__ __host__ inline Deps stage_deps(int s) {
         case S_SSD1: add(S_DOWN1); add(S_DOWN2); add(S_DOWN3); add(S_SSD2); add(S_SSD3); break;
         case S_SSD0: add(S_LUMA); add(S_DOWN3); add(S_SSD1); add(S_SSD2); add(S_SSD3); break;
         case S_LK: add(S_SSD0); break;
-        case S_BOX: add(S_GUIDE); break;
-        case S_COV: add(S_GUIDE); break;
         case S_STRENGTH: add(S_LK); break;
-        case S_ROB: add(S_BOX); add(S_STRENGTH); break;
-        case S_MERGE: add(S_COV); add(S_ROB); add(S_LK); add(S_PHANTOM); break;
+        case S_ROB: add(S_PREP); add(S_STRENGTH); break;
+        case S_MERGE: add(S_PREP); add(S_ROB); add(S_LK); add(S_PHANTOM); break;
         default: break;
     }
     return r;
@@ -91,9 +90,11 @@ __device__ __host__ inline int stage_level(int s) {
 // queue and dependency bookkeeping of an item is small next to its work
 __device__ __host__ inline int stage_k(int s) {
     switch (s) {
-        case S_LUMA: case S_GUIDE: case S_DOWN1: case S_DOWN2: case S_DOWN3: return 256;
-        case S_BOX: case S_COV: case S_ROB: return 128;
-        case S_LK: return 64;
+        case S_DOWN1: case S_DOWN2: case S_DOWN3: return 256;
+        case S_LUMA: return 64;
+        case S_PREP: return 16;
+        case S_ROB: return 4;
+        case S_LK: return 16;
         case S_MERGE: return 32;
         case S_STRENGTH: return 8;
         default: return 4;  // block matching: 128 tiles per sub-item
@@ -105,7 +106,8 @@ __device__ __host__ inline int stage_subitems(const BatchBurst &b, int s, int mw
     const Geom &g = b.g;
     const int nl = b.L.n_levels;
     switch (s) {
-        case S_LUMA: case S_GUIDE: case S_BOX: case S_COV: return div_up(g.wh, kBatchThreads) * g.hh * g.n;
+        case S_LUMA: return div_up(g.wh, 4 * kBatchThreads) * g.hh * g.n;
+        case S_PREP: return div_up(g.wh, stage::kPrepW) * div_up(g.hh, stage::kPrepH) * g.n;
         case S_DOWN1: case S_DOWN2: case S_DOWN3: {
             const int l = stage_level(s);
             return l < nl ? div_up(b.L.lw[l], kBatchThreads) * b.L.lh[l] * g.n : 0;
@@ -114,9 +116,9 @@ __device__ __host__ inline int stage_subitems(const BatchBurst &b, int s, int mw
             const int l = stage_level(s);
             return l < nl ? div_up(b.L.lty[l] * b.L.ltx[l], kBatchThreads) * g.n : 0;
         }
-        case S_LK: return div_up(b.L.lty[0] * b.L.ltx[0], kBatchThreads / 32) * g.n;
+        case S_LK: return div_up(b.L.lty[0] * b.L.ltx[0], kLkTiles) * g.n;
         case S_STRENGTH: return div_up(g.n * g.ty * g.tx, kBatchThreads);
-        case S_ROB: return div_up(g.wh, stage::kRobW) * div_up(g.hh, stage::kRobH) * (g.n - 1);
+        case S_ROB: return g.n > 1 ? div_up(g.wh, stage::kRobW) * div_up(g.hh, stage::kRobH) : 0;
         case S_MERGE: return div_up(b.wo, mw) * div_up(b.ho, mh);
         default: return 0;
     }
@@ -142,18 +144,26 @@ __device__ __forceinline__ void run_merge(const BatchBurst &b, int X, int Y) {
 }
 
 // one sub-item of one stage of burst b, by all 128 threads of the block
-__device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int tid, int mw, int mh,
-                                        float (*Rs)[stage::kRobW + 4]) {
+union BatchSmem {
+    stage::PrepSmem prep;
+    stage::RobSmem rob;
+};
+
+__device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int tid, int mw, int mh, BatchSmem &sm) {
     const Geom &g = b.g;
     const float2 *mv = reinterpret_cast<const float2 *>(b.motion);
     switch (s) {
-        case S_LUMA: case S_GUIDE: case S_BOX: case S_COV: {
-            const int nx = div_up(g.wh, kBatchThreads);
-            const int f = k / (nx * g.hh), r = k - f * nx * g.hh, v = r / nx, u = (r - v * nx) * kBatchThreads + tid;
-            if (s == S_LUMA) stage::luma0(b.burst, g.h, g.w, g.pitch, g.hh, g.wh, b.L.img[0], u, v, f);
-            else if (s == S_GUIDE) stage::guide_px(b.burst, g.h, g.w, g.pitch, g.hh, g.wh, b.P.guide, u, v, f);
-            else if (s == S_BOX) stage::box_px(b.P.guide, g.hh, g.wh, g.ref, b.c, g.wl, b.P.s1, b.P.base_stats, u, v, f);
-            else stage::cov_px(b.P.guide, g.hh, g.wh, b.c, g.wl, b.P.kern, u, v, f);
+        case S_LUMA: {
+            const int nx = div_up(g.wh, 4 * kBatchThreads);
+            const int f = k / (nx * g.hh), r = k - f * nx * g.hh, v = r / nx, u4 = (r - v * nx) * kBatchThreads + tid;
+            stage::luma0(b.burst, g.h, g.pitch, g.hh, g.wh, b.L.img[0], u4, v, f);
+            break;
+        }
+        case S_PREP: {
+            const int nx = div_up(g.wh, stage::kPrepW), ny = div_up(g.hh, stage::kPrepH);
+            const int f = k / (nx * ny), r = k - f * nx * ny, by = r / nx, bx = r - by * nx;
+            stage::prep_block(b.burst, g, b.c, b.P.s1, b.P.base_stats, b.P.kern, sm.prep, bx, by, f,
+                              tid % stage::kPrepW, tid / stage::kPrepW);
             break;
         }
         case S_DOWN1: case S_DOWN2: case S_DOWN3: {
@@ -178,20 +188,19 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
             break;
         }
         case S_LK: {
-            const int per = div_up(b.L.lty[0] * b.L.ltx[0], kBatchThreads / 32);
-            const int f = k / per, warp = (k - f * per) * (kBatchThreads / 32) + (tid >> 5);
-            stage::lk<8>(b.L.img[0], b.L.lh[0], b.L.lw[0], b.L.lty[0], b.L.ltx[0], b.L.vec[0], g.ref, b.lk_iters,
-                         b.motion, nullptr, warp, tid & 31, f);
+            const int per = div_up(b.L.lty[0] * b.L.ltx[0], kLkTiles);
+            const int f = k / per, tile = (k - f * per) * kLkTiles + tid / 8;
+            stage::lk_group<8>(b.L.img[0], b.L.lh[0], b.L.lw[0], b.L.lty[0], b.L.ltx[0], b.L.vec[0], g.ref,
+                               b.lk_iters, b.motion, nullptr, tile, tid & 31, f);
             break;
         }
         case S_STRENGTH:
             stage::strength(mv, g.n, g.ty, g.tx, b.c.m_th, b.c.s1, b.c.s2, b.P.s_tile, k * kBatchThreads + tid);
             break;
         case S_ROB: {
-            const int nx = div_up(g.wh, stage::kRobW), ny = div_up(g.hh, stage::kRobH);
-            const int fi = k / (nx * ny), r = k - fi * nx * ny, by = r / nx, bx = r - by * nx;
-            const int f = fi < g.ref ? fi : fi + 1;  // every frame but the base frame
-            stage::rob_block(b.P.s1, b.P.base_stats, mv, b.P.s_tile, g, b.c.t, f, b.P.rhat, Rs, bx, by,
+            const int nx = div_up(g.wh, stage::kRobW);
+            const int by = k / nx, bx = k - by * nx;
+            stage::rob_block(b.P.s1, b.P.base_stats, mv, b.P.s_tile, g, b.c.t, b.P.rhat, sm.rob, bx, by,
                              tid % stage::kRobW, tid / stage::kRobW);
             break;
         }
@@ -210,14 +219,13 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
 }
 
 // one queue item: stage_k(s) consecutive sub-items
-__device__ __forceinline__ void run_item(const BatchBurst &b, int s, int k, int tid, int mw, int mh,
-                                         float (*Rs)[stage::kRobW + 4]) {
+__device__ __forceinline__ void run_item(const BatchBurst &b, int s, int k, int tid, int mw, int mh, BatchSmem &sm) {
     const int K = stage_k(s), nsub = stage_subitems(b, s, mw, mh);
     for (int j = 0; j < K; ++j) {
         const int sub = k * K + j;
         if (sub >= nsub) break;
-        run_sub(b, s, sub, tid, mw, mh, Rs);
-        if (s == S_ROB) __syncthreads();  // the shared halo is reused by the next sub-item
+        run_sub(b, s, sub, tid, mw, mh, sm);
+        if (s == S_PREP || s == S_ROB) __syncthreads();  // the shared tile is reused by the next sub-item
     }
 }
 
@@ -239,7 +247,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
             int *ctrl, int *done, const int *__restrict__ totals, int mw, int mh, int spin_limit) {
     __shared__ int s_item, s_next, s_ok, s_seg;
     __shared__ unsigned int s_ready[kMaxCachedBursts];  // per burst: bit s set once stage s is complete
-    __shared__ float Rs[stage::kRobH + 4][stage::kRobW + 4];
+    __shared__ BatchSmem sm;
     const int tid = threadIdx.x;
     for (int i = tid; i < kMaxCachedBursts; i += kBatchThreads) s_ready[i] = 0u;
     if (tid == 0) {
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         if (item >= total || !s_ok) break;
         const Segment sg = segs[s_seg];
         const int b = sg.burst, s = sg.stage, k = item - sg.first;
-        run_item(bursts[b], s, k, tid, mw, mh, Rs);
+        run_item(bursts[b], s, k, tid, mw, mh, sm);
         __syncthreads();
         if (tid == 0) add_release(&done[b * S_COUNT + s], 1);
     }
@@ -462,7 +470,6 @@ hmfsr_status hmfsr_batch_plan_create(const hmfsr_burst_desc *descs, int n_bursts
             off = align256(off + sizeof(int2) * (size_t)g.n * L.lty[l] * L.ltx[l]);
         }
         const size_t hw = (size_t)g.hh * g.wh;
-        off = align256(off + sizeof(ushort4) * g.n * hw);
         off = align256(off + sizeof(uint2) * g.n * hw);
         off = align256(off + sizeof(float4) * hw);
         off = align256(off + sizeof(float4) * g.n * hw);
@@ -517,7 +524,6 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
             off = align256(off + sizeof(int2) * (size_t)g.n * bb.L.lty[l] * bb.L.ltx[l]);
         }
         const size_t hw = (size_t)g.hh * g.wh;
-        bb.P.guide = reinterpret_cast<ushort4 *>(base + off); off = align256(off + sizeof(ushort4) * g.n * hw);
         bb.P.s1 = reinterpret_cast<uint2 *>(base + off); off = align256(off + sizeof(uint2) * g.n * hw);
         bb.P.base_stats = reinterpret_cast<float4 *>(base + off); off = align256(off + sizeof(float4) * hw);
         bb.P.kern = reinterpret_cast<float4 *>(base + off); off = align256(off + sizeof(float4) * g.n * hw);

@@ -52,7 +52,6 @@ struct Geom {
 
 // Per-frame merge planes in the workspace (one entry per half-res pixel per frame).
 struct MergePlanes {
-    ushort4 *guide;      // [n][hh*wh] {R, G1+G2, B, Lq}
     uint2 *s1;           // [n][hh*wh] 3x3 guide sums {R | B << 16, G1+G2}
     float4 *base_stats;  // [hh*wh] {max(sum sigma^2, eps), dmd^2 R, G, B} of the base frame
     float4 *kern;        // [n][hh*wh] kernel covariance as {a, delta, ux, uy}: Omega = a I + delta u u^T

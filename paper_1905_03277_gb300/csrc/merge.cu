@@ -10,22 +10,13 @@ namespace {
 using stage::kMergeW;
 using stage::kMergeH;
 using stage::kRobW;
-using stage::kRobH;
 
-__global__ void k_guide(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
-                        ushort4 *__restrict__ guide) {
-    stage::guide_px(burst, h, w, pitch, hh, wh, guide, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
-}
-
-__global__ void k_box(const ushort4 *__restrict__ guide, int hh, int wh, int ref, MergeConsts c, int wl,
-                      uint2 *__restrict__ s1, float4 *__restrict__ base_stats) {
-    stage::box_px(guide, hh, wh, ref, c, wl, s1, base_stats, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
-                  blockIdx.z);
-}
-
-__global__ void k_cov(const ushort4 *__restrict__ guide, int hh, int wh, MergeConsts c, int wl,
-                      float4 *__restrict__ kern) {
-    stage::cov_px(guide, hh, wh, c, wl, kern, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+__global__ void __launch_bounds__(stage::kPrepW * 4) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
+                                                            uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
+                                                            float4 *__restrict__ kern) {
+    __shared__ stage::PrepSmem sm;
+    stage::prep_block(burst, g, c, s1, base_stats, kern, sm, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
+                      threadIdx.y);
 }
 
 __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1, float s2,
@@ -33,11 +24,11 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
     stage::strength(motion, n, ty, tx, m_th, s1, s2, s_tile, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-__global__ void __launch_bounds__(kRobW *kRobH) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
-                                                     const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                                     Geom g, float t_thr, int frame, float *__restrict__ rhat) {
-    __shared__ float Rs[kRobH + 4][kRobW + 4];
-    stage::rob_block(s1, base_stats, motion, s_tile, g, t_thr, frame, rhat, Rs, blockIdx.x, blockIdx.y, threadIdx.x,
+__global__ void __launch_bounds__(kRobW * 4) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
+                                                   const float2 *__restrict__ motion, const float *__restrict__ s_tile,
+                                                   Geom g, float t_thr, float *__restrict__ rhat) {
+    __shared__ stage::RobSmem sm;
+    stage::rob_block(s1, base_stats, motion, s_tile, g, t_thr, rhat, sm, blockIdx.x, blockIdx.y, threadIdx.x,
                      threadIdx.y);
 }
 
@@ -88,18 +79,14 @@ __global__ void k_export(const float4 *__restrict__ kern, const float *__restric
 
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
-    dim3 grid(div_up(g.wh, 128), g.hh, g.n);
-    k_guide<<<grid, 128, 0, s>>>(burst, g.h, g.w, g.pitch, g.hh, g.wh, P.guide);
-    k_box<<<grid, 128, 0, s>>>(P.guide, g.hh, g.wh, g.ref, c, g.wl, P.s1, P.base_stats);
-    k_cov<<<grid, 128, 0, s>>>(P.guide, g.hh, g.wh, c, g.wl, P.kern);
+    k_prep<<<dim3(div_up(g.wh, stage::kPrepW), div_up(g.hh, stage::kPrepH), g.n), dim3(stage::kPrepW, 4), 0, s>>>(
+        burst, g, c, P.s1, P.base_stats, P.kern);
     int nt = g.n * g.ty * g.tx;
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
-    dim3 rgrid(div_up(g.wh, kRobW), div_up(g.hh, kRobH));
-    for (int f = 0; f < g.n; ++f) {
-        if (f == g.ref) continue;
-        k_rob<<<rgrid, dim3(kRobW, kRobH), 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, f, P.rhat);
-    }
+    if (g.n > 1)
+        k_rob<<<dim3(div_up(g.wh, kRobW), div_up(g.hh, stage::kRobH)), dim3(kRobW, 4), 0, s>>>(
+            P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat);
     return cudaGetLastError();
 }
 

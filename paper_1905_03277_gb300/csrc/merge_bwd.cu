@@ -19,16 +19,21 @@ constexpr int kBwdW = 32, kBwdH = 4, kBwdThreads = kBwdW * kBwdH;
 // ---------------------------------------------------------------------------------------
 // per texel: what the kernel-shape derivative needs {A, sqrt(l1_norm), cos 2t, sin 2t}
 // ---------------------------------------------------------------------------------------
-__global__ void k_shape(const ushort4 *__restrict__ guide, int hh, int wh, int wl, float4 *__restrict__ shape) {
+__global__ void k_shape(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh, int wl,
+                        float4 *__restrict__ shape) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
     if (u >= wh) return;
-    const ushort4 *G = guide + (size_t)f * hh * wh;
-    int L[3][3];
+    const uint16_t *fr = burst + (size_t)f * h * pitch;
+    int L[3][3];  // Lq of the clamped 3x3 window: sum of each quad's four samples
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            L[j][i] = G[(size_t)clampi(v - 1 + j, 0, hh - 1) * wh + clampi(u - 1 + i, 0, wh - 1)].w;
+        for (int i = 0; i < 3; ++i) {
+            const uint16_t *q = fr + (size_t)(2 * clampi(v - 1 + j, 0, hh - 1)) * pitch + 2 * clampi(u - 1 + i, 0, wh - 1);
+            const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(q));
+            const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(q + pitch));
+            L[j][i] = (int)((a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16));
+        }
     long long ta = 0, tb = 0, tc = 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -530,7 +535,7 @@ cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, co
     const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
-    k_shape<<<tex_grid, 128, 0, s>>>(P.guide, g.hh, g.wh, g.wl, B.shape);
+    k_shape<<<tex_grid, 128, 0, s>>>(burst, g.h, g.pitch, g.hh, g.wh, g.wl, B.shape);
     k_sel<<<div_up(g.n * g.ty * g.tx, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, B.sel);
     k_rback<<<tex_grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, B.sel, g, c, B.rb, B.flags);
     k_argmin<<<tex_grid, 128, 0, s>>>(B.rb, g, B.flags);

@@ -12,18 +12,37 @@ namespace stage {
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
 constexpr float kBig = 1.0e30f;
 
+// exact uint16 -> float on the FMA pipe (v < 2^23)
+__device__ __forceinline__ float u16f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
+
 // ======================================================================================
 // alignment (Sec. 3.2)
 // ======================================================================================
 // Level 0 = half-res luminance Lq: sum of the four Bayer samples of each quad (Sec. 5.1.2).
-__device__ __forceinline__ void luma0(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
-                                      uint16_t *__restrict__ out, int u, int v, int f) {
+// One thread makes 4 consecutive texels: two 16-byte loads and one 8-byte store where the
+// rows allow it, else 4 scalar quads.
+__device__ __forceinline__ void luma0(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh,
+                                      uint16_t *__restrict__ out, int u4, int v, int f) {
+    const int u = 4 * u4;
     if (u >= wh) return;
     const uint16_t *r0 = burst + ((size_t)f * h + 2 * v) * pitch + 2 * u;
-    uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
-    uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch));
-    uint32_t s = (a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16);
-    out[((size_t)f * hh + v) * wh + u] = (uint16_t)s;
+    uint16_t *o = out + ((size_t)f * hh + v) * wh + u;
+    if (u + 4 <= wh && ((reinterpret_cast<uintptr_t>(r0) | reinterpret_cast<uintptr_t>(r0 + pitch)) & 15) == 0 &&
+        (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(r0));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(r0 + pitch));
+        const uint32_t s0 = (a.x & 0xffffu) + (a.x >> 16) + (b.x & 0xffffu) + (b.x >> 16);
+        const uint32_t s1 = (a.y & 0xffffu) + (a.y >> 16) + (b.y & 0xffffu) + (b.y >> 16);
+        const uint32_t s2 = (a.z & 0xffffu) + (a.z >> 16) + (b.z & 0xffffu) + (b.z >> 16);
+        const uint32_t s3 = (a.w & 0xffffu) + (a.w >> 16) + (b.w & 0xffffu) + (b.w >> 16);
+        *reinterpret_cast<uint2 *>(o) = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
+        return;
+    }
+    for (int i = 0; i < 4 && u + i < wh; ++i) {
+        const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
+        const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
+        o[i] = (uint16_t)((a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16));
+    }
 }
 
 // Next level: integer floor mean of f x f blocks.
@@ -205,45 +224,129 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
     }
 }
 
+// The same refinement with T lanes per tile (T <= 8, 32 / T tiles per warp): lane c of a
+// group owns column c of the tile and walks its T rows, so the bilinear samples of a
+// column share their rows (T + 1 rows of two samples per iteration instead of 4 T
+// samples) and neighbouring lanes read neighbouring texels.  Sums over the group by
+// butterfly shuffles inside the group; every lane of the warp runs every iteration (a
+// skipped or absent tile adds nothing and keeps its vector), so the shuffles stay
+// converged.  f is the same for the whole warp.
+template <int T>
+__device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                         const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
+                                         int32_t *__restrict__ motion_int, int tile, int lane, int f) {
+    static_assert(T == 4 || T == 8, "T lanes per tile");
+    const int c = lane & (T - 1);
+    const bool active = tile < lty * ltx;
+    const size_t o = (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        if (active && c == 0) {
+            motion[2 * o] = 0.f;
+            motion[2 * o + 1] = 0.f;
+            if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+        }
+        return;
+    }
+    const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
+    const uint16_t *R = L0 + (size_t)ref * lh * lw;
+    const uint16_t *A = L0 + (size_t)f * lh * lw;
+    const int2 u = active ? vec0[o] : make_int2(0, 0);
+    const int x = min(tx * T + c, lw - 1), y0 = ty * T;
+    const int xm = max(x - 1, 0), xp = min(x + 1, lw - 1);
+    float gxs[T], gys[T], rv[T];
+    long long hxx = 0, hxy = 0, hyy = 0;
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        const int y = min(y0 + j, lh - 1);
+        const uint16_t *row = R + (size_t)y * lw;
+        const int gx = (int)__ldg(row + xp) - (int)__ldg(row + xm);
+        const int gy = (int)__ldg(R + (size_t)min(y + 1, lh - 1) * lw + x) - (int)__ldg(R + (size_t)max(y - 1, 0) * lw + x);
+        gxs[j] = (float)gx * 0.125f;
+        gys[j] = (float)gy * 0.125f;
+        rv[j] = u16f(__ldg(row + x));
+        hxx += (long long)(gx * gx);
+        hxy += (long long)(gx * gy);
+        hyy += (long long)(gy * gy);
+    }
+#pragma unroll
+    for (int m = T / 2; m > 0; m >>= 1) {
+        hxx += __shfl_xor_sync(0xffffffffu, hxx, m);
+        hxy += __shfl_xor_sync(0xffffffffu, hxy, m);
+        hyy += __shfl_xor_sync(0xffffffffu, hyy, m);
+    }
+    // conditioning guard, exact: skip when tr H == 0 or 10^9 det H <= tr(H)^2
+    const __int128 det_i = (__int128)hxx * hyy - (__int128)hxy * hxy;
+    const __int128 tr_i = (__int128)hxx + hyy;
+    const bool skip = (tr_i == 0) || ((__int128)1000000000 * det_i <= tr_i * tr_i);
+    // H in units of g = (Lq difference) / 8 is H_int / 64
+    const float Hxx = (float)hxx, Hxy = (float)hxy, Hyy = (float)hyy;
+    const float inv = skip ? 0.f : 64.f / fmaf(Hxx, Hyy, -Hxy * Hxy);
+    const bool rows_inside = y0 + T <= lh;  // the tile's rows are not clamped
+    float dx = 0.f, dy = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        const float fdx = floorf(dx), fdy = floorf(dy);
+        const float ax = dx - fdx, ay = dy - fdy;
+        const int ox = u.x + (int)fdx, oy = u.y + (int)fdy;
+        const int x0 = clampi(x + ox, 0, lw - 1), x1 = clampi(x + ox + 1, 0, lw - 1);
+        float bx = 0.f, by = 0.f;
+        if (rows_inside) {
+            const uint16_t *a0 = A + (size_t)clampi(y0 + oy, 0, lh - 1) * lw;
+            float i00 = u16f(__ldg(a0 + x0)), i10 = u16f(__ldg(a0 + x1));
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+                const uint16_t *a1 = A + (size_t)clampi(y0 + j + oy + 1, 0, lh - 1) * lw;
+                const float i01 = u16f(__ldg(a1 + x0)), i11 = u16f(__ldg(a1 + x1));
+                const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
+                const float ia = fmaf(ay, bot, (1.f - ay) * top);
+                const float r = (ia - rv[j]) * 0.25f;
+                bx = fmaf(gxs[j], r, bx);
+                by = fmaf(gys[j], r, by);
+                i00 = i01;
+                i10 = i11;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+                const int iy = min(y0 + j, lh - 1) + oy;
+                const uint16_t *a0 = A + (size_t)clampi(iy, 0, lh - 1) * lw;
+                const uint16_t *a1 = A + (size_t)clampi(iy + 1, 0, lh - 1) * lw;
+                const float i00 = u16f(__ldg(a0 + x0)), i10 = u16f(__ldg(a0 + x1));
+                const float i01 = u16f(__ldg(a1 + x0)), i11 = u16f(__ldg(a1 + x1));
+                const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
+                const float ia = fmaf(ay, bot, (1.f - ay) * top);
+                const float r = (ia - rv[j]) * 0.25f;
+                bx = fmaf(gxs[j], r, bx);
+                by = fmaf(gys[j], r, by);
+            }
+        }
+#pragma unroll
+        for (int m = T / 2; m > 0; m >>= 1) {
+            bx += __shfl_xor_sync(0xffffffffu, bx, m);
+            by += __shfl_xor_sync(0xffffffffu, by, m);
+        }
+        if (!skip) {
+            const float sx = -(Hyy * bx - Hxy * by) * inv;
+            const float sy = -(Hxx * by - Hxy * bx) * inv;
+            dx = fminf(fmaxf(dx + sx, -1.f), 1.f);
+            dy = fminf(fmaxf(dy + sy, -1.f), 1.f);
+        }
+    }
+    if (active && c == 0) {
+        motion[2 * o] = 2.f * ((float)u.x + dx);
+        motion[2 * o + 1] = 2.f * ((float)u.y + dy);
+        if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+    }
+}
+
 // ======================================================================================
 // merge preparation (Sec. 5.1.2, 5.2)
 // ======================================================================================
 // --------------------------------------------------------------------------------------
-// guide image + luminance (Sec. 5.1.2, Sec. 5.2.2): one texel per Bayer quad
+// noise-corrected statistics of the base frame that do not depend on the other frame
+// (Eq. 6, closed-form noise model), from the 3x3 guide sums S1 and sums of squares S2
 // --------------------------------------------------------------------------------------
-__device__ __forceinline__ void guide_px(const uint16_t *__restrict__ burst, int h, int w, int pitch, int hh, int wh,
-                                         ushort4 *__restrict__ guide, int u, int v, int f) {
-    if (u >= wh) return;
-    const uint16_t *r0 = burst + ((size_t)f * h + 2 * v) * pitch + 2 * u;
-    uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
-    uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch));
-    uint32_t R = a & 0xffffu, G1 = a >> 16, G2 = b & 0xffffu, B = b >> 16;
-    guide[((size_t)f * hh + v) * wh + u] = make_ushort4((unsigned short)R, (unsigned short)(G1 + G2),
-                                                        (unsigned short)B, (unsigned short)(R + G1 + G2 + B));
-}
-
-// --------------------------------------------------------------------------------------
-// 3x3 guide sums of every frame; for the base frame also the noise-corrected statistics
-// that do not depend on the other frame (Eq. 6, closed-form noise model)
-// --------------------------------------------------------------------------------------
-__device__ __forceinline__ void box_px(const ushort4 *__restrict__ guide, int hh, int wh, int ref, const MergeConsts &c,
-                                       int wl, uint2 *__restrict__ s1, float4 *__restrict__ base_stats, int u, int v, int f) {
-    if (u >= wh) return;
-    const ushort4 *G = guide + (size_t)f * hh * wh;
-    uint32_t sr = 0, sg = 0, sb = 0;
-    uint32_t qr = 0, qg = 0, qb = 0;
-    for (int j = -1; j <= 1; ++j) {
-        int vv = clampi(v + j, 0, hh - 1);
-        for (int i = -1; i <= 1; ++i) {
-            ushort4 q = G[(size_t)vv * wh + clampi(u + i, 0, wh - 1)];
-            sr += q.x; sg += q.y; sb += q.z;
-            qr += (uint32_t)q.x * q.x; qg += (uint32_t)q.y * q.y; qb += (uint32_t)q.z * q.z;
-        }
-    }
-    size_t idx = (size_t)v * wh + u;
-    s1[(size_t)f * hh * wh + idx] = make_uint2(sr | (sb << 16), sg);
-    if (f != ref) return;
-    const uint32_t S1[3] = {sr, sg, sb}, S2[3] = {qr, qg, qb};
+__device__ __forceinline__ float4 base_stats_of(const uint32_t (&S1)[3], const uint32_t (&S2)[3], const MergeConsts &c,
+                                                int wl) {
     float sig2 = 0.f, dmd2[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -257,37 +360,15 @@ __device__ __forceinline__ void box_px(const ushort4 *__restrict__ guide, int hh
         dmd2[ch] = var_md * (2.f / 9.f);
     }
     float eps = 1e-12f * (float)wl * (float)wl;
-    base_stats[idx] = make_float4(fmaxf(sig2, eps), dmd2[0], dmd2[1], dmd2[2]);
+    return make_float4(fmaxf(sig2, eps), dmd2[0], dmd2[1], dmd2[2]);
 }
 
 // --------------------------------------------------------------------------------------
-// structure tensor -> kernel covariance (Eq. 3, Eq. 4, supplement S.1)
+// structure tensor -> kernel covariance (Eq. 3, Eq. 4, supplement S.1), from the exact
+// integer tensor {sum gx^2, sum gx gy, sum gy^2} of the four 2x2 sub-squares
 // --------------------------------------------------------------------------------------
-__device__ __forceinline__ int lq_at(const ushort4 *G, int hh, int wh, int u, int v) {
-    return G[(size_t)clampi(v, 0, hh - 1) * wh + clampi(u, 0, wh - 1)].w;
-}
-
-__device__ __forceinline__ void cov_px(const ushort4 *__restrict__ guide, int hh, int wh, const MergeConsts &c, int wl,
-                                       float4 *__restrict__ kern, int u, int v, int f) {
-    if (u >= wh) return;
-    const ushort4 *G = guide + (size_t)f * hh * wh;
-    // four 2x2 sub-squares of the 3x3 window, forward differences, exact integer tensor
-    int L[3][3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) L[j][i] = lq_at(G, hh, wh, u - 1 + i, v - 1 + j);
-    long long ta = 0, tb = 0, tc = 0;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            int gx = (L[j][i + 1] - L[j][i]) + (L[j + 1][i + 1] - L[j + 1][i]);
-            int gy = (L[j + 1][i] - L[j][i]) + (L[j + 1][i + 1] - L[j][i + 1]);
-            ta += (long long)gx * gx;
-            tb += (long long)gx * gy;
-            tc += (long long)gy * gy;
-        }
+__device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, long long tc, const MergeConsts &c,
+                                                 int wl) {
     // eigen-analysis: lambda1 = (tr + r)/2, dominant direction at angle theta with
     // cos 2theta = (a-c)/r, sin 2theta = 2b/r (theta = 0 when the tensor is isotropic)
     float tr = (float)(ta + tc);
@@ -312,10 +393,96 @@ __device__ __forceinline__ void cov_px(const ushort4 *__restrict__ guide, int hh
     // Omega = k_across e1 e1^T + k_along e2 e2^T (stretch along the edge, e2)
     //       = min I + |k_along - k_across| u u^T with u = e2 if k_along >= k_across else e1
     float dh = (1.f - D) * (kh_al - kh_ac) * (s_al + s_ac);  // k_along - k_across, no cancellation
-    float4 out;
-    if (dh >= 0.f) out = make_float4(k_ac, dh, -e1y, e1x);
-    else out = make_float4(k_al, -dh, e1x, e1y);
-    kern[((size_t)f * hh + v) * wh + u] = out;
+    if (dh >= 0.f) return make_float4(k_ac, dh, -e1y, e1x);
+    return make_float4(k_al, -dh, e1x, e1y);
+}
+
+// --------------------------------------------------------------------------------------
+// merge preparation of one 32 x 16 block of half-res texels of one frame (Sec. 5.1.2,
+// Sec. 5.2.2, Eq. 3-4, supplement S.1).  The guide quads {R, G1+G2, B, Lq} of the block
+// and a 1-texel halo (clamped at the frame border) are built in shared memory from the
+// raw samples, so the guide image never goes to memory.  Each of the 32 x 4 threads then
+// walks 4 texels down one column with a rolling window of 3-texel row sums: the 3x3 guide
+// sums (and, for the base frame, the noise-corrected statistics of Eq. 6) and the exact
+// integer structure tensor of the 3x3 Lq window (forward differences on its four 2x2
+// sub-squares) -> kernel covariance.  Every thread of the block calls this with the same
+// block coordinates (it synchronises the block).
+// --------------------------------------------------------------------------------------
+constexpr int kPrepW = 32, kPrepH = 16, kPrepRows = kPrepH / 4;
+
+struct PrepSmem {
+    ushort4 q[kPrepH + 2][kPrepW + 2];
+};
+
+__device__ __forceinline__ void prep_block(const uint16_t *__restrict__ burst, const Geom &g, const MergeConsts &c,
+                                           uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
+                                           float4 *__restrict__ kern, PrepSmem &sm, int bx, int by, int f, int tx,
+                                           int ty) {
+    const int u0 = bx * kPrepW - 1, v0 = by * kPrepH - 1;
+    const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
+    for (int k = ty * kPrepW + tx; k < (kPrepH + 2) * (kPrepW + 2); k += kPrepW * 4) {
+        const int ly = k / (kPrepW + 2), lx = k - ly * (kPrepW + 2);
+        const int u = clampi(u0 + lx, 0, g.wh - 1), v = clampi(v0 + ly, 0, g.hh - 1);
+        const uint16_t *r0 = fr + (size_t)(2 * v) * g.pitch + 2 * u;
+        const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
+        const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + g.pitch));
+        const uint32_t R = a & 0xffffu, G = (a >> 16) + (b & 0xffffu), B = b >> 16;
+        sm.q[ly][lx] = make_ushort4((unsigned short)R, (unsigned short)G, (unsigned short)B, (unsigned short)(R + G + B));
+    }
+    __syncthreads();
+    const int u = bx * kPrepW + tx, vt = by * kPrepH + ty * kPrepRows;
+    const bool is_ref = (f == g.ref);
+    const size_t hw = (size_t)g.hh * g.wh;
+    // 3-texel row sums of R, G, B (and their squares for the base frame) and the Lq
+    // values of the 6 rows the thread's 4 texels need
+    uint32_t hs[kPrepRows + 2][3], hq[kPrepRows + 2][3];
+    int L[kPrepRows + 2][3];
+#pragma unroll
+    for (int k = 0; k < kPrepRows + 2; ++k) {
+        const ushort4 q0 = sm.q[ty * kPrepRows + k][tx], q1 = sm.q[ty * kPrepRows + k][tx + 1];
+        const ushort4 q2 = sm.q[ty * kPrepRows + k][tx + 2];
+        hs[k][0] = (uint32_t)q0.x + q1.x + q2.x;
+        hs[k][1] = (uint32_t)q0.y + q1.y + q2.y;
+        hs[k][2] = (uint32_t)q0.z + q1.z + q2.z;
+        if (is_ref) {
+            hq[k][0] = (uint32_t)q0.x * q0.x + (uint32_t)q1.x * q1.x + (uint32_t)q2.x * q2.x;
+            hq[k][1] = (uint32_t)q0.y * q0.y + (uint32_t)q1.y * q1.y + (uint32_t)q2.y * q2.y;
+            hq[k][2] = (uint32_t)q0.z * q0.z + (uint32_t)q1.z * q1.z + (uint32_t)q2.z * q2.z;
+        }
+        L[k][0] = q0.w;
+        L[k][1] = q1.w;
+        L[k][2] = q2.w;
+    }
+    // tensor terms of the two sub-squares between rows k and k+1
+    long long pa[kPrepRows + 1], pb[kPrepRows + 1], pc[kPrepRows + 1];
+#pragma unroll
+    for (int k = 0; k < kPrepRows + 1; ++k) {
+        pa[k] = pb[k] = pc[k] = 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int gx = (L[k][i + 1] - L[k][i]) + (L[k + 1][i + 1] - L[k + 1][i]);
+            const int gy = (L[k + 1][i] - L[k][i]) + (L[k + 1][i + 1] - L[k][i + 1]);
+            pa[k] += (long long)gx * gx;
+            pb[k] += (long long)gx * gy;
+            pc[k] += (long long)gy * gy;
+        }
+    }
+    if (u >= g.wh) return;
+#pragma unroll
+    for (int r = 0; r < kPrepRows; ++r) {
+        const int v = vt + r;
+        if (v >= g.hh) break;
+        const size_t idx = (size_t)v * g.wh + u;
+        const uint32_t S1[3] = {hs[r][0] + hs[r + 1][0] + hs[r + 2][0], hs[r][1] + hs[r + 1][1] + hs[r + 2][1],
+                                hs[r][2] + hs[r + 1][2] + hs[r + 2][2]};
+        s1[(size_t)f * hw + idx] = make_uint2(S1[0] | (S1[2] << 16), S1[1]);
+        if (is_ref) {
+            const uint32_t S2[3] = {hq[r][0] + hq[r + 1][0] + hq[r + 2][0], hq[r][1] + hq[r + 1][1] + hq[r + 2][1],
+                                    hq[r][2] + hq[r + 1][2] + hq[r + 2][2]};
+            base_stats[idx] = base_stats_of(S1, S2, c, g.wl);
+        }
+        kern[(size_t)f * hw + idx] = kern_of_tensor(pa[r] + pa[r + 1], pb[r] + pb[r + 1], pc[r] + pc[r + 1], c, g.wl);
+    }
 }
 
 // --------------------------------------------------------------------------------------
@@ -342,83 +509,118 @@ __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int 
 }
 
 // --------------------------------------------------------------------------------------
-// robustness (Eq. 5, 6) on a 32x8 base tile with a 2-px halo, then the 5x5 minimum (Eq. 9)
+// robustness (Eq. 5, 6) of every frame on one 32 x 16 block of base texels with a
+// 2-texel halo, then the 5x5 minimum (Eq. 9).  The base frame's sums and statistics and
+// each position's motion tile are read once into shared memory and serve all frames.
+// Each of the 32 x 4 threads takes the minimum for 4 texels down one column from 5-wide
+// row minima.  Every thread of the block calls this with the same block coordinates (it
+// synchronises the block).
 // --------------------------------------------------------------------------------------
-constexpr int kRobW = 32, kRobH = 4;
+constexpr int kRobW = 32, kRobH = 16, kRobRows = kRobH / 4;
+constexpr int kRobPW = kRobW + 4, kRobPH = kRobH + 4, kRobP = kRobPW * kRobPH;
 
-// Rs: (kRobH + 4) x (kRobW + 4) floats of shared memory; every thread of the 32 x 4
-// block calls this with the same block coordinates (it synchronises the block).
+struct RobSmem {
+    float4 st[kRobP];  // base statistics
+    uint2 sb[kRobP];   // base 3x3 sums
+    int ti[kRobP];     // motion tile of the position, -1 outside the frame
+    float R[kRobPH][kRobPW];
+};
+
 __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                          const Geom &g, float t_thr, int frame, float *__restrict__ rhat,
-                                          float (*Rs)[kRobW + 4], int bx, int by, int tx, int ty) {
-    const int u0 = bx * kRobW - 2, v0 = by * kRobH - 2;
+                                          const Geom &g, float t_thr, float *__restrict__ rhat, RobSmem &sm, int bx,
+                                          int by, int tx, int ty) {
+    const int u0 = bx * kRobW - 2, v0 = by * kRobH - 2, tid = ty * kRobW + tx;
     const size_t hw = (size_t)g.hh * g.wh;
     const uint2 *S1b = s1 + (size_t)g.ref * hw;
-    const uint2 *S1n = s1 + (size_t)frame * hw;
-    const float2 *mvf = motion + (size_t)frame * g.ty * g.tx;
-    const float *stf = s_tile + (size_t)frame * g.ty * g.tx;
     const int half_tile = g.tile / 2;
-    for (int k = ty * kRobW + tx; k < (kRobH + 4) * (kRobW + 4); k += kRobW * kRobH) {
-        int ly = k / (kRobW + 4), lx = k % (kRobW + 4);
-        int u = u0 + lx, v = v0 + ly;
-        float R = kBig;
+    // each thread only reads back the entries it wrote here: no barrier needed
+    for (int k = tid; k < kRobP; k += kRobW * 4) {
+        const int ly = k / kRobPW, lx = k - ly * kRobPW;
+        const int u = u0 + lx, v = v0 + ly;
+        int ti = -1;
         if (u >= 0 && u < g.wh && v >= 0 && v < g.hh) {
-            int txi = min(u / half_tile, g.tx - 1), tyi = min(v / half_tile, g.ty - 1);
-            float2 mv = mvf[(size_t)tyi * g.tx + txi];
-            float s = stf[(size_t)tyi * g.tx + txi];
-            // aligned position (u, v) + v/2 split into an exact integer part and fraction
-            float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
-            float flx = floorf(hx), fly = floorf(hy);
-            float fx = hx - flx, fy = hy - fly;
-            int ix = u + (int)flx, iy = v + (int)fly;
-            int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
-            int y0 = clampi(iy, 0, g.hh - 1), y1 = clampi(iy + 1, 0, g.hh - 1);
-            uint2 sb = S1b[(size_t)v * g.wh + u];
-            uint2 n00 = S1n[(size_t)y0 * g.wh + x0], n10 = S1n[(size_t)y0 * g.wh + x1];
-            uint2 n01 = S1n[(size_t)y1 * g.wh + x0], n11 = S1n[(size_t)y1 * g.wh + x1];
-            float b00 = (1.f - fx) * (1.f - fy), b10 = fx * (1.f - fy), b01 = (1.f - fx) * fy, b11 = fx * fy;
-            // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9 (exact differences)
-            int rb = sb.x & 0xffff, bb = sb.x >> 16, gb = sb.y;
-            float dR = fmaf(b00, (float)(rb - (int)(n00.x & 0xffff)), fmaf(b10, (float)(rb - (int)(n10.x & 0xffff)),
-                       fmaf(b01, (float)(rb - (int)(n01.x & 0xffff)), b11 * (float)(rb - (int)(n11.x & 0xffff)))));
-            float dB = fmaf(b00, (float)(bb - (int)(n00.x >> 16)), fmaf(b10, (float)(bb - (int)(n10.x >> 16)),
-                       fmaf(b01, (float)(bb - (int)(n01.x >> 16)), b11 * (float)(bb - (int)(n11.x >> 16)))));
-            float dG = fmaf(b00, (float)(gb - (int)n00.y), fmaf(b10, (float)(gb - (int)n10.y),
-                       fmaf(b01, (float)(gb - (int)n01.y), b11 * (float)(gb - (int)n11.y))));
-            dR *= (1.f / 9.f);
-            dB *= (1.f / 9.f);
-            dG *= (1.f / 18.f);
-            float4 st = base_stats[(size_t)v * g.wh + u];
-            float dd = 0.f;
-            {
-                float d2 = dR * dR, den = d2 + st.y;
-                float d = den > 0.f ? __fdividef(dR * d2, den) : 0.f;  // Wiener shrinkage (Eq. 6)
-                dd = fmaf(d, d, dd);
-            }
-            {
-                float d2 = dG * dG, den = d2 + st.z;
-                float d = den > 0.f ? __fdividef(dG * d2, den) : 0.f;
-                dd = fmaf(d, d, dd);
-            }
-            {
-                float d2 = dB * dB, den = d2 + st.w;
-                float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
-                dd = fmaf(d, d, dd);
-            }
-            R = fminf(fmaxf(fmaf(s, expf(-__fdividef(dd, st.x)), -t_thr), 0.f), 1.f);  // Eq. 5
+            ti = min(v / half_tile, g.ty - 1) * g.tx + min(u / half_tile, g.tx - 1);
+            sm.sb[k] = S1b[(size_t)v * g.wh + u];
+            sm.st[k] = base_stats[(size_t)v * g.wh + u];
         }
-        Rs[ly][lx] = R;
+        sm.ti[k] = ti;
     }
-    __syncthreads();
-    int u = bx * kRobW + tx, v = by * kRobH + ty;
-    if (u >= g.wh || v >= g.hh) return;
-    float m = kBig;
+    const int uo = bx * kRobW + tx, vo = by * kRobH + ty * kRobRows;
+    for (int frame = 0; frame < g.n; ++frame) {
+        if (frame == g.ref) continue;
+        const uint2 *S1n = s1 + (size_t)frame * hw;
+        const float2 *mvf = motion + (size_t)frame * g.ty * g.tx;
+        const float *stf = s_tile + (size_t)frame * g.ty * g.tx;
+        for (int k = tid; k < kRobP; k += kRobW * 4) {
+            const int ly = k / kRobPW, lx = k - ly * kRobPW;
+            const int ti = sm.ti[k];
+            float R = kBig;
+            if (ti >= 0) {
+                const int u = u0 + lx, v = v0 + ly;
+                const float2 mv = mvf[ti];
+                const float s = stf[ti];
+                // aligned position (u, v) + v/2 split into an exact integer part and fraction
+                const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
+                const float flx = floorf(hx), fly = floorf(hy);
+                const float fx = hx - flx, fy = hy - fly;
+                const int ix = u + (int)flx, iy = v + (int)fly;
+                const int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
+                const int y0 = clampi(iy, 0, g.hh - 1), y1 = clampi(iy + 1, 0, g.hh - 1);
+                const uint2 sb = sm.sb[k];
+                const uint2 n00 = S1n[(size_t)y0 * g.wh + x0], n10 = S1n[(size_t)y0 * g.wh + x1];
+                const uint2 n01 = S1n[(size_t)y1 * g.wh + x0], n11 = S1n[(size_t)y1 * g.wh + x1];
+                const float b00 = (1.f - fx) * (1.f - fy), b10 = fx * (1.f - fy), b01 = (1.f - fx) * fy, b11 = fx * fy;
+                // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9; the
+                // differences of exact integers (< 2^17) are exact in FP32
+                const float rb = u16f(sb.x & 0xffffu), bb = u16f(sb.x >> 16), gb = u16f(sb.y);
+                float dR = fmaf(b00, rb - u16f(n00.x & 0xffffu), fmaf(b10, rb - u16f(n10.x & 0xffffu),
+                           fmaf(b01, rb - u16f(n01.x & 0xffffu), b11 * (rb - u16f(n11.x & 0xffffu)))));
+                float dB = fmaf(b00, bb - u16f(n00.x >> 16), fmaf(b10, bb - u16f(n10.x >> 16),
+                           fmaf(b01, bb - u16f(n01.x >> 16), b11 * (bb - u16f(n11.x >> 16)))));
+                float dG = fmaf(b00, gb - u16f(n00.y), fmaf(b10, gb - u16f(n10.y),
+                           fmaf(b01, gb - u16f(n01.y), b11 * (gb - u16f(n11.y)))));
+                dR *= (1.f / 9.f);
+                dB *= (1.f / 9.f);
+                dG *= (1.f / 18.f);
+                const float4 st = sm.st[k];
+                float dd = 0.f;
+                {
+                    const float d2 = dR * dR, den = d2 + st.y;
+                    const float d = den > 0.f ? __fdividef(dR * d2, den) : 0.f;  // Wiener shrinkage (Eq. 6)
+                    dd = fmaf(d, d, dd);
+                }
+                {
+                    const float d2 = dG * dG, den = d2 + st.z;
+                    const float d = den > 0.f ? __fdividef(dG * d2, den) : 0.f;
+                    dd = fmaf(d, d, dd);
+                }
+                {
+                    const float d2 = dB * dB, den = d2 + st.w;
+                    const float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
+                    dd = fmaf(d, d, dd);
+                }
+                R = fminf(fmaxf(fmaf(s, expf(-__fdividef(dd, st.x)), -t_thr), 0.f), 1.f);  // Eq. 5
+            }
+            sm.R[ly][lx] = R;
+        }
+        __syncthreads();
+        float hm[kRobRows + 4];
 #pragma unroll
-    for (int j = 0; j < 5; ++j)
+        for (int j = 0; j < kRobRows + 4; ++j) {
+            const float *row = sm.R[ty * kRobRows + j] + tx;
+            hm[j] = fminf(fminf(fminf(row[0], row[1]), fminf(row[2], row[3])), row[4]);
+        }
+        if (uo < g.wh) {
 #pragma unroll
-        for (int i = 0; i < 5; ++i) m = fminf(m, Rs[ty + j][tx + i]);
-    rhat[(size_t)frame * hw + (size_t)v * g.wh + u] = m;
+            for (int r = 0; r < kRobRows; ++r) {
+                if (vo + r >= g.hh) break;
+                const float m = fminf(fminf(fminf(hm[r], hm[r + 1]), fminf(hm[r + 2], hm[r + 3])), hm[r + 4]);
+                rhat[(size_t)frame * hw + (size_t)(vo + r) * g.wh + uo] = m;
+            }
+        }
+        __syncthreads();  // the next frame reuses sm.R
+    }
 }
 
 // ======================================================================================
@@ -429,8 +631,6 @@ __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const fl
 // --------------------------------------------------------------------------------------
 constexpr int kMergeW = 32, kMergeH = 4;
 
-// exact uint16 -> float on the FMA pipe (v < 2^23)
-__device__ __forceinline__ float u16f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
 
 // The 3x3 Bayer neighbourhood of frame sample rows around (kx, ky): raw values and the
 // weight exponents q' (log2 units) of the quadratic form; samples outside the frame get
