@@ -23,6 +23,23 @@ __global__ void __launch_bounds__(64) k_ssd(const uint16_t *__restrict__ img, in
                        blockIdx.y);
 }
 
+template <int T, int RAD>
+__global__ void __launch_bounds__(64) k_ssd_rows(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                                 const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                                 int2 *__restrict__ vec) {
+    stage::ssd_rows<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec,
+                            blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
+template <int T, int RAD>
+__global__ void __launch_bounds__(128) k_ssd_split(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                                   const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                                   int2 *__restrict__ vec) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    stage::ssd_split<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, t >> 4, threadIdx.x & 15,
+                             blockIdx.y);
+}
+
 template <int T>
 __global__ void k_lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
                            const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
@@ -42,12 +59,26 @@ __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, i
 
 static const int kFactors[3] = {2, 4, 4};
 
+// Block matching of one level: rows outermost for small radii; the offsets dy spread
+// over lanes when the level has too few tiles to fill the GPU one thread per tile.
+constexpr int kSplitBelow = 152 * 256;  // tiles x frames
+
 template <int T, int RAD>
 static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
     const int tiles = L.lty[l] * L.ltx[l];
-    k_ssd<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(
-        L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], top ? nullptr : L.vec[l + 1], top ? 0 : L.lty[l + 1],
-        top ? 0 : L.ltx[l + 1], fsh, ref, L.vec[l]);
+    const int2 *parent = top ? nullptr : L.vec[l + 1];
+    const int pty = top ? 0 : L.lty[l + 1], ptx = top ? 0 : L.ltx[l + 1];
+    if constexpr (RAD <= 2) {
+        k_ssd_rows<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
+                                                                     parent, pty, ptx, fsh, ref, L.vec[l]);
+    } else {
+        if ((long long)tiles * n < kSplitBelow)
+            k_ssd_split<T, RAD><<<dim3(div_up(tiles * 16, 128), n), 128, 0, s>>>(
+                L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
+        else
+            k_ssd<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
+                                                                    parent, pty, ptx, fsh, ref, L.vec[l]);
+    }
 }
 
 template <int T>

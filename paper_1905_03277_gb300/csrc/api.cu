@@ -103,6 +103,7 @@ size_t carve_merge(void *ws, const Geom &g, MergePlanes *P) {
     P->kern = c.take<float4>(g.n * hw);
     P->rhat = c.take<float>(g.n * hw);
     P->s_tile = c.take<float>((size_t)g.n * g.ty * g.tx);
+    P->geo = c.take<int4>((size_t)g.n * g.ty * g.tx);
     return c.off;
 }
 

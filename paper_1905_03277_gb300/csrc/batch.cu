@@ -70,7 +70,7 @@ __device__ __host__ inline Deps stage_deps(int s) {
         case S_LK: add(S_SSD0); break;
         case S_STRENGTH: add(S_LK); break;
         case S_ROB: add(S_PREP); add(S_STRENGTH); break;
-        case S_MERGE: add(S_PREP); add(S_ROB); add(S_LK); add(S_PHANTOM); break;
+        case S_MERGE: add(S_PREP); add(S_ROB); add(S_LK); add(S_STRENGTH); add(S_PHANTOM); break;
         default: break;
     }
     return r;
@@ -107,7 +107,7 @@ __device__ __host__ inline int stage_subitems(const BatchBurst &b, int s, int mw
     const int nl = b.L.n_levels;
     switch (s) {
         case S_LUMA: return div_up(g.wh, 4 * kBatchThreads) * g.hh * g.n;
-        case S_PREP: return div_up(g.wh, stage::kPrepW) * div_up(g.hh, stage::kPrepH) * g.n;
+        case S_PREP: return div_up(g.wh, kBatchThreads) * div_up(g.hh, stage::kPrepStrip) * g.n;
         case S_DOWN1: case S_DOWN2: case S_DOWN3: {
             const int l = stage_level(s);
             return l < nl ? div_up(b.L.lw[l], kBatchThreads) * b.L.lh[l] * g.n : 0;
@@ -133,19 +133,22 @@ __device__ __forceinline__ void run_ssd(const BatchBurst &b, int l, int tile, in
     const AlignLevels &L = b.L;
     const bool top = (l == L.n_levels - 1);
     const int fsh = top ? 0 : (l == 0 ? 1 : 2);  // log2 of the factors 2, 4, 4 below level l+1
-    stage::ssd<8, RAD>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], top ? nullptr : L.vec[l + 1],
-                       top ? 0 : L.lty[l + 1], top ? 0 : L.ltx[l + 1], fsh, b.g.ref, L.vec[l], tile, f);
+    if constexpr (RAD <= 2)
+        stage::ssd_rows<8, RAD>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], top ? nullptr : L.vec[l + 1],
+                                top ? 0 : L.lty[l + 1], top ? 0 : L.ltx[l + 1], fsh, b.g.ref, L.vec[l], tile, f);
+    else
+        stage::ssd<8, RAD>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], top ? nullptr : L.vec[l + 1],
+                           top ? 0 : L.lty[l + 1], top ? 0 : L.ltx[l + 1], fsh, b.g.ref, L.vec[l], tile, f);
 }
 
 template <int SN, int SD>
 __device__ __forceinline__ void run_merge(const BatchBurst &b, int X, int Y) {
-    stage::merge_px<false, SN, SD>(b.burst, reinterpret_cast<const float2 *>(b.motion), b.g, b.P.kern, b.P.rhat,
+    stage::merge_px<false, SN, SD>(b.burst, b.P.geo, b.g, b.P.kern, b.P.rhat,
                                    b.snum, b.sden, b.ho, b.wo, b.rgb, nullptr, X, Y);
 }
 
 // one sub-item of one stage of burst b, by all 128 threads of the block
 union BatchSmem {
-    stage::PrepSmem prep;
     stage::RobSmem rob;
 };
 
@@ -160,10 +163,10 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
             break;
         }
         case S_PREP: {
-            const int nx = div_up(g.wh, stage::kPrepW), ny = div_up(g.hh, stage::kPrepH);
+            const int nx = div_up(g.wh, kBatchThreads), ny = div_up(g.hh, stage::kPrepStrip);
             const int f = k / (nx * ny), r = k - f * nx * ny, by = r / nx, bx = r - by * nx;
-            stage::prep_block(b.burst, g, b.c, b.P.s1, b.P.base_stats, b.P.kern, sm.prep, bx, by, f,
-                              tid % stage::kPrepW, tid / stage::kPrepW);
+            stage::prep_strip(b.burst, g, b.c, b.P.s1, b.P.base_stats, b.P.kern, bx * kBatchThreads + (tid & ~31),
+                              by * stage::kPrepStrip, f, tid & 31);
             break;
         }
         case S_DOWN1: case S_DOWN2: case S_DOWN3: {
@@ -196,6 +199,7 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
         }
         case S_STRENGTH:
             stage::strength(mv, g.n, g.ty, g.tx, b.c.m_th, b.c.s1, b.c.s2, b.P.s_tile, k * kBatchThreads + tid);
+            stage::geo_entry(mv, g.n, g.ty * g.tx, g.ref, 2 * b.snum, b.P.geo, k * kBatchThreads + tid);
             break;
         case S_ROB: {
             const int nx = div_up(g.wh, stage::kRobW);
@@ -225,7 +229,7 @@ __device__ __forceinline__ void run_item(const BatchBurst &b, int s, int k, int 
         const int sub = k * K + j;
         if (sub >= nsub) break;
         run_sub(b, s, sub, tid, mw, mh, sm);
-        if (s == S_PREP || s == S_ROB) __syncthreads();  // the shared tile is reused by the next sub-item
+        if (s == S_ROB) __syncthreads();  // the shared tile is reused by the next sub-item
     }
 }
 
@@ -475,6 +479,7 @@ hmfsr_status hmfsr_batch_plan_create(const hmfsr_burst_desc *descs, int n_bursts
         off = align256(off + sizeof(float4) * g.n * hw);
         off = align256(off + sizeof(float) * g.n * hw);
         off = align256(off + sizeof(float) * (size_t)g.n * g.ty * g.tx);
+        off = align256(off + sizeof(int4) * (size_t)g.n * g.ty * g.tx);
         off = align256(off + sizeof(float) * (size_t)g.n * g.ty * g.tx * 2);  // motion when the caller gives none
     }
     p->ws_bytes = off;
@@ -529,6 +534,7 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
         bb.P.kern = reinterpret_cast<float4 *>(base + off); off = align256(off + sizeof(float4) * g.n * hw);
         bb.P.rhat = reinterpret_cast<float *>(base + off); off = align256(off + sizeof(float) * g.n * hw);
         bb.P.s_tile = reinterpret_cast<float *>(base + off); off = align256(off + sizeof(float) * (size_t)g.n * g.ty * g.tx);
+        bb.P.geo = reinterpret_cast<int4 *>(base + off); off = align256(off + sizeof(int4) * (size_t)g.n * g.ty * g.tx);
         float *own_motion = reinterpret_cast<float *>(base + off);
         bb.motion = (motion_dev && motion_dev[b]) ? motion_dev[b] : own_motion;
         if (reinterpret_cast<uintptr_t>(bb.motion) & 7) return HMFSR_ERR_INVALID_ARG;

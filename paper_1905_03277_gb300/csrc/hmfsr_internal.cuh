@@ -57,6 +57,7 @@ struct MergePlanes {
     float4 *kern;        // [n][hh*wh] kernel covariance as {a, delta, ux, uy}: Omega = a I + delta u u^T
     float *rhat;         // [n][hh*wh] final robustness (base grid); unused for the base frame
     float *s_tile;       // [n][ty*tx] robustness scale from the motion prior
+    int4 *geo;           // [n][ty*tx] window geometry for the output scale {floor(Q v), Q v - floor(Q v)}
 };
 
 struct MergeConsts {

@@ -11,12 +11,12 @@ using stage::kMergeW;
 using stage::kMergeH;
 using stage::kRobW;
 
-__global__ void __launch_bounds__(stage::kPrepW * 4) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
-                                                            uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                                            float4 *__restrict__ kern) {
-    __shared__ stage::PrepSmem sm;
-    stage::prep_block(burst, g, c, s1, base_stats, kern, sm, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x,
-                      threadIdx.y);
+// 4 warps side by side: 128 texel columns x kPrepStrip rows of one frame
+__global__ void __launch_bounds__(128) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
+                                              uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
+                                              float4 *__restrict__ kern) {
+    stage::prep_strip(burst, g, c, s1, base_stats, kern, blockIdx.x * 128 + (threadIdx.x & ~31),
+                      blockIdx.y * stage::kPrepStrip, blockIdx.z, threadIdx.x & 31);
 }
 
 __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1, float s2,
@@ -32,19 +32,23 @@ __global__ void __launch_bounds__(kRobW * 4) k_rob(const uint2 *__restrict__ s1,
                      threadIdx.y);
 }
 
+__global__ void k_geo(const float2 *__restrict__ motion, int n, int ntl, int ref, int Q, int4 *__restrict__ geo) {
+    stage::geo_entry(motion, n, ntl, ref, Q, geo, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <bool kDen, int SN, int SD>
 __global__ void __launch_bounds__(kMergeW *kMergeH, 8) k_merge(const uint16_t *__restrict__ burst,
-                                                           const float2 *__restrict__ motion, Geom g,
+                                                           const int4 *__restrict__ geo, Geom g,
                                                            const float4 *__restrict__ kern,
                                                            const float *__restrict__ rhat_planes, int snum_rt,
                                                            int sden_rt, int ho, int wo, float *__restrict__ rgb,
                                                            float *__restrict__ den_out) {
-    stage::merge_px<kDen, SN, SD>(burst, motion, g, kern, rhat_planes, snum_rt, sden_rt, ho, wo, rgb, den_out,
+    stage::merge_px<kDen, SN, SD>(burst, geo, g, kern, rhat_planes, snum_rt, sden_rt, ho, wo, rgb, den_out,
                                   blockIdx.x * kMergeW + threadIdx.x, blockIdx.y * kMergeH + threadIdx.y);
 }
 
 template <bool kDen>
-static void launch_k_merge(dim3 grid, cudaStream_t s, const uint16_t *burst, const float2 *mv, const Geom &g,
+static void launch_k_merge(dim3 grid, cudaStream_t s, const uint16_t *burst, const int4 *mv, const Geom &g,
                            const MergePlanes &P, int snum, int sden, int ho, int wo, float *rgb, float *den) {
     const dim3 block(kMergeW, kMergeH);
     if (snum == 1 && sden == 1)
@@ -79,8 +83,8 @@ __global__ void k_export(const float4 *__restrict__ kern, const float *__restric
 
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
-    k_prep<<<dim3(div_up(g.wh, stage::kPrepW), div_up(g.hh, stage::kPrepH), g.n), dim3(stage::kPrepW, 4), 0, s>>>(
-        burst, g, c, P.s1, P.base_stats, P.kern);
+    k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, stage::kPrepStrip), g.n), 128, 0, s>>>(burst, g, c, P.s1,
+                                                                                      P.base_stats, P.kern);
     int nt = g.n * g.ty * g.tx;
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
@@ -94,11 +98,13 @@ cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const
                                int snum, int sden, float *rgb, float *den, cudaStream_t s) {
     int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     dim3 grid(div_up(wo, kMergeW), div_up(ho, kMergeH));
-    const float2 *mv = reinterpret_cast<const float2 *>(motion);
+    const int ntl = g.ty * g.tx;
+    k_geo<<<div_up(g.n * ntl, 128), 128, 0, s>>>(reinterpret_cast<const float2 *>(motion), g.n, ntl, g.ref, 2 * snum,
+                                                 P.geo);
     if (den)
-        launch_k_merge<true>(grid, s, burst, mv, g, P, snum, sden, ho, wo, rgb, den);
+        launch_k_merge<true>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, den);
     else
-        launch_k_merge<false>(grid, s, burst, mv, g, P, snum, sden, ho, wo, rgb, nullptr);
+        launch_k_merge<false>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, nullptr);
     return cudaGetLastError();
 }
 

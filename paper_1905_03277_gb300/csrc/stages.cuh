@@ -69,6 +69,41 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
+// Squared differences of one tile row against one candidate row, exactly: luminance
+// values are below 2^15 (4 x 7281), so 4 squared differences fit 32 bits.
+template <int T>
+__device__ __forceinline__ unsigned long long row_ssd(const int *rv, const int *av) {
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int i0 = 0; i0 < T; i0 += 4) {
+        unsigned int part = 0;
+#pragma unroll
+        for (int i = i0; i < i0 + 4 && i < T; ++i) {
+            const int d = rv[i] - av[i];
+            part += (unsigned int)(d * d);
+        }
+        acc += part;
+    }
+    return acc;
+}
+
+// The block-matching key: smallest SSD, then smallest |dx| + |dy|, then smaller dy, then
+// smaller dx -- one 64-bit key whose minimum decides.
+__device__ __forceinline__ unsigned long long ssd_key(unsigned long long ssd, int dx, int dy) {
+    return (ssd << 12) | ((unsigned long long)(abs(dx) + abs(dy)) << 8) | ((unsigned long long)(dy + 7) << 4) |
+           (unsigned long long)(dx + 7);
+}
+
+// candidate centre of a tile: the parent level's vector times the level factor 1 << fsh
+__device__ __forceinline__ int2 ssd_centre(const int2 *__restrict__ parent, int pty, int ptx, int fsh, int tx, int ty,
+                                           int T, int f) {
+    if (!parent) return make_int2(0, 0);
+    const int px = min(((tx * T + T / 2) >> fsh) / T, ptx - 1);
+    const int py = min(((ty * T + T / 2) >> fsh) / T, pty - 1);
+    const int2 pv = __ldg(parent + (size_t)f * pty * ptx + (size_t)py * ptx + px);
+    return make_int2(pv.x << fsh, pv.y << fsh);
+}
+
 // One thread per tile of one level: exhaustive integer SSD over offsets |d| <= RAD
 // around the candidate (the parent's vector times the level factor).  For each dy the
 // thread streams the tile's rows (L1-cached reads, clamped at the border) and keeps the
@@ -87,14 +122,8 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
         *out = make_int2(0, 0);
         return;
     }
-    int cx = 0, cy = 0;
-    if (parent) {  // level factor 1 << fsh
-        const int px = min(((tx * T + T / 2) >> fsh) / T, ptx - 1);
-        const int py = min(((ty * T + T / 2) >> fsh) / T, pty - 1);
-        const int2 pv = __ldg(parent + (size_t)f * pty * ptx + (size_t)py * ptx + px);
-        cx = pv.x << fsh;
-        cy = pv.y << fsh;
-    }
+    const int2 cc = ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
+    const int cx = cc.x, cy = cc.y;
     const uint16_t *R = img + (size_t)ref * lh * lw;
     const uint16_t *A = img + (size_t)f * lh * lw;
     const int x0 = tx * T, y0 = ty * T;
@@ -112,29 +141,134 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
 #pragma unroll
             for (int i = 0; i < T + 2 * RAD; ++i) av[i] = __ldg(arow + clampi(x0 + cx - RAD + i, 0, lw - 1));
 #pragma unroll
-            for (int k = 0; k < kW; ++k) {
-#pragma unroll
-                for (int i0 = 0; i0 < T; i0 += 8) {
-                    unsigned int part = 0;  // 8 squared 14-bit differences fit 32 bits
-#pragma unroll
-                    for (int i = i0; i < i0 + 8 && i < T; ++i) {
-                        const int d = rv[i] - av[i + k];
-                        part += (unsigned int)(d * d);
-                    }
-                    acc[k] += part;
-                }
-            }
+            for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
         }
 #pragma unroll
         for (int k = 0; k < kW; ++k) {
-            const int dx = k - RAD;
-            const unsigned long long key = (acc[k] << 12) | ((unsigned long long)(abs(dx) + abs(dy)) << 8) |
-                                           ((unsigned long long)(dy + 7) << 4) | (unsigned long long)(dx + 7);
+            const unsigned long long key = ssd_key(acc[k], k - RAD, dy);
             best = key < best ? key : best;
         }
     }
     const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
     *out = make_int2(cx + bdx, cy + bdy);
+}
+
+// The same search with the tile rows outermost (small radii): each candidate row is read
+// once and serves the 2 RAD + 1 offsets dy that use it; a rolling window of 2 RAD + 1
+// candidate rows stays in registers.  Same sums and keys as ssd(), so the same vector.
+template <int T, int RAD>
+__device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                         const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                         int2 *__restrict__ vec, int tile, int f) {
+    constexpr int kW = 2 * RAD + 1, kA = T + 2 * RAD;
+    if (tile >= lty * ltx) return;
+    const int ty = tile / ltx, tx = tile - ty * ltx;
+    int2 *out = vec + (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        *out = make_int2(0, 0);
+        return;
+    }
+    const int2 cc = ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
+    const uint16_t *R = img + (size_t)ref * lh * lw;
+    const uint16_t *A = img + (size_t)f * lh * lw;
+    const int x0 = tx * T, y0 = ty * T;
+    unsigned long long acc[kW][kW];
+#pragma unroll
+    for (int a = 0; a < kW; ++a)
+#pragma unroll
+        for (int b = 0; b < kW; ++b) acc[a][b] = 0;
+    int av[kW][kA];  // av[d]: candidate row y0 + j + d - RAD (+ the centre's dy)
+#pragma unroll
+    for (int d = 0; d < kW - 1; ++d) {
+        const uint16_t *arow = A + (size_t)clampi(y0 + d - RAD + cc.y, 0, lh - 1) * lw;
+#pragma unroll
+        for (int i = 0; i < kA; ++i) av[d][i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        {
+            const uint16_t *arow = A + (size_t)clampi(y0 + j + RAD + cc.y, 0, lh - 1) * lw;
+#pragma unroll
+            for (int i = 0; i < kA; ++i) av[kW - 1][i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
+        }
+        const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
+        int rv[T];
+#pragma unroll
+        for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
+#pragma unroll
+        for (int d = 0; d < kW; ++d)
+#pragma unroll
+            for (int k = 0; k < kW; ++k) acc[d][k] += row_ssd<T>(rv, av[d] + k);
+#pragma unroll
+        for (int d = 0; d < kW - 1; ++d)
+#pragma unroll
+            for (int i = 0; i < kA; ++i) av[d][i] = av[d + 1][i];
+    }
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int d = 0; d < kW; ++d)
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            const unsigned long long key = ssd_key(acc[d][k], k - RAD, d - RAD);
+            best = key < best ? key : best;
+        }
+    const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
+    *out = make_int2(cc.x + bdx, cc.y + bdy);
+}
+
+// The same search with the offsets dy spread over the lanes of a 16-lane group (lane d
+// takes dy = d - RAD; lanes beyond 2 RAD only join the reduction), for levels with too
+// few tiles to fill the GPU one thread per tile.  The group's minimum key is taken by
+// butterfly shuffles; lane 0 of the group writes.  Every lane of the warp calls this; f
+// is the same for the whole warp.
+template <int T, int RAD>
+__device__ __forceinline__ void ssd_split(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                          const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                          int2 *__restrict__ vec, int tile, int lane16, int f) {
+    constexpr int kW = 2 * RAD + 1;
+    static_assert(kW <= 16, "one lane per dy");
+    const bool active = tile < lty * ltx;
+    if (f == ref) {
+        if (active && lane16 == 0) vec[(size_t)f * lty * ltx + tile] = make_int2(0, 0);
+        return;
+    }
+    const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
+    const int2 cc = active ? ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f) : make_int2(0, 0);
+    unsigned long long best = ~0ull;
+    if (active && lane16 < kW) {
+        const int dy = lane16 - RAD;
+        const uint16_t *R = img + (size_t)ref * lh * lw;
+        const uint16_t *A = img + (size_t)f * lh * lw;
+        const int x0 = tx * T, y0 = ty * T;
+        unsigned long long acc[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) acc[k] = 0;
+        for (int j = 0; j < T; ++j) {
+            const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
+            const uint16_t *arow = A + (size_t)clampi(y0 + j + cc.y + dy, 0, lh - 1) * lw;
+            int rv[T], av[T + 2 * RAD];
+#pragma unroll
+            for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
+#pragma unroll
+            for (int i = 0; i < T + 2 * RAD; ++i) av[i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
+#pragma unroll
+            for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
+        }
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            const unsigned long long key = ssd_key(acc[k], k - RAD, dy);
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, m);
+        best = o < best ? o : best;
+    }
+    if (active && lane16 == 0) {
+        const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
+        vec[(size_t)f * lty * ltx + tile] = make_int2(cc.x + bdx, cc.y + bdy);
+    }
 }
 
 // Lucas-Kanade refinement (Sec. 3.2) of one level-0 tile per warp, on I = Lq / 4.  Each
@@ -398,90 +532,130 @@ __device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, lon
 }
 
 // --------------------------------------------------------------------------------------
-// merge preparation of one 32 x 16 block of half-res texels of one frame (Sec. 5.1.2,
-// Sec. 5.2.2, Eq. 3-4, supplement S.1).  The guide quads {R, G1+G2, B, Lq} of the block
-// and a 1-texel halo (clamped at the frame border) are built in shared memory from the
-// raw samples, so the guide image never goes to memory.  Each of the 32 x 4 threads then
-// walks 4 texels down one column with a rolling window of 3-texel row sums: the 3x3 guide
-// sums (and, for the base frame, the noise-corrected statistics of Eq. 6) and the exact
-// integer structure tensor of the 3x3 Lq window (forward differences on its four 2x2
-// sub-squares) -> kernel covariance.  Every thread of the block calls this with the same
-// block coordinates (it synchronises the block).
+// merge preparation of one strip of half-res texels of one frame (Sec. 5.1.2, Sec. 5.2.2,
+// Eq. 3-4, supplement S.1): one warp, 32 consecutive texel columns, kPrepStrip rows.
+// Each lane builds the guide quad {R, G1+G2, B, Lq} of its column from the raw samples
+// row by row (the guide image never goes to memory); the left and right neighbours come
+// from the adjacent lanes (lanes 0 and 31 read the strip's halo quads), rows and
+// columns clamped at the frame border.  A rolling window over three rows gives the 3x3
+// guide sums (and, for the base frame, the noise-corrected statistics of Eq. 6) and the
+// exact integer structure tensor of the 3x3 Lq window (forward differences on its four
+// 2x2 sub-squares) -> kernel covariance.  Raw rows are fetched two rows ahead.  The R
+// and B sums travel packed in one word: 9 x 7281 < 2^16, so the halves never carry.
 // --------------------------------------------------------------------------------------
-constexpr int kPrepW = 32, kPrepH = 16, kPrepRows = kPrepH / 4;
+constexpr int kPrepStrip = 32;
 
-struct PrepSmem {
-    ushort4 q[kPrepH + 2][kPrepW + 2];
+struct PrepRow {
+    uint32_t a, b;    // the lane's quad: {R, G1} and {G2, B}
+    uint32_t ha, hb;  // lanes 0 and 31: the halo quad beside the strip
 };
 
-__device__ __forceinline__ void prep_block(const uint16_t *__restrict__ burst, const Geom &g, const MergeConsts &c,
+struct PrepState {
+    uint32_t rb[2], gs[2];  // 3-texel row sums of the two previous rows: R | B << 16, G1 + G2
+    uint32_t q[2][3];       // 3-texel row sums of squares (base frame)
+    int L[3];               // Lq of the previous row at columns -1, 0, +1
+    long long pa, pb, pc;   // tensor terms of the previous pair of rows
+};
+
+__device__ __forceinline__ PrepRow prep_fetch(const uint16_t *__restrict__ fr, int pitch, int hh, int uc, int uh,
+                                              bool halo, int v) {
+    const uint16_t *row = fr + (size_t)(2 * clampi(v, 0, hh - 1)) * pitch;
+    PrepRow p;
+    p.a = __ldg(reinterpret_cast<const uint32_t *>(row + 2 * uc));
+    p.b = __ldg(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uc));
+    p.ha = p.hb = 0u;
+    if (halo) {
+        p.ha = __ldg(reinterpret_cast<const uint32_t *>(row + 2 * uh));
+        p.hb = __ldg(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uh));
+    }
+    return p;
+}
+
+// one raw row pair of the strip (strip row r = -1 .. kPrepStrip); emits texel row r - 1
+__device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r, int lane, bool is_ref, bool out_col,
+                                         int v0, const Geom &g, const MergeConsts &c, int f, int u,
+                                         uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
+                                         float4 *__restrict__ kern) {
+    const uint32_t R = p.a & 0xffffu, G = (p.a >> 16) + (p.b & 0xffffu), B = p.b >> 16;
+    const uint32_t c0 = R | (B << 16), c1 = G | ((R + G + B) << 16);  // {R, B}, {G, Lq}
+    uint32_t l0 = __shfl_up_sync(0xffffffffu, c0, 1), l1 = __shfl_up_sync(0xffffffffu, c1, 1);
+    uint32_t r0 = __shfl_down_sync(0xffffffffu, c0, 1), r1 = __shfl_down_sync(0xffffffffu, c1, 1);
+    if (lane == 0 || lane == 31) {
+        const uint32_t hR = p.ha & 0xffffu, hG = (p.ha >> 16) + (p.hb & 0xffffu), hB = p.hb >> 16;
+        const uint32_t h0 = hR | (hB << 16), h1 = hG | ((hR + hG + hB) << 16);
+        if (lane == 0) { l0 = h0; l1 = h1; }
+        else { r0 = h0; r1 = h1; }
+    }
+    const uint32_t rb = l0 + c0 + r0;                              // R and B halves stay below 2^16
+    const uint32_t gs = (l1 & 0xffffu) + G + (r1 & 0xffffu);
+    const int L[3] = {(int)(l1 >> 16), (int)(c1 >> 16), (int)(r1 >> 16)};
+    uint32_t q[3] = {0u, 0u, 0u};
+    if (is_ref) {
+        const uint32_t lR = l0 & 0xffffu, lB = l0 >> 16, lG = l1 & 0xffffu;
+        const uint32_t rR = r0 & 0xffffu, rB = r0 >> 16, rG = r1 & 0xffffu;
+        q[0] = lR * lR + R * R + rR * rR;
+        q[1] = lG * lG + G * G + rG * rG;
+        q[2] = lB * lB + B * B + rB * rB;
+    }
+    // tensor terms of the two sub-squares between the previous row and this one
+    long long pa = 0, pb = 0, pc = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int gx = (st.L[i + 1] - st.L[i]) + (L[i + 1] - L[i]);
+        const int gy = (L[i] - st.L[i]) + (L[i + 1] - st.L[i + 1]);
+        pa += (long long)gx * gx;
+        pb += (long long)gx * gy;
+        pc += (long long)gy * gy;
+    }
+    if (r >= 1 && out_col) {
+        const int v = v0 + r - 1;
+        if (v < g.hh) {
+            const size_t hw = (size_t)g.hh * g.wh, idx = (size_t)v * g.wh + u;
+            const uint32_t srb = st.rb[0] + st.rb[1] + rb, sg = st.gs[0] + st.gs[1] + gs;
+            s1[(size_t)f * hw + idx] = make_uint2(srb, sg);
+            if (is_ref) {
+                const uint32_t S1[3] = {srb & 0xffffu, sg, srb >> 16};
+                const uint32_t S2[3] = {st.q[0][0] + st.q[1][0] + q[0], st.q[0][1] + st.q[1][1] + q[1],
+                                        st.q[0][2] + st.q[1][2] + q[2]};
+                base_stats[idx] = base_stats_of(S1, S2, c, g.wl);
+            }
+            kern[(size_t)f * hw + idx] = kern_of_tensor(st.pa + pa, st.pb + pb, st.pc + pc, c, g.wl);
+        }
+    }
+    st.rb[0] = st.rb[1]; st.rb[1] = rb;
+    st.gs[0] = st.gs[1]; st.gs[1] = gs;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) { st.q[0][ch] = st.q[1][ch]; st.q[1][ch] = q[ch]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st.L[i] = L[i];
+    st.pa = pa; st.pb = pb; st.pc = pc;
+}
+
+// strip (u0 .. u0 + 31) x (v0 .. v0 + kPrepStrip - 1) of frame f; every lane of the warp
+// calls this (the strip's shuffles need them all)
+__device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, const Geom &g, const MergeConsts &c,
                                            uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                           float4 *__restrict__ kern, PrepSmem &sm, int bx, int by, int f, int tx,
-                                           int ty) {
-    const int u0 = bx * kPrepW - 1, v0 = by * kPrepH - 1;
+                                           float4 *__restrict__ kern, int u0, int v0, int f, int lane) {
     const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
-    for (int k = ty * kPrepW + tx; k < (kPrepH + 2) * (kPrepW + 2); k += kPrepW * 4) {
-        const int ly = k / (kPrepW + 2), lx = k - ly * (kPrepW + 2);
-        const int u = clampi(u0 + lx, 0, g.wh - 1), v = clampi(v0 + ly, 0, g.hh - 1);
-        const uint16_t *r0 = fr + (size_t)(2 * v) * g.pitch + 2 * u;
-        const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0));
-        const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + g.pitch));
-        const uint32_t R = a & 0xffffu, G = (a >> 16) + (b & 0xffffu), B = b >> 16;
-        sm.q[ly][lx] = make_ushort4((unsigned short)R, (unsigned short)G, (unsigned short)B, (unsigned short)(R + G + B));
-    }
-    __syncthreads();
-    const int u = bx * kPrepW + tx, vt = by * kPrepH + ty * kPrepRows;
-    const bool is_ref = (f == g.ref);
-    const size_t hw = (size_t)g.hh * g.wh;
-    // 3-texel row sums of R, G, B (and their squares for the base frame) and the Lq
-    // values of the 6 rows the thread's 4 texels need
-    uint32_t hs[kPrepRows + 2][3], hq[kPrepRows + 2][3];
-    int L[kPrepRows + 2][3];
+    const int u = u0 + lane, uc = min(u, g.wh - 1);
+    const bool halo = (lane == 0 || lane == 31);
+    const int uh = clampi(lane == 0 ? u0 - 1 : u0 + 32, 0, g.wh - 1);
+    const bool is_ref = (f == g.ref), out_col = u < g.wh;
+    PrepState st;
+    st.rb[0] = st.rb[1] = st.gs[0] = st.gs[1] = 0u;
 #pragma unroll
-    for (int k = 0; k < kPrepRows + 2; ++k) {
-        const ushort4 q0 = sm.q[ty * kPrepRows + k][tx], q1 = sm.q[ty * kPrepRows + k][tx + 1];
-        const ushort4 q2 = sm.q[ty * kPrepRows + k][tx + 2];
-        hs[k][0] = (uint32_t)q0.x + q1.x + q2.x;
-        hs[k][1] = (uint32_t)q0.y + q1.y + q2.y;
-        hs[k][2] = (uint32_t)q0.z + q1.z + q2.z;
-        if (is_ref) {
-            hq[k][0] = (uint32_t)q0.x * q0.x + (uint32_t)q1.x * q1.x + (uint32_t)q2.x * q2.x;
-            hq[k][1] = (uint32_t)q0.y * q0.y + (uint32_t)q1.y * q1.y + (uint32_t)q2.y * q2.y;
-            hq[k][2] = (uint32_t)q0.z * q0.z + (uint32_t)q1.z * q1.z + (uint32_t)q2.z * q2.z;
-        }
-        L[k][0] = q0.w;
-        L[k][1] = q1.w;
-        L[k][2] = q2.w;
-    }
-    // tensor terms of the two sub-squares between rows k and k+1
-    long long pa[kPrepRows + 1], pb[kPrepRows + 1], pc[kPrepRows + 1];
-#pragma unroll
-    for (int k = 0; k < kPrepRows + 1; ++k) {
-        pa[k] = pb[k] = pc[k] = 0;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int gx = (L[k][i + 1] - L[k][i]) + (L[k + 1][i + 1] - L[k + 1][i]);
-            const int gy = (L[k + 1][i] - L[k][i]) + (L[k + 1][i + 1] - L[k][i + 1]);
-            pa[k] += (long long)gx * gx;
-            pb[k] += (long long)gx * gy;
-            pc[k] += (long long)gy * gy;
-        }
-    }
-    if (u >= g.wh) return;
-#pragma unroll
-    for (int r = 0; r < kPrepRows; ++r) {
-        const int v = vt + r;
-        if (v >= g.hh) break;
-        const size_t idx = (size_t)v * g.wh + u;
-        const uint32_t S1[3] = {hs[r][0] + hs[r + 1][0] + hs[r + 2][0], hs[r][1] + hs[r + 1][1] + hs[r + 2][1],
-                                hs[r][2] + hs[r + 1][2] + hs[r + 2][2]};
-        s1[(size_t)f * hw + idx] = make_uint2(S1[0] | (S1[2] << 16), S1[1]);
-        if (is_ref) {
-            const uint32_t S2[3] = {hq[r][0] + hq[r + 1][0] + hq[r + 2][0], hq[r][1] + hq[r + 1][1] + hq[r + 2][1],
-                                    hq[r][2] + hq[r + 1][2] + hq[r + 2][2]};
-            base_stats[idx] = base_stats_of(S1, S2, c, g.wl);
-        }
-        kern[(size_t)f * hw + idx] = kern_of_tensor(pa[r] + pa[r + 1], pb[r] + pb[r + 1], pc[r] + pc[r + 1], c, g.wl);
+    for (int ch = 0; ch < 3; ++ch) st.q[0][ch] = st.q[1][ch] = 0u;
+    st.L[0] = st.L[1] = st.L[2] = 0;
+    st.pa = st.pb = st.pc = 0;
+    PrepRow p0 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 - 1);
+    PrepRow p1 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0);
+    for (int r = -1; r <= kPrepStrip; r += 2) {
+        const PrepRow cur0 = p0;
+        p0 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 + r + 2);
+        prep_row(cur0, st, r, lane, is_ref, out_col, v0, g, c, f, u, s1, base_stats, kern);
+        const PrepRow cur1 = p1;
+        p1 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 + r + 3);
+        prep_row(cur1, st, r + 1, lane, is_ref, out_col, v0, g, c, f, u, s1, base_stats, kern);
     }
 }
 
@@ -510,20 +684,25 @@ __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int 
 
 // --------------------------------------------------------------------------------------
 // robustness (Eq. 5, 6) of every frame on one 32 x 16 block of base texels with a
-// 2-texel halo, then the 5x5 minimum (Eq. 9).  The base frame's sums and statistics and
-// each position's motion tile are read once into shared memory and serve all frames.
+// 2-texel halo, then the 5x5 minimum (Eq. 9).  The base frame's sums and statistics are
+// read once into shared memory and serve all frames; per frame, each motion tile the
+// region touches gets its integer offset, bilinear weights and robustness scale once.
 // Each of the 32 x 4 threads takes the minimum for 4 texels down one column from 5-wide
 // row minima.  Every thread of the block calls this with the same block coordinates (it
 // synchronises the block).
 // --------------------------------------------------------------------------------------
 constexpr int kRobW = 32, kRobH = 16, kRobRows = kRobH / 4;
 constexpr int kRobPW = kRobW + 4, kRobPH = kRobH + 4, kRobP = kRobPW * kRobPH;
+constexpr int kRobMaxTiles = 64;  // (36 / 4 + 1) x (20 / 4 + 1) for the smallest tile (4 texels)
+constexpr float kLog2e = 1.44269504088896340736f;
 
 struct RobSmem {
-    float4 st[kRobP];  // base statistics
-    uint2 sb[kRobP];   // base 3x3 sums
-    int ti[kRobP];     // motion tile of the position, -1 outside the frame
+    float4 st[kRobP];          // base statistics
+    uint2 sb[kRobP];           // base 3x3 sums
+    int lt[kRobP];             // the position's motion tile within the region, -1 outside the frame
     float R[kRobPH][kRobPW];
+    float4 tw[kRobMaxTiles];   // per tile, this frame: bilinear weights b00, b10, b01, b11
+    int4 to[kRobMaxTiles];     // per tile, this frame: {integer offset x, y, robustness scale bits, 0}
 };
 
 __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
@@ -533,53 +712,61 @@ __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const fl
     const int u0 = bx * kRobW - 2, v0 = by * kRobH - 2, tid = ty * kRobW + tx;
     const size_t hw = (size_t)g.hh * g.wh;
     const uint2 *S1b = s1 + (size_t)g.ref * hw;
-    const int half_tile = g.tile / 2;
+    const int ht = g.tile / 2;  // motion tile in texels
+    // motion tiles the region touches (a tile index is clamped to the last tile)
+    const int tx_lo = min(max(u0, 0) / ht, g.tx - 1), tx_hi = min(min(u0 + kRobPW - 1, g.wh - 1) / ht, g.tx - 1);
+    const int ty_lo = min(max(v0, 0) / ht, g.ty - 1), ty_hi = min(min(v0 + kRobPH - 1, g.hh - 1) / ht, g.ty - 1);
+    const int ntx = tx_hi - tx_lo + 1, nt = ntx * (ty_hi - ty_lo + 1);
     // each thread only reads back the entries it wrote here: no barrier needed
     for (int k = tid; k < kRobP; k += kRobW * 4) {
         const int ly = k / kRobPW, lx = k - ly * kRobPW;
         const int u = u0 + lx, v = v0 + ly;
-        int ti = -1;
+        int lt = -1;
         if (u >= 0 && u < g.wh && v >= 0 && v < g.hh) {
-            ti = min(v / half_tile, g.ty - 1) * g.tx + min(u / half_tile, g.tx - 1);
+            lt = (min(v / ht, g.ty - 1) - ty_lo) * ntx + (min(u / ht, g.tx - 1) - tx_lo);
             sm.sb[k] = S1b[(size_t)v * g.wh + u];
             sm.st[k] = base_stats[(size_t)v * g.wh + u];
         }
-        sm.ti[k] = ti;
+        sm.lt[k] = lt;
     }
     const int uo = bx * kRobW + tx, vo = by * kRobH + ty * kRobRows;
     for (int frame = 0; frame < g.n; ++frame) {
         if (frame == g.ref) continue;
+        if (tid < nt) {
+            const int gt = (ty_lo + tid / ntx) * g.tx + tx_lo + tid % ntx;
+            const float2 mv = motion[(size_t)frame * g.ty * g.tx + gt];
+            const float s = s_tile[(size_t)frame * g.ty * g.tx + gt];
+            // aligned position (u, v) + v/2 split into an exact integer part and fraction
+            const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
+            const float flx = floorf(hx), fly = floorf(hy);
+            const float fx = hx - flx, fy = hy - fly;
+            sm.tw[tid] = make_float4((1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy);
+            sm.to[tid] = make_int4((int)flx, (int)fly, __float_as_int(s), 0);
+        }
+        __syncthreads();
         const uint2 *S1n = s1 + (size_t)frame * hw;
-        const float2 *mvf = motion + (size_t)frame * g.ty * g.tx;
-        const float *stf = s_tile + (size_t)frame * g.ty * g.tx;
         for (int k = tid; k < kRobP; k += kRobW * 4) {
             const int ly = k / kRobPW, lx = k - ly * kRobPW;
-            const int ti = sm.ti[k];
+            const int lt = sm.lt[k];
             float R = kBig;
-            if (ti >= 0) {
-                const int u = u0 + lx, v = v0 + ly;
-                const float2 mv = mvf[ti];
-                const float s = stf[ti];
-                // aligned position (u, v) + v/2 split into an exact integer part and fraction
-                const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
-                const float flx = floorf(hx), fly = floorf(hy);
-                const float fx = hx - flx, fy = hy - fly;
-                const int ix = u + (int)flx, iy = v + (int)fly;
+            if (lt >= 0) {
+                const float4 bw = sm.tw[lt];
+                const int4 to = sm.to[lt];
+                const int ix = u0 + lx + to.x, iy = v0 + ly + to.y;
                 const int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
-                const int y0 = clampi(iy, 0, g.hh - 1), y1 = clampi(iy + 1, 0, g.hh - 1);
+                const uint2 *r0 = S1n + (size_t)clampi(iy, 0, g.hh - 1) * g.wh;
+                const uint2 *r1 = S1n + (size_t)clampi(iy + 1, 0, g.hh - 1) * g.wh;
                 const uint2 sb = sm.sb[k];
-                const uint2 n00 = S1n[(size_t)y0 * g.wh + x0], n10 = S1n[(size_t)y0 * g.wh + x1];
-                const uint2 n01 = S1n[(size_t)y1 * g.wh + x0], n11 = S1n[(size_t)y1 * g.wh + x1];
-                const float b00 = (1.f - fx) * (1.f - fy), b10 = fx * (1.f - fy), b01 = (1.f - fx) * fy, b11 = fx * fy;
+                const uint2 n00 = r0[x0], n10 = r0[x1], n01 = r1[x0], n11 = r1[x1];
                 // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9; the
                 // differences of exact integers (< 2^17) are exact in FP32
                 const float rb = u16f(sb.x & 0xffffu), bb = u16f(sb.x >> 16), gb = u16f(sb.y);
-                float dR = fmaf(b00, rb - u16f(n00.x & 0xffffu), fmaf(b10, rb - u16f(n10.x & 0xffffu),
-                           fmaf(b01, rb - u16f(n01.x & 0xffffu), b11 * (rb - u16f(n11.x & 0xffffu)))));
-                float dB = fmaf(b00, bb - u16f(n00.x >> 16), fmaf(b10, bb - u16f(n10.x >> 16),
-                           fmaf(b01, bb - u16f(n01.x >> 16), b11 * (bb - u16f(n11.x >> 16)))));
-                float dG = fmaf(b00, gb - u16f(n00.y), fmaf(b10, gb - u16f(n10.y),
-                           fmaf(b01, gb - u16f(n01.y), b11 * (gb - u16f(n11.y)))));
+                float dR = fmaf(bw.x, rb - u16f(n00.x & 0xffffu), fmaf(bw.y, rb - u16f(n10.x & 0xffffu),
+                           fmaf(bw.z, rb - u16f(n01.x & 0xffffu), bw.w * (rb - u16f(n11.x & 0xffffu)))));
+                float dB = fmaf(bw.x, bb - u16f(n00.x >> 16), fmaf(bw.y, bb - u16f(n10.x >> 16),
+                           fmaf(bw.z, bb - u16f(n01.x >> 16), bw.w * (bb - u16f(n11.x >> 16)))));
+                float dG = fmaf(bw.x, gb - u16f(n00.y), fmaf(bw.y, gb - u16f(n10.y),
+                           fmaf(bw.z, gb - u16f(n01.y), bw.w * (gb - u16f(n11.y)))));
                 dR *= (1.f / 9.f);
                 dB *= (1.f / 9.f);
                 dG *= (1.f / 18.f);
@@ -600,7 +787,9 @@ __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const fl
                     const float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
                     dd = fmaf(d, d, dd);
                 }
-                R = fminf(fmaxf(fmaf(s, expf(-__fdividef(dd, st.x)), -t_thr), 0.f), 1.f);  // Eq. 5
+                // Eq. 5: s exp(-dd / sigma^2) - t, clamped to [0, 1]
+                const float e = fast_exp2(-__fdividef(dd, st.x) * kLog2e);
+                R = fminf(fmaxf(fmaf(__int_as_float(to.z), e, -t_thr), 0.f), 1.f);
             }
             sm.R[ly][lx] = R;
         }
@@ -619,7 +808,7 @@ __device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const fl
                 rhat[(size_t)frame * hw + (size_t)(vo + r) * g.wh + uo] = m;
             }
         }
-        __syncthreads();  // the next frame reuses sm.R
+        __syncthreads();  // the next frame reuses sm.R and the tile tables
     }
 }
 
@@ -655,13 +844,47 @@ __device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int p
     }
 }
 
+// floor(a / B) for B > 0: an arithmetic shift when B is a compile-time power of two,
+// the exact integer floor division otherwise (B = 0: use the runtime divisor b)
+template <int B>
+__device__ __forceinline__ int floor_div_q(int a, int b) {
+    if constexpr (B > 0 && (B & (B - 1)) == 0) {
+        int sh = 0;
+        while ((1 << sh) < B) ++sh;
+        return a >> sh;
+    } else if constexpr (B > 0) {
+        return floor_div(a, B);
+    } else {
+        return floor_div(a, b);
+    }
+}
+
+// Window geometry of one motion tile of one frame for Q = 2 x (output px per raw px
+// numerator): {floor(Q vx), floor(Q vy)} exactly and the fractions {Q vx - F, Q vy - F}
+// (Sec. 5.1: the window centre and the kernel's sampling point).  The base frame's entry
+// is zero: its motion is zero by definition.  i runs over n x tiles.
+__device__ __forceinline__ void geo_entry(const float2 *__restrict__ motion, int n, int ntl, int ref, int Q,
+                                          int4 *__restrict__ geo, int i) {
+    if (i >= n * ntl) return;
+    int4 e = make_int4(0, 0, 0, 0);
+    if (i / ntl != ref) {
+        const float2 mv = motion[i];
+        const int FX = floor_mul(Q, mv.x), FY = floor_mul(Q, mv.y);
+        const float fQ = (float)Q;
+        e = make_int4(FX, FY, __float_as_int(fmaf(fQ, mv.x, -(float)FX)), __float_as_int(fmaf(fQ, mv.y, -(float)FY)));
+    }
+    geo[i] = e;
+}
+
 // SN/SD > 0: compile-time output scale SN/SD (constant divisors); 0: runtime snum/sden.
+// geo: the window geometry of every (frame, motion tile) for this scale (geo_entry).
 template <bool kDen, int SN, int SD>
-__device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, const float2 *__restrict__ motion,
+__device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, const int4 *__restrict__ geo,
                                          const Geom &g, const float4 *__restrict__ kern,
                                          const float *__restrict__ rhat_planes, int snum_rt, int sden_rt, int ho, int wo,
                                          float *__restrict__ rgb, float *__restrict__ den_out, int X, int Y) {
     if (X >= wo || Y >= ho) return;
+    constexpr int QC = 2 * SN, Q2C = 4 * SN;
     const int snum = SN > 0 ? SN : snum_rt, sden = SD > 0 ? SD : sden_rt;
     const int Q = 2 * snum, Q2 = 4 * snum;
     const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
@@ -669,39 +892,50 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
     const int Px = 2 * sden * X + sden - snum, Py = 2 * sden * Y + sden - snum;
     const int txi = min(max(floor_div(Px, Q * g.tile), 0), g.tx - 1);
     const int tyi = min(max(floor_div(Py, Q * g.tile), 0), g.ty - 1);
-    const size_t hw = (size_t)g.hh * g.wh;
+    const size_t hw = (size_t)g.hh * g.wh, ntl = (size_t)g.ty * g.tx;
+    const int4 *geo_px = geo + (size_t)tyi * g.tx + txi;
     // Rhat is sampled on the base half-res grid at (x0 - 1/2)/2 = (P - num) / 2Q
-    const int rx = floor_div(Px - snum, Q2), ry = floor_div(Py - snum, Q2);
+    const int rx = floor_div_q<Q2C>(Px - snum, Q2), ry = floor_div_q<Q2C>(Py - snum, Q2);
     const float rfx = (float)(Px - snum - rx * Q2) * inv2Q, rfy = (float)(Py - snum - ry * Q2) * inv2Q;
     const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
     const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
     const int r00 = ry0 * g.wh + rx0, r10 = ry0 * g.wh + rx1, r01 = ry1 * g.wh + rx0, r11 = ry1 * g.wh + rx1;
     const float rw00 = (1.f - rfx) * (1.f - rfy), rw10 = rfx * (1.f - rfy), rw01 = (1.f - rfx) * rfy, rw11 = rfx * rfy;
+    // a frame's robustness at this pixel (1 for the base frame)
+    auto rhat_at = [&](int f) -> float {
+        if (f == g.ref) return 1.f;
+        const float *Rp = rhat_planes + (size_t)f * hw;
+        return fmaf(rw00, __ldg(Rp + r00), fmaf(rw10, __ldg(Rp + r10), fmaf(rw01, __ldg(Rp + r01), rw11 * __ldg(Rp + r11))));
+    };
 
     float numR = 0.f, numG = 0.f, numB = 0.f, denR = 0.f, denG = 0.f, denB = 0.f;
     float mR = kBig, mG = kBig, mB = kBig;  // per-channel exponent shifts (log2 units)
 
+    // frames in the order base frame, then the others; the next frame's geometry and
+    // robustness are fetched while this one is merged
+    int f_nx = g.ref;
+    int4 geo_nx = __ldg(geo_px + (size_t)f_nx * ntl);
+    float rh_nx = 1.f;
     for (int it = 0; it < g.n; ++it) {
-        const int f = (it == 0) ? g.ref : (it <= g.ref ? it - 1 : it);
-        float vx = 0.f, vy = 0.f, rh = 1.f;
-        if (f != g.ref) {
-            const float *Rp = rhat_planes + (size_t)f * hw;
-            rh = fmaf(rw00, __ldg(Rp + r00), fmaf(rw10, __ldg(Rp + r10), fmaf(rw01, __ldg(Rp + r01), rw11 * __ldg(Rp + r11))));
-            if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
-            const float2 mv = __ldg(motion + ((size_t)f * g.ty + tyi) * g.tx + txi);
-            vx = mv.x;
-            vy = mv.y;
+        const int f = f_nx;
+        const int4 gq = geo_nx;
+        const float rh = rh_nx;
+        if (it + 1 < g.n) {
+            f_nx = (it + 1 <= g.ref) ? it : it + 1;
+            geo_nx = __ldg(geo_px + (size_t)f_nx * ntl);
+            rh_nx = rhat_at(f_nx);
         }
-        // window centre k = round(x0 + v) (ties up), exactly
-        const int FX = floor_mul(Q, vx), FY = floor_mul(Q, vy);
-        const int kx = floor_div(Px + snum + FX, Q), ky = floor_div(Py + snum + FY, Q);
-        // offset of the centre sample from x0 + v: (kx Q - Px - Q v) / Q
-        const float dx0 = fmaf(-fQ, vx, (float)(kx * Q - Px)) * invQ;
-        const float dy0 = fmaf(-fQ, vy, (float)(ky * Q - Py)) * invQ;
+        if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
+        // window centre k = round(x0 + v) (ties up), exactly: F = floor(Q v)
+        const int FX = gq.x, FY = gq.y;
+        const float zx = __int_as_float(gq.z), zy = __int_as_float(gq.w);  // Q v - F
+        const int kx = floor_div_q<QC>(Px + snum + FX, Q), ky = floor_div_q<QC>(Py + snum + FY, Q);
+        // offset of the centre sample from x0 + v: (kx Q - Px - F - (Q v - F)) / Q
+        const float dx0 = ((float)(kx * Q - Px - FX) - zx) * invQ;
+        const float dy0 = ((float)(ky * Q - Py - FY) - zy) * invQ;
         // Omega is sampled on frame f's half-res grid at (x0 + v - 1/2)/2
-        const float zx = fmaf(fQ, vx, -(float)FX), zy = fmaf(fQ, vy, -(float)FY);
         const int gx = Px - snum + FX, gy = Py - snum + FY;
-        const int ox = floor_div(gx, Q2), oy = floor_div(gy, Q2);
+        const int ox = floor_div_q<Q2C>(gx, Q2), oy = floor_div_q<Q2C>(gy, Q2);
         const float ofx = ((float)(gx - ox * Q2) + zx) * inv2Q, ofy = ((float)(gy - oy * Q2) + zy) * inv2Q;
         const int ox0 = clampi(ox, 0, g.wh - 1), ox1 = clampi(ox + 1, 0, g.wh - 1);
         const int oy0 = clampi(oy, 0, g.hh - 1) * g.wh, oy1 = clampi(oy + 1, 0, g.hh - 1) * g.wh;
