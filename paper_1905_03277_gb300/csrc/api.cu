@@ -29,8 +29,11 @@ bool valid_desc(const hmfsr_burst_desc *d, hmfsr_status *why) {
     if (!d) return false;
     if (d->n_frames < 1 || d->n_frames > 4096) return false;
     if (d->height < 4 || d->width < 4 || (d->height & 1) || (d->width & 1)) return false;
+    // at most 65536 x 65536: a half-res plane stays below 2^31 texels (32-bit offsets)
     if (d->height > 65536 || d->width > 65536) return false;
     if (d->pitch_elems < d->width || (d->pitch_elems & 1)) return false;
+    // one frame holds fewer than 2^31 samples (32-bit offsets within a frame)
+    if ((long long)d->height * d->pitch_elems >= (1LL << 31)) return false;
     if (d->ref < 0 || d->ref >= d->n_frames) return false;
     // 3x3 sums of a 16-bit guide channel must fit 16 bits, Lq 16 bits
     if (d->white_level < 1 || d->white_level > 7281) return false;

@@ -93,7 +93,7 @@ __device__ __host__ inline int stage_k(int s) {
         case S_DOWN1: case S_DOWN2: case S_DOWN3: return 256;
         case S_LUMA: return 64;
         case S_PREP: return 16;
-        case S_ROB: return 4;
+        case S_ROB: return 2;
         case S_LK: return 16;
         case S_MERGE: return 32;
         case S_STRENGTH: return 8;
@@ -118,7 +118,7 @@ __device__ __host__ inline int stage_subitems(const BatchBurst &b, int s, int mw
         }
         case S_LK: return div_up(b.L.lty[0] * b.L.ltx[0], kLkTiles) * g.n;
         case S_STRENGTH: return div_up(g.n * g.ty * g.tx, kBatchThreads);
-        case S_ROB: return g.n > 1 ? div_up(g.wh, stage::kRobW) * div_up(g.hh, stage::kRobH) : 0;
+        case S_ROB: return div_up(g.wh, 4 * stage::kRobOut) * div_up(g.hh, stage::kRobStrip) * (g.n - 1);
         case S_MERGE: return div_up(b.wo, mw) * div_up(b.ho, mh);
         default: return 0;
     }
@@ -148,11 +148,7 @@ __device__ __forceinline__ void run_merge(const BatchBurst &b, int X, int Y) {
 }
 
 // one sub-item of one stage of burst b, by all 128 threads of the block
-union BatchSmem {
-    stage::RobSmem rob;
-};
-
-__device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int tid, int mw, int mh, BatchSmem &sm) {
+__device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int tid, int mw, int mh) {
     const Geom &g = b.g;
     const float2 *mv = reinterpret_cast<const float2 *>(b.motion);
     switch (s) {
@@ -202,10 +198,11 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
             stage::geo_entry(mv, g.n, g.ty * g.tx, g.ref, 2 * b.snum, b.P.geo, k * kBatchThreads + tid);
             break;
         case S_ROB: {
-            const int nx = div_up(g.wh, stage::kRobW);
-            const int by = k / nx, bx = k - by * nx;
-            stage::rob_block(b.P.s1, b.P.base_stats, mv, b.P.s_tile, g, b.c.t, b.P.rhat, sm.rob, bx, by,
-                             tid % stage::kRobW, tid / stage::kRobW);
+            const int nx = div_up(g.wh, 4 * stage::kRobOut), ny = div_up(g.hh, stage::kRobStrip);
+            const int fi = k / (nx * ny), r = k - fi * nx * ny, by = r / nx, bx = r - by * nx;
+            const int f = fi < g.ref ? fi : fi + 1;  // every frame but the base frame
+            stage::rob_strip(b.P.s1, b.P.base_stats, mv, b.P.s_tile, g, b.c.t, b.P.rhat,
+                             (bx * 4 + (tid >> 5)) * stage::kRobOut, by * stage::kRobStrip, f, tid & 31);
             break;
         }
         case S_MERGE: {
@@ -223,13 +220,12 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
 }
 
 // one queue item: stage_k(s) consecutive sub-items
-__device__ __forceinline__ void run_item(const BatchBurst &b, int s, int k, int tid, int mw, int mh, BatchSmem &sm) {
+__device__ __forceinline__ void run_item(const BatchBurst &b, int s, int k, int tid, int mw, int mh) {
     const int K = stage_k(s), nsub = stage_subitems(b, s, mw, mh);
     for (int j = 0; j < K; ++j) {
         const int sub = k * K + j;
         if (sub >= nsub) break;
-        run_sub(b, s, sub, tid, mw, mh, sm);
-        if (s == S_ROB) __syncthreads();  // the shared tile is reused by the next sub-item
+        run_sub(b, s, sub, tid, mw, mh);
     }
 }
 
@@ -251,7 +247,6 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
             int *ctrl, int *done, const int *__restrict__ totals, int mw, int mh, int spin_limit) {
     __shared__ int s_item, s_next, s_ok, s_seg;
     __shared__ unsigned int s_ready[kMaxCachedBursts];  // per burst: bit s set once stage s is complete
-    __shared__ BatchSmem sm;
     const int tid = threadIdx.x;
     for (int i = tid; i < kMaxCachedBursts; i += kBatchThreads) s_ready[i] = 0u;
     if (tid == 0) {
@@ -299,7 +294,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         if (item >= total || !s_ok) break;
         const Segment sg = segs[s_seg];
         const int b = sg.burst, s = sg.stage, k = item - sg.first;
-        run_item(bursts[b], s, k, tid, mw, mh, sm);
+        run_item(bursts[b], s, k, tid, mw, mh);
         __syncthreads();
         if (tid == 0) add_release(&done[b * S_COUNT + s], 1);
     }
@@ -394,7 +389,8 @@ void drop_graph(hmfsr_batch_plan_t *p) {
 bool batch_desc_ok(const hmfsr_burst_desc &d, const hmfsr_merge_params &m, const hmfsr_align_params &a, int sn, int sd) {
     if (d.n_frames < 1 || d.height < 32 || d.width < 32 || (d.height & 1) || (d.width & 1) || d.pitch_elems < d.width ||
         (d.pitch_elems & 1) || d.ref < 0 || d.ref >= d.n_frames || d.cfa != 0 || d.black_level != 0 ||
-        d.white_level < 1 || d.white_level > 7281)
+        d.white_level < 1 || d.white_level > 7281 || d.height > 65536 || d.width > 65536 ||
+        (long long)d.height * d.pitch_elems >= (1LL << 31))
         return false;
     if (m.tile != 16 || a.tile != 16 || a.n_levels < 1 || a.n_levels > 4 || a.lk_iters < 0 || a.lk_iters > 16)
         return false;

@@ -34,6 +34,13 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// 1/x on the SFU (rcp.approx, flush-to-zero): relative error ~2^-23; no range handling.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // sqrt on the SFU (sqrt.approx, flush-to-zero): relative error ~2^-23.
 __device__ __forceinline__ float fast_sqrt(float x) {
     float y;

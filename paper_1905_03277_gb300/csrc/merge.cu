@@ -9,7 +9,6 @@ namespace {
 
 using stage::kMergeW;
 using stage::kMergeH;
-using stage::kRobW;
 
 // 4 warps side by side: 128 texel columns x kPrepStrip rows of one frame
 __global__ void __launch_bounds__(128) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
@@ -24,12 +23,14 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
     stage::strength(motion, n, ty, tx, m_th, s1, s2, s_tile, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-__global__ void __launch_bounds__(kRobW * 4) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
-                                                   const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                                   Geom g, float t_thr, float *__restrict__ rhat) {
-    __shared__ stage::RobSmem sm;
-    stage::rob_block(s1, base_stats, motion, s_tile, g, t_thr, rhat, sm, blockIdx.x, blockIdx.y, threadIdx.x,
-                     threadIdx.y);
+// 4 warps side by side: 4 x kRobOut texel columns x kRobStrip rows of one frame
+// (blockIdx.z runs over the frames other than the base frame)
+__global__ void __launch_bounds__(128) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
+                                             const float2 *__restrict__ motion, const float *__restrict__ s_tile,
+                                             Geom g, float t_thr, float *__restrict__ rhat) {
+    const int frame = (int)blockIdx.z < g.ref ? (int)blockIdx.z : (int)blockIdx.z + 1;
+    stage::rob_strip(s1, base_stats, motion, s_tile, g, t_thr, rhat, (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut,
+                     blockIdx.y * stage::kRobStrip, frame, threadIdx.x & 31);
 }
 
 __global__ void k_geo(const float2 *__restrict__ motion, int n, int ntl, int ref, int Q, int4 *__restrict__ geo) {
@@ -89,7 +90,7 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
     if (g.n > 1)
-        k_rob<<<dim3(div_up(g.wh, kRobW), div_up(g.hh, stage::kRobH)), dim3(kRobW, 4), 0, s>>>(
+        k_rob<<<dim3(div_up(g.wh, 4 * stage::kRobOut), div_up(g.hh, stage::kRobStrip), g.n - 1), 128, 0, s>>>(
             P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat);
     return cudaGetLastError();
 }

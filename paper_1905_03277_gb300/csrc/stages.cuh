@@ -501,29 +501,30 @@ __device__ __forceinline__ float4 base_stats_of(const uint32_t (&S1)[3], const u
 // structure tensor -> kernel covariance (Eq. 3, Eq. 4, supplement S.1), from the exact
 // integer tensor {sum gx^2, sum gx gy, sum gy^2} of the four 2x2 sub-squares
 // --------------------------------------------------------------------------------------
+// inv_dtr = 1 / (16 WL D_tr)
 __device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, long long tc, const MergeConsts &c,
-                                                 int wl) {
+                                                 float inv_dtr) {
     // eigen-analysis: lambda1 = (tr + r)/2, dominant direction at angle theta with
     // cos 2theta = (a-c)/r, sin 2theta = 2b/r (theta = 0 when the tensor is isotropic)
     float tr = (float)(ta + tc);
     float amc = (float)(ta - tc), b2 = 2.f * (float)tb;
     float r = fast_sqrt(fmaf(amc, amc, b2 * b2));
     float cs = 1.f, sn = 0.f;
-    if (!(ta == tc && tb == 0)) { const float ir = __fdividef(1.f, r); cs = amc * ir; sn = b2 * ir; }
+    if (!(ta == tc && tb == 0)) { const float ir = fast_rcp(r); cs = amc * ir; sn = b2 * ir; }
     float l1 = 0.5f * (tr + r);
-    float A = (ta + tc == 0) ? 1.f : 1.f + fast_sqrt(__fdividef(r, tr));
+    float A = (ta + tc == 0) ? 1.f : 1.f + fast_sqrt(r * fast_rcp(tr));
     // lambda in units of luminance normalised to [0,1]: sqrt(l1_norm) = sqrt(l1) / (16 WL)
-    float D = fminf(fmaxf(fmaf(-fast_sqrt(l1), __fdividef(1.f, 16.f * (float)wl * c.d_tr), 1.f) + c.d_th, 0.f), 1.f);
+    float D = fminf(fmaxf(fmaf(-fast_sqrt(l1), inv_dtr, 1.f) + c.d_th, 0.f), 1.f);
     float kh_al = c.k_detail * (c.k_stretch * A);
-    float kh_ac = __fdividef(c.k_detail, c.k_shrink * A);
+    float kh_ac = c.k_detail * fast_rcp(c.k_shrink * A);
     float kd = c.k_detail * c.k_denoise;
     float s_al = fmaf(1.f - D, kh_al, D * kd);   // standard deviations before squaring
     float s_ac = fmaf(1.f - D, kh_ac, D * kd);
     float k_al = s_al * s_al, k_ac = s_ac * s_ac;
     // half-angle unit vector e1 = (cos theta, sin theta), without cancellation
     float e1x, e1y;
-    if (cs >= 0.f) { e1x = fast_sqrt(fmaf(0.5f, cs, 0.5f)); e1y = __fdividef(sn, 2.f * e1x); }
-    else { e1y = fast_sqrt(fmaf(-0.5f, cs, 0.5f)); e1x = __fdividef(sn, 2.f * e1y); }
+    if (cs >= 0.f) { e1x = fast_sqrt(fmaf(0.5f, cs, 0.5f)); e1y = sn * fast_rcp(2.f * e1x); }
+    else { e1y = fast_sqrt(fmaf(-0.5f, cs, 0.5f)); e1x = sn * fast_rcp(2.f * e1y); }
     // Omega = k_across e1 e1^T + k_along e2 e2^T (stretch along the edge, e2)
     //       = min I + |k_along - k_across| u u^T with u = e2 if k_along >= k_across else e1
     float dh = (1.f - D) * (kh_al - kh_ac) * (s_al + s_ac);  // k_along - k_across, no cancellation
@@ -573,9 +574,9 @@ __device__ __forceinline__ PrepRow prep_fetch(const uint16_t *__restrict__ fr, i
 
 // one raw row pair of the strip (strip row r = -1 .. kPrepStrip); emits texel row r - 1
 __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r, int lane, bool is_ref, bool out_col,
-                                         int v0, const Geom &g, const MergeConsts &c, int f, int u,
-                                         uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                         float4 *__restrict__ kern) {
+                                         int v0, const Geom &g, const MergeConsts &c, float inv_dtr, int u,
+                                         uint2 *__restrict__ s1f, float4 *__restrict__ base_stats,
+                                         float4 *__restrict__ kernf) {
     const uint32_t R = p.a & 0xffffu, G = (p.a >> 16) + (p.b & 0xffffu), B = p.b >> 16;
     const uint32_t c0 = R | (B << 16), c1 = G | ((R + G + B) << 16);  // {R, B}, {G, Lq}
     uint32_t l0 = __shfl_up_sync(0xffffffffu, c0, 1), l1 = __shfl_up_sync(0xffffffffu, c1, 1);
@@ -610,16 +611,16 @@ __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r,
     if (r >= 1 && out_col) {
         const int v = v0 + r - 1;
         if (v < g.hh) {
-            const size_t hw = (size_t)g.hh * g.wh, idx = (size_t)v * g.wh + u;
+            const int idx = v * g.wh + u;
             const uint32_t srb = st.rb[0] + st.rb[1] + rb, sg = st.gs[0] + st.gs[1] + gs;
-            s1[(size_t)f * hw + idx] = make_uint2(srb, sg);
+            s1f[idx] = make_uint2(srb, sg);
             if (is_ref) {
                 const uint32_t S1[3] = {srb & 0xffffu, sg, srb >> 16};
                 const uint32_t S2[3] = {st.q[0][0] + st.q[1][0] + q[0], st.q[0][1] + st.q[1][1] + q[1],
                                         st.q[0][2] + st.q[1][2] + q[2]};
                 base_stats[idx] = base_stats_of(S1, S2, c, g.wl);
             }
-            kern[(size_t)f * hw + idx] = kern_of_tensor(st.pa + pa, st.pb + pb, st.pc + pc, c, g.wl);
+            kernf[idx] = kern_of_tensor(st.pa + pa, st.pb + pb, st.pc + pc, c, inv_dtr);
         }
     }
     st.rb[0] = st.rb[1]; st.rb[1] = rb;
@@ -641,6 +642,10 @@ __device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, c
     const bool halo = (lane == 0 || lane == 31);
     const int uh = clampi(lane == 0 ? u0 - 1 : u0 + 32, 0, g.wh - 1);
     const bool is_ref = (f == g.ref), out_col = u < g.wh;
+    const size_t hw = (size_t)g.hh * g.wh;
+    uint2 *s1f = s1 + (size_t)f * hw;
+    float4 *kernf = kern + (size_t)f * hw;
+    const float inv_dtr = fast_rcp(16.f * (float)g.wl * c.d_tr);
     PrepState st;
     st.rb[0] = st.rb[1] = st.gs[0] = st.gs[1] = 0u;
 #pragma unroll
@@ -652,10 +657,10 @@ __device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, c
     for (int r = -1; r <= kPrepStrip; r += 2) {
         const PrepRow cur0 = p0;
         p0 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 + r + 2);
-        prep_row(cur0, st, r, lane, is_ref, out_col, v0, g, c, f, u, s1, base_stats, kern);
+        prep_row(cur0, st, r, lane, is_ref, out_col, v0, g, c, inv_dtr, u, s1f, base_stats, kernf);
         const PrepRow cur1 = p1;
         p1 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 + r + 3);
-        prep_row(cur1, st, r + 1, lane, is_ref, out_col, v0, g, c, f, u, s1, base_stats, kern);
+        prep_row(cur1, st, r + 1, lane, is_ref, out_col, v0, g, c, inv_dtr, u, s1f, base_stats, kernf);
     }
 }
 
@@ -683,132 +688,115 @@ __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int 
 }
 
 // --------------------------------------------------------------------------------------
-// robustness (Eq. 5, 6) of every frame on one 32 x 16 block of base texels with a
-// 2-texel halo, then the 5x5 minimum (Eq. 9).  The base frame's sums and statistics are
-// read once into shared memory and serve all frames; per frame, each motion tile the
-// region touches gets its integer offset, bilinear weights and robustness scale once.
-// Each of the 32 x 4 threads takes the minimum for 4 texels down one column from 5-wide
-// row minima.  Every thread of the block calls this with the same block coordinates (it
-// synchronises the block).
+// robustness (Eq. 5, 6) and its 5x5 minimum (Eq. 9) on one strip of base texels of one
+// frame: one warp, kRobOut columns, kRobStrip rows.  Lane l evaluates R at column
+// u0 - 2 + l for the rows v0 - 2 .. v0 + kRobStrip + 1, walking down: within a motion
+// tile the bilinear neighbours of the row below are the bottom neighbours of this row,
+// so each row reads two new sums instead of four.  The 5-wide row minimum comes from
+// the next four lanes (lanes 0 .. kRobOut - 1 write); a rolling window of five row
+// minima gives the column minimum.  Every lane of the warp calls this.
 // --------------------------------------------------------------------------------------
-constexpr int kRobW = 32, kRobH = 16, kRobRows = kRobH / 4;
-constexpr int kRobPW = kRobW + 4, kRobPH = kRobH + 4, kRobP = kRobPW * kRobPH;
-constexpr int kRobMaxTiles = 64;  // (36 / 4 + 1) x (20 / 4 + 1) for the smallest tile (4 texels)
+constexpr int kRobOut = 28, kRobStrip = 64;
 constexpr float kLog2e = 1.44269504088896340736f;
 
-struct RobSmem {
-    float4 st[kRobP];          // base statistics
-    uint2 sb[kRobP];           // base 3x3 sums
-    int lt[kRobP];             // the position's motion tile within the region, -1 outside the frame
-    float R[kRobPH][kRobPW];
-    float4 tw[kRobMaxTiles];   // per tile, this frame: bilinear weights b00, b10, b01, b11
-    int4 to[kRobMaxTiles];     // per tile, this frame: {integer offset x, y, robustness scale bits, 0}
-};
+// Wiener-shrunk squared difference of one channel (Eq. 6): (d d^2 / (d^2 + dmd^2))^2 added
+// to dd; a zero denominator means a zero difference
+__device__ __forceinline__ float wiener_add(float d, float dmd2, float dd) {
+    const float d2 = d * d;
+    const float w = (d * d2) * fast_rcp(fmaxf(d2 + dmd2, 1e-30f));
+    return fmaf(w, w, dd);
+}
 
-__device__ __forceinline__ void rob_block(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
+__device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                          const Geom &g, float t_thr, float *__restrict__ rhat, RobSmem &sm, int bx,
-                                          int by, int tx, int ty) {
-    const int u0 = bx * kRobW - 2, v0 = by * kRobH - 2, tid = ty * kRobW + tx;
+                                          const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
+                                          int frame, int lane) {
     const size_t hw = (size_t)g.hh * g.wh;
-    const uint2 *S1b = s1 + (size_t)g.ref * hw;
+    const int wh = g.wh, u = u0 - 2 + lane;
+    const bool col_ok = u >= 0 && u < wh;
+    const int uc = clampi(u, 0, wh - 1);
     const int ht = g.tile / 2;  // motion tile in texels
-    // motion tiles the region touches (a tile index is clamped to the last tile)
-    const int tx_lo = min(max(u0, 0) / ht, g.tx - 1), tx_hi = min(min(u0 + kRobPW - 1, g.wh - 1) / ht, g.tx - 1);
-    const int ty_lo = min(max(v0, 0) / ht, g.ty - 1), ty_hi = min(min(v0 + kRobPH - 1, g.hh - 1) / ht, g.ty - 1);
-    const int ntx = tx_hi - tx_lo + 1, nt = ntx * (ty_hi - ty_lo + 1);
-    // each thread only reads back the entries it wrote here: no barrier needed
-    for (int k = tid; k < kRobP; k += kRobW * 4) {
-        const int ly = k / kRobPW, lx = k - ly * kRobPW;
-        const int u = u0 + lx, v = v0 + ly;
-        int lt = -1;
-        if (u >= 0 && u < g.wh && v >= 0 && v < g.hh) {
-            lt = (min(v / ht, g.ty - 1) - ty_lo) * ntx + (min(u / ht, g.tx - 1) - tx_lo);
-            sm.sb[k] = S1b[(size_t)v * g.wh + u];
-            sm.st[k] = base_stats[(size_t)v * g.wh + u];
-        }
-        sm.lt[k] = lt;
-    }
-    const int uo = bx * kRobW + tx, vo = by * kRobH + ty * kRobRows;
-    for (int frame = 0; frame < g.n; ++frame) {
-        if (frame == g.ref) continue;
-        if (tid < nt) {
-            const int gt = (ty_lo + tid / ntx) * g.tx + tx_lo + tid % ntx;
-            const float2 mv = motion[(size_t)frame * g.ty * g.tx + gt];
-            const float s = s_tile[(size_t)frame * g.ty * g.tx + gt];
-            // aligned position (u, v) + v/2 split into an exact integer part and fraction
-            const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
-            const float flx = floorf(hx), fly = floorf(hy);
-            const float fx = hx - flx, fy = hy - fly;
-            sm.tw[tid] = make_float4((1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy);
-            sm.to[tid] = make_int4((int)flx, (int)fly, __float_as_int(s), 0);
-        }
-        __syncthreads();
-        const uint2 *S1n = s1 + (size_t)frame * hw;
-        for (int k = tid; k < kRobP; k += kRobW * 4) {
-            const int ly = k / kRobPW, lx = k - ly * kRobPW;
-            const int lt = sm.lt[k];
-            float R = kBig;
-            if (lt >= 0) {
-                const float4 bw = sm.tw[lt];
-                const int4 to = sm.to[lt];
-                const int ix = u0 + lx + to.x, iy = v0 + ly + to.y;
-                const int x0 = clampi(ix, 0, g.wh - 1), x1 = clampi(ix + 1, 0, g.wh - 1);
-                const uint2 *r0 = S1n + (size_t)clampi(iy, 0, g.hh - 1) * g.wh;
-                const uint2 *r1 = S1n + (size_t)clampi(iy + 1, 0, g.hh - 1) * g.wh;
-                const uint2 sb = sm.sb[k];
-                const uint2 n00 = r0[x0], n10 = r0[x1], n01 = r1[x0], n11 = r1[x1];
-                // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9; the
-                // differences of exact integers (< 2^17) are exact in FP32
-                const float rb = u16f(sb.x & 0xffffu), bb = u16f(sb.x >> 16), gb = u16f(sb.y);
-                float dR = fmaf(bw.x, rb - u16f(n00.x & 0xffffu), fmaf(bw.y, rb - u16f(n10.x & 0xffffu),
-                           fmaf(bw.z, rb - u16f(n01.x & 0xffffu), bw.w * (rb - u16f(n11.x & 0xffffu)))));
-                float dB = fmaf(bw.x, bb - u16f(n00.x >> 16), fmaf(bw.y, bb - u16f(n10.x >> 16),
-                           fmaf(bw.z, bb - u16f(n01.x >> 16), bw.w * (bb - u16f(n11.x >> 16)))));
-                float dG = fmaf(bw.x, gb - u16f(n00.y), fmaf(bw.y, gb - u16f(n10.y),
-                           fmaf(bw.z, gb - u16f(n01.y), bw.w * (gb - u16f(n11.y)))));
+    const int txi = min(uc / ht, g.tx - 1);
+    const uint2 *S1b = s1 + (size_t)g.ref * hw;
+    const uint2 *S1n = s1 + (size_t)frame * hw;
+    const float2 *mvf = motion + (size_t)frame * g.ty * g.tx + txi;
+    const float *stf = s_tile + (size_t)frame * g.ty * g.tx + txi;
+    float *out = rhat + (size_t)frame * hw;
+    // tile row of the first row and the position within it, advanced row by row
+    const int vfirst = max(v0 - 2, 0);
+    int tq = vfirst / ht, tr = vfirst - tq * ht;
+    int cur_tile = -1, fly = 0, x0 = 0, x1 = 0;
+    float b00 = 0.f, b10 = 0.f, b01 = 0.f, b11 = 0.f, sc = 0.f;
+    uint2 nt0 = make_uint2(0u, 0u), nt1 = nt0, nb0 = nt0, nb1 = nt0;  // sums at the top / bottom neighbours
+    bool have_prev = false;
+    float h0 = kBig, h1 = kBig, h2 = kBig, h3 = kBig;  // row minima of the four rows above
+    int off = (v0 - 2) * wh + uc;                        // this lane's texel in the row (32-bit offsets)
+    for (int e = 0; e < kRobStrip + 4; ++e, off += wh) {
+        const int v = v0 - 2 + e;
+        float R = kBig;
+        if (v >= 0 && v < g.hh) {  // the same for the whole warp
+            const int tyi = min(tq, g.ty - 1);
+            if (tyi != cur_tile) {
+                cur_tile = tyi;
+                const float2 mv = mvf[tyi * g.tx];
+                sc = stf[tyi * g.tx];
+                // aligned position (u, v) + v/2 split into an exact integer part and fraction
+                const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
+                const float flx = floorf(hx), flyf = floorf(hy);
+                const float fx = hx - flx, fy = hy - flyf;
+                b00 = (1.f - fx) * (1.f - fy); b10 = fx * (1.f - fy); b01 = (1.f - fx) * fy; b11 = fx * fy;
+                fly = (int)flyf;
+                x0 = clampi(uc + (int)flx, 0, wh - 1);
+                x1 = clampi(uc + (int)flx + 1, 0, wh - 1);
+                have_prev = false;
+            }
+            if (++tr == ht) { tr = 0; ++tq; }
+            const int iy = v + fly;
+            if (have_prev) {
+                nt0 = nb0;
+                nt1 = nb1;
+            } else {
+                const int o0 = clampi(iy, 0, g.hh - 1) * wh;
+                nt0 = S1n[o0 + x0];
+                nt1 = S1n[o0 + x1];
+            }
+            const int o1 = clampi(iy + 1, 0, g.hh - 1) * wh;
+            nb0 = S1n[o1 + x0];
+            nb1 = S1n[o1 + x1];
+            have_prev = true;
+            if (col_ok) {
+                const uint2 sb = S1b[off];
+                const float4 st = base_stats[off];
+                // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9, from exact
+                // integer differences
+                const int ri = (int)(sb.x & 0xffffu), bi = (int)(sb.x >> 16), gi = (int)sb.y;
+                float dR = fmaf(b00, (float)(ri - (int)(nt0.x & 0xffffu)), fmaf(b10, (float)(ri - (int)(nt1.x & 0xffffu)),
+                           fmaf(b01, (float)(ri - (int)(nb0.x & 0xffffu)), b11 * (float)(ri - (int)(nb1.x & 0xffffu)))));
+                float dB = fmaf(b00, (float)(bi - (int)(nt0.x >> 16)), fmaf(b10, (float)(bi - (int)(nt1.x >> 16)),
+                           fmaf(b01, (float)(bi - (int)(nb0.x >> 16)), b11 * (float)(bi - (int)(nb1.x >> 16)))));
+                float dG = fmaf(b00, (float)(gi - (int)nt0.y), fmaf(b10, (float)(gi - (int)nt1.y),
+                           fmaf(b01, (float)(gi - (int)nb0.y), b11 * (float)(gi - (int)nb1.y))));
                 dR *= (1.f / 9.f);
                 dB *= (1.f / 9.f);
                 dG *= (1.f / 18.f);
-                const float4 st = sm.st[k];
-                float dd = 0.f;
-                {
-                    const float d2 = dR * dR, den = d2 + st.y;
-                    const float d = den > 0.f ? __fdividef(dR * d2, den) : 0.f;  // Wiener shrinkage (Eq. 6)
-                    dd = fmaf(d, d, dd);
-                }
-                {
-                    const float d2 = dG * dG, den = d2 + st.z;
-                    const float d = den > 0.f ? __fdividef(dG * d2, den) : 0.f;
-                    dd = fmaf(d, d, dd);
-                }
-                {
-                    const float d2 = dB * dB, den = d2 + st.w;
-                    const float d = den > 0.f ? __fdividef(dB * d2, den) : 0.f;
-                    dd = fmaf(d, d, dd);
-                }
+                const float dd = wiener_add(dB, st.w, wiener_add(dG, st.z, wiener_add(dR, st.y, 0.f)));
                 // Eq. 5: s exp(-dd / sigma^2) - t, clamped to [0, 1]
-                const float e = fast_exp2(-__fdividef(dd, st.x) * kLog2e);
-                R = fminf(fmaxf(fmaf(__int_as_float(to.z), e, -t_thr), 0.f), 1.f);
+                const float ex = fast_exp2(-(dd * fast_rcp(st.x)) * kLog2e);
+                R = fminf(fmaxf(fmaf(sc, ex, -t_thr), 0.f), 1.f);
             }
-            sm.R[ly][lx] = R;
+        } else {
+            have_prev = false;
         }
-        __syncthreads();
-        float hm[kRobRows + 4];
-#pragma unroll
-        for (int j = 0; j < kRobRows + 4; ++j) {
-            const float *row = sm.R[ty * kRobRows + j] + tx;
-            hm[j] = fminf(fminf(fminf(row[0], row[1]), fminf(row[2], row[3])), row[4]);
+        // 5-wide row minimum from lanes l .. l + 4
+        float m = fminf(R, __shfl_down_sync(0xffffffffu, R, 1));
+        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 2));
+        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 3));
+        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 4));
+        if (e >= 4) {
+            const int vo = v - 2, uo = u0 + lane;
+            if (lane < kRobOut && uo < wh && vo < g.hh) out[vo * wh + uo] = fminf(fminf(fminf(h0, h1), fminf(h2, h3)), m);
         }
-        if (uo < g.wh) {
-#pragma unroll
-            for (int r = 0; r < kRobRows; ++r) {
-                if (vo + r >= g.hh) break;
-                const float m = fminf(fminf(fminf(hm[r], hm[r + 1]), fminf(hm[r + 2], hm[r + 3])), hm[r + 4]);
-                rhat[(size_t)frame * hw + (size_t)(vo + r) * g.wh + uo] = m;
-            }
-        }
-        __syncthreads();  // the next frame reuses sm.R and the tile tables
+        h0 = h1; h1 = h2; h2 = h3; h3 = m;
     }
 }
 
@@ -832,16 +820,71 @@ __device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int p
     for (int j = 0; j < 3; ++j) {
         const int yy = ky - 1 + j;
         const bool yok = !kBorder || ((unsigned)yy < (unsigned)h);
-        const uint16_t *row = fr + (size_t)(kBorder ? clampi(yy, 0, h - 1) : yy) * pitch;
+        const int row = (kBorder ? clampi(yy, 0, h - 1) : yy) * pitch;  // 32-bit: frames hold < 2^31 samples
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int xx = kx - 1 + i;
-            rv[j][i] = u16f(__ldg(row + (kBorder ? clampi(xx, 0, w - 1) : xx)));
+            rv[j][i] = (float)__ldg(fr + row + (kBorder ? clampi(xx, 0, w - 1) : xx));
             const float qq = fmaf(Ex[i], dys[j], Ax[i] + Cy[j]);
             if (kBorder) q[j][i] = (yok && (unsigned)xx < (unsigned)w) ? qq : INFINITY;
             else q[j][i] = qq;
         }
     }
+}
+
+// running sums of one output pixel: Eq. 1's numerator and denominator per channel, each
+// scaled by 2^-m with a per-channel exponent shift m (log2 units)
+struct PixelAcc {
+    float numR = 0.f, numG = 0.f, numB = 0.f, denR = 0.f, denG = 0.f, denB = 0.f;
+    float mR = kBig, mG = kBig, mB = kBig;
+};
+
+// One frame's contribution (Eq. 1-2) to one pixel from the weight exponents q' and
+// values of its 3x3 window; cg: the window's centre sample is green; sw: its centre row
+// is odd (the Bayer arrangement of the window).
+__device__ __forceinline__ void accumulate_frame(const float (&q)[3][3], const float (&rv)[3][3], float rh, bool cg,
+                                                 bool sw, PixelAcc &a) {
+    // per-class minima: C = centre, H = (+-1, 0), V = (0, +-1), K = corners
+    const float qC = q[1][1];
+    const float mH = fminf(q[1][0], q[1][2]), mV = fminf(q[0][1], q[2][1]);
+    const float mK = fminf(fminf(q[0][0], q[0][2]), fminf(q[2][0], q[2][2]));
+    const float f1 = cg ? mH : qC, f2 = cg ? mV : mK, fG = cg ? fminf(qC, mK) : fminf(mH, mV);
+    const float fR = sw ? f2 : f1, fB = sw ? f1 : f2;
+    if (fR < a.mR - 64.f || fG < a.mG - 64.f || fB < a.mB - 64.f) {
+        // move a channel's shift down to this frame's minimum (rare after the base frame)
+        if (fR < a.mR - 64.f) { const float s = fast_exp2(fR - a.mR); a.numR *= s; a.denR *= s; a.mR = fR; }
+        if (fG < a.mG - 64.f) { const float s = fast_exp2(fG - a.mG); a.numG *= s; a.denG *= s; a.mG = fG; }
+        if (fB < a.mB - 64.f) { const float s = fast_exp2(fB - a.mB); a.numB *= s; a.denB *= s; a.mB = fB; }
+    }
+    const float mS1 = sw ? a.mB : a.mR, mS2 = sw ? a.mR : a.mB;
+    const float sC = cg ? a.mG : mS1, sK = cg ? a.mG : mS2, sH = cg ? mS1 : a.mG, sV = cg ? mS2 : a.mG;
+    float w;
+    w = fast_exp2(sC - q[1][1]);
+    const float nC = w * rv[1][1], dC = w;
+    w = fast_exp2(sH - q[1][0]);
+    float nH = w * rv[1][0], dH = w;
+    w = fast_exp2(sH - q[1][2]);
+    nH = fmaf(w, rv[1][2], nH); dH += w;
+    w = fast_exp2(sV - q[0][1]);
+    float nV = w * rv[0][1], dV = w;
+    w = fast_exp2(sV - q[2][1]);
+    nV = fmaf(w, rv[2][1], nV); dV += w;
+    w = fast_exp2(sK - q[0][0]);
+    float nK = w * rv[0][0], dK = w;
+    w = fast_exp2(sK - q[0][2]);
+    nK = fmaf(w, rv[0][2], nK); dK += w;
+    w = fast_exp2(sK - q[2][0]);
+    nK = fmaf(w, rv[2][0], nK); dK += w;
+    w = fast_exp2(sK - q[2][2]);
+    nK = fmaf(w, rv[2][2], nK); dK += w;
+    const float n1 = cg ? nH : nC, n2 = cg ? nV : nK, nG = cg ? nC + nK : nH + nV;
+    const float d1 = cg ? dH : dC, d2 = cg ? dV : dK, dG = cg ? dC + dK : dH + dV;
+    a.numR = fmaf(rh, sw ? n2 : n1, a.numR);
+    a.denR = fmaf(rh, sw ? d2 : d1, a.denR);
+    a.numB = fmaf(rh, sw ? n1 : n2, a.numB);
+    a.denB = fmaf(rh, sw ? d1 : d2, a.denB);
+    a.numG = fmaf(rh, nG, a.numG);
+    a.denG = fmaf(rh, dG, a.denG);
 }
 
 // floor(a / B) for B > 0: an arithmetic shift when B is a compile-time power of two,
@@ -883,7 +926,7 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
                                          const Geom &g, const float4 *__restrict__ kern,
                                          const float *__restrict__ rhat_planes, int snum_rt, int sden_rt, int ho, int wo,
                                          float *__restrict__ rgb, float *__restrict__ den_out, int X, int Y) {
-    if (X >= wo || Y >= ho) return;
+    if (X < 0 || Y < 0 || X >= wo || Y >= ho) return;
     constexpr int QC = 2 * SN, Q2C = 4 * SN;
     const int snum = SN > 0 ? SN : snum_rt, sden = SD > 0 ? SD : sden_rt;
     const int Q = 2 * snum, Q2 = 4 * snum;
@@ -908,8 +951,8 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         return fmaf(rw00, __ldg(Rp + r00), fmaf(rw10, __ldg(Rp + r10), fmaf(rw01, __ldg(Rp + r01), rw11 * __ldg(Rp + r11))));
     };
 
-    float numR = 0.f, numG = 0.f, numB = 0.f, denR = 0.f, denG = 0.f, denB = 0.f;
-    float mR = kBig, mG = kBig, mB = kBig;  // per-channel exponent shifts (log2 units)
+    PixelAcc acc;
+    const size_t fstride = (size_t)g.h * g.pitch;
 
     // frames in the order base frame, then the others; the next frame's geometry and
     // robustness are fetched while this one is merged
@@ -940,8 +983,8 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         const int ox0 = clampi(ox, 0, g.wh - 1), ox1 = clampi(ox + 1, 0, g.wh - 1);
         const int oy0 = clampi(oy, 0, g.hh - 1) * g.wh, oy1 = clampi(oy + 1, 0, g.hh - 1) * g.wh;
         const float4 *K = kern + (size_t)f * hw;
-        const float4 t0 = __ldg(K + oy0 + ox0), t1 = __ldg(K + oy0 + ox1);
-        const float4 t2 = __ldg(K + oy1 + ox0), t3 = __ldg(K + oy1 + ox1);
+        const float4 t0 = __ldg(K + (oy0 + ox0)), t1 = __ldg(K + (oy0 + ox1));
+        const float4 t2 = __ldg(K + (oy1 + ox0)), t3 = __ldg(K + (oy1 + ox1));
         const float b0 = (1.f - ofx) * (1.f - ofy), b1 = ofx * (1.f - ofy), b2 = (1.f - ofx) * ofy, b3 = ofx * ofy;
         // Omega = a I + M, M = sum_k g_k u_k u_k^T;  adj(Omega) = a I + sum_k g_k u_k^perp u_k^perp^T
         // (the library is built without automatic FMA contraction; the fused
@@ -963,7 +1006,7 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         const float s1 = fmaf(g2 * c12, c12, (g3 * c13) * c13);
         const float detM = fmaf(g0, s0, fmaf(g1, s1, (g2 * g3) * (c23 * c23)));
         const float det = fmaf(a, a + Gs, detM);
-        const float sc = __fdividef(kHalfLog2e, det);
+        const float sc = kHalfLog2e * fast_rcp(det);
         // q'(d) = (d^T adj(Omega) d) / det * log2(e)/2: weight = 2^-q'
         const float Bxx = (a + Nxx) * sc, Byy = (a + Nyy) * sc, Bxy2 = 2.f * Nxy * sc;
         const float dxs[3] = {dx0 - 1.f, dx0, dx0 + 1.f};
@@ -976,64 +1019,23 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
             Cy[i] = Byy * dys[i] * dys[i];
         }
         // the 3x3 Bayer neighbourhood; samples outside the frame are left out
-        const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
+        const uint16_t *fr = burst + (size_t)f * fstride;
         float q[3][3], rv[3][3];
         if ((unsigned)(kx - 1) < (unsigned)(g.w - 2) && (unsigned)(ky - 1) < (unsigned)(g.h - 2))
             gather3x3<false>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
         else
             gather3x3<true>(fr, g.pitch, g.h, g.w, kx, ky, Ax, Ex, Cy, dys, q, rv);
-        // per-class minima: C = centre, H = (+-1, 0), V = (0, +-1), K = corners
-        const float qC = q[1][1];
-        const float mH = fminf(q[1][0], q[1][2]), mV = fminf(q[0][1], q[2][1]);
-        const float mK = fminf(fminf(q[0][0], q[0][2]), fminf(q[2][0], q[2][2]));
-        // CFA mapping: cg = centre is green; sw = centre row is odd
-        const bool cg = ((kx ^ ky) & 1) != 0, sw = (ky & 1) != 0;
-        const float f1 = cg ? mH : qC, f2 = cg ? mV : mK, fG = cg ? fminf(qC, mK) : fminf(mH, mV);
-        const float fR = sw ? f2 : f1, fB = sw ? f1 : f2;
-        if (fR < mR - 64.f || fG < mG - 64.f || fB < mB - 64.f) {
-            // move a channel's shift down to this frame's minimum (rare after the base frame)
-            if (fR < mR - 64.f) { const float s = fast_exp2(fR - mR); numR *= s; denR *= s; mR = fR; }
-            if (fG < mG - 64.f) { const float s = fast_exp2(fG - mG); numG *= s; denG *= s; mG = fG; }
-            if (fB < mB - 64.f) { const float s = fast_exp2(fB - mB); numB *= s; denB *= s; mB = fB; }
-        }
-        const float mS1 = sw ? mB : mR, mS2 = sw ? mR : mB;
-        const float sC = cg ? mG : mS1, sK = cg ? mG : mS2, sH = cg ? mS1 : mG, sV = cg ? mS2 : mG;
-        float w;
-        w = fast_exp2(sC - q[1][1]);
-        const float nC = w * rv[1][1], dC = w;
-        w = fast_exp2(sH - q[1][0]);
-        float nH = w * rv[1][0], dH = w;
-        w = fast_exp2(sH - q[1][2]);
-        nH = fmaf(w, rv[1][2], nH); dH += w;
-        w = fast_exp2(sV - q[0][1]);
-        float nV = w * rv[0][1], dV = w;
-        w = fast_exp2(sV - q[2][1]);
-        nV = fmaf(w, rv[2][1], nV); dV += w;
-        w = fast_exp2(sK - q[0][0]);
-        float nK = w * rv[0][0], dK = w;
-        w = fast_exp2(sK - q[0][2]);
-        nK = fmaf(w, rv[0][2], nK); dK += w;
-        w = fast_exp2(sK - q[2][0]);
-        nK = fmaf(w, rv[2][0], nK); dK += w;
-        w = fast_exp2(sK - q[2][2]);
-        nK = fmaf(w, rv[2][2], nK); dK += w;
-        const float n1 = cg ? nH : nC, n2 = cg ? nV : nK, nG = cg ? nC + nK : nH + nV;
-        const float d1 = cg ? dH : dC, d2 = cg ? dV : dK, dG = cg ? dC + dK : dH + dV;
-        numR = fmaf(rh, sw ? n2 : n1, numR);
-        denR = fmaf(rh, sw ? d2 : d1, denR);
-        numB = fmaf(rh, sw ? n1 : n2, numB);
-        denB = fmaf(rh, sw ? d1 : d2, denB);
-        numG = fmaf(rh, nG, numG);
-        denG = fmaf(rh, dG, denG);
+        // Bayer arrangement of the window: cg = centre sample is green; sw = centre row is odd
+        accumulate_frame(q, rv, rh, ((kx ^ ky) & 1) != 0, (ky & 1) != 0, acc);
     }
     const size_t po = (size_t)ho * wo, o = (size_t)Y * wo + X;
-    rgb[o] = numR / denR;
-    rgb[po + o] = numG / denG;
-    rgb[2 * po + o] = numB / denB;
+    rgb[o] = acc.numR / acc.denR;
+    rgb[po + o] = acc.numG / acc.denG;
+    rgb[2 * po + o] = acc.numB / acc.denB;
     if (kDen) {
-        den_out[o] = log2f(denR) - mR;
-        den_out[po + o] = log2f(denG) - mG;
-        den_out[2 * po + o] = log2f(denB) - mB;
+        den_out[o] = log2f(acc.denR) - acc.mR;
+        den_out[po + o] = log2f(acc.denG) - acc.mG;
+        den_out[2 * po + o] = log2f(acc.denB) - acc.mB;
     }
 }
 

@@ -73,10 +73,10 @@ def lk_conditioned(raw_np, ref, tile, floor=1e-6):
     return lmin > floor * np.maximum(lmax, 1e-30) * 1e3
 
 
-def check_align(raw, dev, ref=0, tile=16, **kw):
+def check_align(raw, dev, ref=0, tile=16, white_level=4095, **kw):
     raw_np = raw.numpy()
     ap = hm.AlignParams(tile=tile, **kw)
-    g_motion, g_int = hm.align(raw.to(dev), ref, ap, with_int=True)
+    g_motion, g_int = hm.align(raw.to(dev), ref, ap, with_int=True, white_level=white_level)
     mi, mf, fl, _ = oracle.align(raw_np, ref=ref, tile=tile, n_levels=ap.n_levels, radius=ap.radius,
                                  lk_iters=ap.lk_iters)
     g_int = g_int.cpu().numpy()
@@ -105,6 +105,18 @@ def test_align_ragged_sizes_and_ref(dev):
     check_align(b["raw"], dev, ref=1, tile=8, n_levels=2, lk_iters=5)
     check_align(b["raw"], dev, ref=3, tile=64, n_levels=3, radius=(0, 7, 5, 4), lk_iters=1)
     check_align(b["raw"], dev, ref=0, radius=(3, 6, 2, 0), lk_iters=0)
+
+
+def test_align_full_swing_13_bit(dev):
+    # 13-bit frames of black and white 16-px blocks: a misaligned level-0 tile row sums
+    # 8 squared differences of ~29000, beyond 2^32; the search must stay exact
+    rng = np.random.default_rng(1905_03277 + 31)
+    n, h, w, wl = 4, 128, 192, 7281
+    img = np.kron((rng.random((h // 16, w // 16)) > 0.5) * float(wl), np.ones((16, 16)))
+    frames = [np.roll(img, tuple(rng.integers(-6, 7, size=2)), axis=(0, 1)) for _ in range(n)]
+    raw = np.clip(np.stack(frames) + rng.normal(0.0, 20.0, (n, h, w)), 0, wl).astype(np.uint16)
+    check_align(torch.from_numpy(raw), dev, white_level=wl)
+
 
 
 # --------------------------------------------------------------------------------------
