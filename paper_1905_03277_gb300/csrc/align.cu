@@ -59,7 +59,7 @@ __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, i
 
 static const int kFactors[3] = {2, 4, 4};
 
-// Block matching of one level: rows outermost for small radii; the offsets dy spread
+// Block matching of one level: rows outermost for small radii and tiles; the offsets dy spread
 // over lanes when the level has too few tiles to fill the GPU one thread per tile.
 constexpr int kSplitBelow = 152 * 256;  // tiles x frames
 
@@ -68,7 +68,7 @@ static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, boo
     const int tiles = L.lty[l] * L.ltx[l];
     const int2 *parent = top ? nullptr : L.vec[l + 1];
     const int pty = top ? 0 : L.lty[l + 1], ptx = top ? 0 : L.ltx[l + 1];
-    if constexpr (RAD <= 2) {
+    if constexpr (RAD <= 2 && T <= 8) {
         k_ssd_rows<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
                                                                      parent, pty, ptx, fsh, ref, L.vec[l]);
     } else {

@@ -19,7 +19,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "stages.cuh"
+#include "accumulate.cuh"
 
 namespace hmfsr {
 namespace {

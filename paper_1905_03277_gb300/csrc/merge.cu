@@ -2,7 +2,7 @@
 // (Eq. 5-9) and the kernel-regression accumulation (Eq. 1-2) with a fused
 // normalisation -- the per-burst kernels.  Their bodies (and the numerical design notes)
 // live in stages.cuh, shared with the batched persistent kernel.
-#include "stages.cuh"
+#include "accumulate.cuh"
 
 namespace hmfsr {
 namespace {
