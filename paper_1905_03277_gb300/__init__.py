@@ -19,8 +19,8 @@ import torch
 from . import _lib
 from ._lib import build  # noqa: F401  (re-exported)
 
-__all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "build", "workspace_size",
-           "out_size", "n_tiles"]
+__all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "AlignMergePipeline", "build",
+           "workspace_size", "out_size", "n_tiles"]
 
 
 @dataclass
@@ -187,6 +187,86 @@ def align_merge(burst: torch.Tensor, params: MergeParams | None = None, scale=(1
         out = torch.empty(rgb.shape, dtype=rgb.dtype, pin_memory=True)
     out.copy_(rgb, non_blocking=True)
     return out
+
+
+class AlignMergePipeline:
+    """The whole path over a stream of host bursts of one shape, with the copies of one
+    burst overlapped with the compute of another.
+
+    `depth` device slots each hold a burst, its motion field and its RGB result.  Per
+    `submit`, the host burst is copied in on a copy stream, aligned and merged (through
+    hmfsr_align and hmfsr_merge) on a compute stream, and the RGB copied back into the
+    caller's host tensor on a second copy stream; CUDA events order the three, so burst
+    k + 1 travels in and burst k - 1 travels out while burst k is merged.  Host buffers
+    should be pinned; the caller keeps a submitted burst and its output untouched until
+    `synchronize` (or a later submit of the same slot) says the copies are done.  Every
+    device buffer is allocated once, here."""
+
+    def __init__(self, shape, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
+                 align_params: AlignParams | None = None, device=None, white_level: int = 4095, depth: int = 2):
+        L = _lib.load()
+        self.params = params or MergeParams()
+        self.align_params = align_params or AlignParams(tile=self.params.tile)
+        self.scale, self.ref, self.white_level, self.depth = tuple(scale), ref, white_level, depth
+        self.device = torch.device(device or "cuda")
+        n, h, w = shape
+        self.shape = (n, h, w)
+        ty, tx = n_tiles(h, w, self.params.tile)
+        ho, wo = out_size(h, w, scale)
+        mk = lambda *a, **k: torch.empty(*a, device=self.device, **k)
+        self.bursts = [mk((n, h, w), dtype=torch.uint16) for _ in range(depth)]
+        self.motions = [mk((n, ty, tx, 2), dtype=torch.float32) for _ in range(depth)]
+        self.rgbs = [mk((3, ho, wo), dtype=torch.float32) for _ in range(depth)]
+        self.desc = _desc(self.bursts[0], ref, white_level)
+        wa = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(self.desc), self.align_params.tile, 1, 1)
+        wm = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(self.desc), self.params.tile, scale[0], scale[1])
+        if wa == 0 or wm == 0:
+            raise ValueError("unsupported burst shape, tile or scale")
+        self._ws_raw = mk(wa + wm + 512, dtype=torch.uint8)  # one compute stream: the slots share it
+        base = (-self._ws_raw.data_ptr()) % 256
+        self.ws_align = self._ws_raw[base:base + wa]
+        off = base + ((wa + 255) // 256) * 256
+        self.ws_merge = self._ws_raw[off:off + wm]
+        self.h2d, self.compute, self.d2h = (torch.cuda.Stream(self.device) for _ in range(3))
+        self.ev_in = [torch.cuda.Event() for _ in range(depth)]
+        self.ev_done = [torch.cuda.Event() for _ in range(depth)]
+        self.ev_out = [torch.cuda.Event() for _ in range(depth)]
+        self.used = [False] * depth
+        self.k = 0
+        self._ap, self._mp = self.align_params.c(), self.params.c()
+
+    def submit(self, host_burst: torch.Tensor, host_out: torch.Tensor) -> None:
+        L = _lib.load()
+        if tuple(host_burst.shape) != self.shape or host_burst.dtype != torch.uint16:
+            raise ValueError(f"burst must be uint16 {self.shape}")
+        i = self.k % self.depth
+        self.k += 1
+        b, mv, rgb = self.bursts[i], self.motions[i], self.rgbs[i]
+        with torch.cuda.stream(self.h2d):
+            if self.used[i]:
+                self.h2d.wait_event(self.ev_done[i])  # the slot's previous burst has been merged
+            b.copy_(host_burst, non_blocking=True)
+            self.ev_in[i].record(self.h2d)
+        self.compute.wait_event(self.ev_in[i])
+        if self.used[i]:
+            self.compute.wait_event(self.ev_out[i])  # the slot's previous RGB has been read out
+        cs = ctypes.c_void_p(self.compute.cuda_stream)
+        _lib.check(L.hmfsr_align(_ptr(b), ctypes.byref(self.desc), ctypes.byref(self._ap), _ptr(mv), None,
+                                 _ptr(self.ws_align), self.ws_align.numel(), cs), "hmfsr_align")
+        _lib.check(L.hmfsr_merge(_ptr(b), ctypes.byref(self.desc), _ptr(mv), ctypes.byref(self._mp), self.scale[0],
+                                 self.scale[1], _ptr(rgb), None, _ptr(self.ws_merge), self.ws_merge.numel(), cs),
+                   "hmfsr_merge")
+        self.ev_done[i].record(self.compute)
+        with torch.cuda.stream(self.d2h):
+            self.d2h.wait_event(self.ev_done[i])
+            host_out.copy_(rgb, non_blocking=True)
+            self.ev_out[i].record(self.d2h)
+        self.used[i] = True
+
+    def synchronize(self) -> None:
+        """Wait until every submitted burst's result is in its host tensor."""
+        for st in (self.h2d, self.compute, self.d2h):
+            st.synchronize()
 
 
 def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
