@@ -256,3 +256,42 @@ def merge_fingerprint(burst, motion, params: MergeParams, scale=(1, 1), ref: int
     p = params.c()
     return int(lib().orc_merge_fingerprint(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float),
                                            tile, ctypes.byref(p), wl, scale[0], scale[1]))
+
+
+# ---------------------------------------------------------------------------------------
+# Noise-dependent tuning (supplement: "Noise-dependent Tuning"; "Tuning Procedure and
+# Parameters").  The SNR of the base frame (one raw sample, one frame) is the mean
+# brightness over its noise standard deviation under var(x) = a x + b; the parameters
+# that trade resolution against denoising are piecewise linear in SNR over [6, 30],
+# running from the denoising end of the printed ranges (low SNR) to the detail end; the
+# tile is 16 px and grows to 32 and 64 px in very low light.
+# ---------------------------------------------------------------------------------------
+SNR_RANGE = (6.0, 30.0)
+# parameter: (value at SNR <= 6, value at SNR >= 30)
+SNR_RAMPS = {"k_detail": (0.33, 0.25), "k_denoise": (5.0, 3.0), "d_th": (0.010, 0.001), "d_tr": (0.020, 0.006)}
+FIXED_TUNING = {"k_stretch": 4.0, "k_shrink": 2.0, "t": 0.12, "s1": 12.0, "s2": 2.0, "m_th": 0.8}
+
+
+def frame_mean(frame) -> float:
+    """Mean sample value of one raw frame, from its exact integer sum."""
+    f = np.asarray(frame)
+    return int(f.astype(np.int64).sum()) / f.size
+
+
+def snr_of(mean: float, noise_a: float, noise_b: float) -> float:
+    var = noise_a * mean + noise_b
+    return mean / np.sqrt(var) if var > 0 else float("inf")
+
+
+def snr_tuning(mean: float, noise_a: float, noise_b: float) -> dict:
+    """Every tuned value for a base frame of mean brightness `mean` (DN)."""
+    snr = snr_of(mean, noise_a, noise_b)
+    lo, hi = SNR_RANGE
+    s = hi if np.isinf(snr) else snr
+    frac = min(max((s - lo) / (hi - lo), 0.0), 1.0)
+    out = {k: (1.0 - frac) * a + frac * b for k, (a, b) in SNR_RAMPS.items()}
+    out.update(FIXED_TUNING)
+    # very low light: the lowest third of the range, split in two
+    out["tile"] = 64 if s < 10.0 else (32 if s < 14.0 else 16)
+    out["snr"] = snr
+    return out

@@ -463,3 +463,60 @@ def test_lk_recovers_subpixel_shift():
         err = np.abs(mf[k, 1:-1, 1:-1] - np.array([sx, sy]))
         assert np.median(err) < 0.05 and err.max() < 0.25
         assert fl[k].sum() == 0
+
+
+# --------------------------------------------------------------------------------------
+# noise-dependent tuning (supplement: "Noise-dependent Tuning", "Tuning Procedure and
+# Parameters"): the range ends printed there, and the reading's linearity in SNR
+# --------------------------------------------------------------------------------------
+def test_frame_mean_is_the_plain_average():
+    rng = np.random.default_rng(1905_03277 + 51)
+    f = rng.integers(0, 4096, size=(6, 10), dtype=np.uint16)
+    total = 0
+    for row in f.tolist():
+        for v in row:
+            total += v
+    assert oracle.frame_mean(f) == total / 60
+
+
+def test_snr_closed_form():
+    # a flat frame at 1000 DN under var = 4 x + 36 has SNR 1000 / sqrt(4036)
+    f = np.full((8, 8), 1000, dtype=np.uint16)
+    assert oracle.snr_of(oracle.frame_mean(f), 4.0, 36.0) == pytest.approx(1000.0 / 4036.0 ** 0.5, rel=1e-15)
+
+
+def test_tuning_range_ends_are_the_printed_values():
+    low = oracle.snr_tuning(100.0, 256.0, 0.0)        # SNR 0.625: below the range
+    high = oracle.snr_tuning(4000.0, 1.0, 0.0)        # SNR 63: above the range
+    assert (low["k_detail"], low["k_denoise"], low["d_th"], low["d_tr"]) == (0.33, 5.0, 0.010, 0.020)
+    assert (high["k_detail"], high["k_denoise"], high["d_th"], high["d_tr"]) == (0.25, 3.0, 0.001, 0.006)
+    assert low["tile"] == 64 and high["tile"] == 16
+    for k, v in {"k_stretch": 4, "k_shrink": 2, "t": 0.12, "s1": 12, "s2": 2, "m_th": 0.8}.items():
+        assert low[k] == v and high[k] == v
+    free = oracle.snr_tuning(500.0, 0.0, 0.0)           # noise-free model: the detail end
+    assert free["snr"] == float("inf") and free["k_detail"] == 0.25 and free["tile"] == 16
+
+
+def test_tuning_midpoint_and_monotone():
+    # mean 3240 under var = 10 x gives SNR 3240 / 180 = 18, the middle of [6, 30]
+    mid = oracle.snr_tuning(3240.0, 10.0, 0.0)
+    assert mid["snr"] == pytest.approx(18.0, rel=1e-15)
+    assert mid["k_detail"] == pytest.approx(0.29, abs=1e-15)
+    assert mid["k_denoise"] == pytest.approx(4.0, abs=1e-15)
+    assert mid["d_th"] == pytest.approx(0.0055, abs=1e-15)
+    assert mid["d_tr"] == pytest.approx(0.013, abs=1e-15)
+    prev = None
+    for mean in np.linspace(10.0, 4000.0, 200):
+        cur = oracle.snr_tuning(float(mean), 4.0, 36.0)
+        if prev is not None:
+            assert cur["snr"] > prev["snr"]
+            for k in ("k_detail", "k_denoise", "d_th", "d_tr"):
+                assert cur[k] <= prev[k]
+            assert cur["tile"] <= prev["tile"]
+        prev = cur
+
+
+@pytest.mark.parametrize("snr,tile", [(6.0, 64), (9.999, 64), (10.0, 32), (13.999, 32), (14.0, 16), (29.0, 16)])
+def test_tuning_tile_steps(snr, tile):
+    # b = 0: SNR = sqrt(mean / a), so mean = a SNR^2 hits the SNR exactly
+    assert oracle.snr_tuning(snr * snr, 1.0, 0.0)["tile"] == tile
