@@ -293,6 +293,29 @@ def run_gpu(args):
         e2e_ms = float(t.item())
     e2e_value = world * mp / (e2e_ms / 1e3)
 
+    # noise-dependent tuning: the exact sum of a frame on the GPU (HBM-bound; the calls
+    # rotate over the 8 frames, 195 MB > L2), then the parameters the base frame selects
+    fsum = torch.empty(1, dtype=torch.int64, device=dev)
+    for f in range(n):
+        hm.frame_sum(raw, f, out=fsum)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    sum_reps = 4 * n
+    t0.record(stream)
+    for i in range(sum_reps):
+        hm.frame_sum(raw, i % n, out=fsum)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sum_us = t0.elapsed_time(t1) / sum_reps * 1e3
+    tmp, tap, tsnr = hm.auto_params(raw, b["gain"], b["read"] ** 2, ref=0)
+    frame_bytes = h * w * 2
+    tuning = {"snr": tsnr, "tile": tap.tile, "k_detail": tmp.k_detail, "k_denoise": tmp.k_denoise,
+              "frame_sum_us": sum_us, "frame_sum_gbs": frame_bytes / sum_us / 1e3,
+              "hbm_frac": frame_bytes / sum_us / 1e3 / ((measured_peaks() or {}).get("hbm_gbs", FALLBACK_HBM_GBS)),
+              "kernel": "k_frame_sum (hmfsr_frame_sum), 24.4 MB per 12-MP frame",
+              "per_call": "the zeroing memset and the kernel, launched from Python back to back"}
+
     # adjoint (fitting workload: 8 x 1024x1024 at 1.5x): forward with den, then backward
     fb = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 3 + 1000 * rank, device=dev)
     fraw = fb["raw"]
@@ -405,6 +428,7 @@ def run_gpu(args):
                                  "merge_accumulate": statistics.median(acc_ms)},
                 "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
                 "batched": batched,
+                "snr_tuning": tuning,
                 "adjoint": {"workload": "fit: 8 x 1024x1024 RGGB, 1.5x output", "forward_ms": statistics.median(fwd_ms),
                             "backward_ms": statistics.median(bwd_ms),
                             "backward_over_forward": statistics.median(bwd_ms) / statistics.median(fwd_ms)}}

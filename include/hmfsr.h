@@ -209,6 +209,32 @@ hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *burs
 
 void hmfsr_batch_free(hmfsr_batch_plan plan);
 
+/* ---- Noise-dependent tuning (supplement: "Noise-dependent Tuning" and "Tuning
+ * Procedure and Parameters").  The paper picks its kernel parameters and tile size from
+ * one input, the base frame's SNR, estimated from the mean brightness and the noise
+ * model (Sec. 5.2.2).  ---- */
+
+/* Exact sum of every sample of frame `frame` (width x height, row stride pitch_elems),
+ * written to *sum_dev, one 8-byte-aligned unsigned 64-bit integer in device memory that
+ * the call zeroes first on `stream`.  mean = sum / (width * height).  Asynchronous;
+ * HMFSR_ERR_INVALID_ARG for a bad frame index, size or pointer. */
+hmfsr_status hmfsr_frame_sum(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, int frame,
+                             unsigned long long *sum_dev, void *stream);
+
+/* Host-only (no GPU): from the base frame's mean sample value `mean` (DN) and the noise
+ * model var(x) = noise_a * x + noise_b, SNR = mean / sqrt(noise_a * mean + noise_b) (one
+ * raw sample of one frame; +infinity for a noise-free model), then every parameter of
+ * *mparams and *aparams:
+ *   k_detail 0.33 -> 0.25, k_denoise 5 -> 3, d_th 0.010 -> 0.001, d_tr 0.020 -> 0.006,
+ *   linear in SNR from SNR <= 6 (the denoising end) to SNR >= 30 (the detail end);
+ *   tile 64 for SNR < 10, 32 for SNR < 14, else 16 (both structs);
+ *   k_stretch 4, k_shrink 2, t 0.12, s1 12, s2 2, m_th 0.8, noise_a/b as given;
+ *   alignment: 4 levels, radii 1 (finest), 4, 4, 4, 3 Lucas-Kanade iterations.
+ * `snr` may be NULL.  HMFSR_ERR_INVALID_ARG for a negative or non-finite mean or noise
+ * coefficient, or a NULL struct. */
+hmfsr_status hmfsr_snr_tuning(double mean, float noise_a, float noise_b, hmfsr_merge_params *mparams,
+                              hmfsr_align_params *aparams, double *snr);
+
 /* Human-readable name of a status code (static string). */
 const char *hmfsr_status_string(hmfsr_status s);
 

@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import build  # noqa: F401  (re-exported)
 
 __all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "AlignMergePipeline", "build",
-           "workspace_size", "out_size", "n_tiles"]
+           "workspace_size", "out_size", "n_tiles", "frame_sum", "snr_tuning", "auto_params"]
 
 
 @dataclass
@@ -267,6 +267,38 @@ class AlignMergePipeline:
         """Wait until every submitted burst's result is in its host tensor."""
         for st in (self.h2d, self.compute, self.d2h):
             st.synchronize()
+
+
+def frame_sum(burst: torch.Tensor, frame: int = 0, stream=None, out: torch.Tensor | None = None):
+    """Exact sum of one frame's samples (hmfsr_frame_sum), read back to the host; with
+    `out` (a one-element int64 device tensor) the sum stays there and the call returns
+    without waiting."""
+    L = _lib.load()
+    d = _desc(burst, 0, 4095)
+    dst = out if out is not None else torch.empty(1, dtype=torch.int64, device=burst.device)  # < 2^63
+    _lib.check(L.hmfsr_frame_sum(_ptr(burst), ctypes.byref(d), frame, _ptr(dst), _stream(burst.device, stream)),
+               "hmfsr_frame_sum")
+    return dst if out is not None else int(dst.item())
+
+
+def snr_tuning(mean: float, noise_a: float, noise_b: float):
+    """(MergeParams, AlignParams, snr) for a base frame of mean brightness `mean` in DN and
+    the noise model var = noise_a * x + noise_b (hmfsr_snr_tuning; host arithmetic)."""
+    L = _lib.load()
+    mp, ap, snr = _lib.MergeParamsC(), _lib.AlignParamsC(), ctypes.c_double()
+    _lib.check(L.hmfsr_snr_tuning(float(mean), float(noise_a), float(noise_b), ctypes.byref(mp), ctypes.byref(ap),
+                                  ctypes.byref(snr)), "hmfsr_snr_tuning")
+    m = MergeParams(**{f.name: getattr(mp, f.name) for f in fields(MergeParams)})
+    a = AlignParams(tile=ap.tile, n_levels=ap.n_levels, radius=tuple(ap.radius), lk_iters=ap.lk_iters)
+    return m, a, snr.value
+
+
+def auto_params(burst: torch.Tensor, noise_a: float, noise_b: float, ref: int = 0, stream=None):
+    """The paper's automatic parameter choice for this burst: the base frame's mean
+    brightness (one device reduction and an 8-byte read back) and the noise model give
+    the SNR, and the SNR every parameter.  Returns (MergeParams, AlignParams, snr)."""
+    n, h, w = burst.shape
+    return snr_tuning(frame_sum(burst, ref, stream) / (h * w), noise_a, noise_b)
 
 
 def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,

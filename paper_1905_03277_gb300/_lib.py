@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libhmfsr.so")
-SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu")
+SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu", "tuning.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic FMA contraction, so a device function gives the same bits in
 # every kernel it is inlined into (fused multiply-adds are written out with fmaf)
@@ -84,7 +84,8 @@ OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD = 0, 1, 2, 3
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
            "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_configure",
-           "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_status_string", "hmfsr_version")
+           "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
+           "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
 
@@ -133,6 +134,11 @@ def load(path: str | None = None):
     L.hmfsr_batch_tune.restype = ci
     L.hmfsr_batch_free.argtypes = [vp]
     L.hmfsr_batch_free.restype = None
+    L.hmfsr_frame_sum.argtypes = [vp, P(BurstDesc), ci, vp, vp]
+    L.hmfsr_frame_sum.restype = ci
+    L.hmfsr_snr_tuning.argtypes = [ctypes.c_double, ctypes.c_float, ctypes.c_float, P(MergeParamsC), P(AlignParamsC),
+                                   P(ctypes.c_double)]
+    L.hmfsr_snr_tuning.restype = ci
     L.hmfsr_status_string.argtypes = [ci]
     L.hmfsr_status_string.restype = ctypes.c_char_p
     L.hmfsr_version.argtypes = []

@@ -140,3 +140,32 @@ def test_batch_plan_validation_on_host(L):
         hm.BatchPlan([(4, 64, 96)], refs=4)                # ref out of range
     with pytest.raises(RuntimeError, match="invalid argument"):
         p.configure(merge_tile_w=48)                       # must divide 128
+
+
+def test_snr_tuning_through_the_abi_matches_the_oracle(L):
+    # host-only entry point: no GPU needed
+    import oracle
+    for mean, a, b in [(50.0, 4.0, 36.0), (700.0, 2.0, 9.0), (1500.0, 4.0, 36.0), (3240.0, 10.0, 0.0),
+                       (4000.0, 0.5, 4.0), (800.0, 0.0, 0.0), (0.0, 1.0, 1.0)]:
+        mp, ap, snr = hm.snr_tuning(mean, a, b)
+        want = oracle.snr_tuning(mean, a, b)
+        assert snr == want["snr"]
+        assert mp.tile == ap.tile == want["tile"]
+        for k in ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink", "t", "s1", "s2", "m_th"):
+            assert getattr(mp, k) == pytest.approx(want[k], rel=1e-7, abs=1e-12), k
+        assert (mp.noise_a, mp.noise_b) == (a, b)
+        assert (ap.n_levels, ap.radius, ap.lk_iters) == (4, (1, 4, 4, 4), 3)
+
+
+def test_tuning_entry_points_reject_bad_arguments(L):
+    mp, ap = _lib.MergeParamsC(), _lib.AlignParamsC()
+    assert L.hmfsr_snr_tuning(-1.0, 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(float("nan"), 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(10.0, -1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(10.0, 1.0, 1.0, None, ctypes.byref(ap), None) == -1
+    d = desc(n=2)
+    # fake, never dereferenced pointers: every case returns before any launch
+    assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), 2, ctypes.c_void_p(256), None) == -1
+    assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), -1, ctypes.c_void_p(256), None) == -1
+    assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), 0, ctypes.c_void_p(260), None) == -1
+    assert L.hmfsr_frame_sum(None, ctypes.byref(d), 0, ctypes.c_void_p(256), None) == -1

@@ -242,3 +242,37 @@ def test_full_size_sampled(dev, config, k):
     assert np.isfinite(got).all()
     assert err.max(axis=0).max() <= MAX_ABS, f"max {err.max(axis=0)}"
     assert (err.mean(axis=0) <= MEAN_ABS).all(), f"mean {err.mean(axis=0)}"
+
+
+# --------------------------------------------------------------------------------------
+# noise-dependent tuning: the base frame's exact sum and the parameters it selects
+# --------------------------------------------------------------------------------------
+def test_frame_sum_exact(dev, tiny_burst):
+    raw = tiny_burst["raw"]
+    for f in range(raw.shape[0]):
+        assert hm.frame_sum(raw.to(dev), f) == int(raw[f].numpy().astype(np.int64).sum())
+    # ragged rows, a row stride beyond the width, widths below one 8-sample load
+    rng = np.random.default_rng(1905_03277 + 52)
+    for n, h, w, pitch in [(3, 10, 6, 6), (2, 37, 101, 104), (2, 64, 250, 256), (1, 5, 4, 12)]:
+        full = rng.integers(0, 65536, size=(n, h, pitch), dtype=np.uint16)
+        t = torch.from_numpy(full).to(dev)[:, :, :w]
+        for f in range(n):
+            assert hm.frame_sum(t, f) == int(full[f, :, :w].astype(np.int64).sum())
+    # a full-size frame of 12-bit samples
+    big = rng.integers(0, 4096, size=(1, 3024, 4032), dtype=np.uint16)
+    assert hm.frame_sum(torch.from_numpy(big).to(dev), 0) == int(big.astype(np.int64).sum())
+
+
+def test_auto_params_match_the_oracle(dev, tiny_burst):
+    raw = tiny_burst["raw"]
+    for ref in (0, 3):
+        mp, ap, snr = hm.auto_params(raw.to(dev), tiny_burst["gain"], tiny_burst["read"] ** 2, ref=ref)
+        want = oracle.snr_tuning(oracle.frame_mean(raw[ref].numpy()), tiny_burst["gain"], tiny_burst["read"] ** 2)
+        assert snr == pytest.approx(want["snr"], rel=1e-12)
+        assert mp.tile == ap.tile == want["tile"]
+        for k in ("k_detail", "k_denoise", "d_th", "d_tr"):
+            assert getattr(mp, k) == pytest.approx(want[k], rel=1e-7)
+    # the selected parameters drive a merge that stays at parity with the oracle
+    motion = oracle.align(raw.numpy(), ref=0, tile=mp.tile)[1].astype(np.float32)
+    rgb = hm.merge(raw.to(dev), torch.from_numpy(motion).to(dev), mp).cpu().numpy()
+    assert_merge_close(rgb, oracle.merge(raw.numpy(), motion, oparams(mp), tile=mp.tile), "auto parameters")
