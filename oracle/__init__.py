@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
-        "t", "s1", "s2", "m_th", "noise_a", "noise_b")]
+        "t", "s1", "s2", "m_th", "noise_a", "noise_b")] + [("noise_table", ctypes.c_void_p)]
 
 
 @dataclass
@@ -54,9 +54,18 @@ class MergeParams:
     noise_a: float = 1.0
     noise_b: float = 4.0
 
-    def c(self) -> _Params:
+    def c(self, noise_table=None) -> _Params:
+        """The C struct; `noise_table` (NOISE_LEVELS x 4, from noise_table()) replaces the
+        closed-form noise statistics."""
         # promote the float32 values the CUDA path sees
-        return _Params(*[float(np.float32(getattr(self, f.name))) for f in fields(self)])
+        p = _Params(*[float(np.float32(getattr(self, f.name))) for f in fields(self)], None)
+        if noise_table is not None:
+            tab = np.ascontiguousarray(noise_table, dtype=np.float64)
+            if tab.shape != (NOISE_LEVELS, 4):
+                raise ValueError(f"noise table must be [{NOISE_LEVELS}, 4]")
+            p.noise_table = tab.ctypes.data
+            p._keep = tab  # the array outlives the struct's use
+        return p
 
 
 def lib():
@@ -81,6 +90,10 @@ def lib():
         L.orc_merge_backward.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci, f64p, f64p, f64p, ci]
         L.orc_merge_fingerprint.argtypes = [u16p, ci, ci, ci, ci, f32p, ci, P(_Params), ci, ci, ci]
         L.orc_merge_fingerprint.restype = ctypes.c_ulonglong
+        L.orc_noise_table.argtypes = [ctypes.c_double, ctypes.c_double, ci, f64p]
+        L.orc_noise_table.restype = None
+        L.orc_philox.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+        L.orc_philox.restype = None
         for name in ("orc_luma", "orc_structure_tensor", "orc_kernel_from_tensor", "orc_omega_plane",
                      "orc_tile_strength", "orc_robustness", "orc_merge_rows", "orc_merge_pixels", "orc_align",
                      "orc_merge_backward"):
@@ -155,13 +168,13 @@ def tile_strength(motion_frame, params: MergeParams):
     return M, s
 
 
-def robustness(base, alt, motion_alt, tile: int, params: MergeParams, wl: int = 4095):
+def robustness(base, alt, motion_alt, tile: int, params: MergeParams, wl: int = 4095, noise_table=None):
     base, alt = _u16(base), _u16(alt)
     h, w = base.shape
     mv = np.ascontiguousarray(motion_alt, dtype=np.float32)
     R = np.empty((h // 2, w // 2), np.float64)
     Rh = np.empty((h // 2, w // 2), np.float64)
-    p = params.c()
+    p = params.c(noise_table)
     _check(lib().orc_robustness(_ptr(base, ctypes.c_uint16), _ptr(alt, ctypes.c_uint16), h, w,
                                 _ptr(mv, ctypes.c_float), tile, ctypes.byref(p), wl,
                                 _ptr(R, ctypes.c_double), _ptr(Rh, ctypes.c_double)), "robustness")
@@ -174,7 +187,7 @@ def out_size(h: int, w: int, scale) -> tuple:
 
 
 def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: int = 16, wl: int = 4095,
-          rows=None, with_den: bool = False, n_threads: int = 0):
+          rows=None, with_den: bool = False, n_threads: int = 0, noise_table=None):
     """Oracle merge of output rows [y0, y1) (all rows by default): double [3, rows, Wo]."""
     burst = _u16(burst)
     n, h, w = burst.shape
@@ -186,7 +199,7 @@ def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: 
     y0, y1 = (0, ho) if rows is None else rows
     out = np.empty((3, y1 - y0, wo), np.float64)
     den = np.empty((3, y1 - y0, wo), np.float64) if with_den else None
-    p = params.c()
+    p = params.c(noise_table)
     _check(lib().orc_merge_rows(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
                                 ctypes.byref(p), wl, scale[0], scale[1], y0, y1, _ptr(out, ctypes.c_double),
                                 _ptr(den, ctypes.c_double) if den is not None else None, n_threads), "merge")
@@ -194,14 +207,14 @@ def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: 
 
 
 def merge_pixels(burst, motion, params: MergeParams, xy, scale=(1, 1), ref: int = 0, tile: int = 16,
-                 wl: int = 4095, n_threads: int = 0) -> np.ndarray:
+                 wl: int = 4095, n_threads: int = 0, noise_table=None) -> np.ndarray:
     """Oracle merge of the output pixels xy[k] = (X, Y): double [k, 3]."""
     burst = _u16(burst)
     n, h, w = burst.shape
     mv = np.ascontiguousarray(motion, dtype=np.float32)
     xy = np.ascontiguousarray(xy, dtype=np.int32)
     out = np.empty((xy.shape[0], 3), np.float64)
-    p = params.c()
+    p = params.c(noise_table)
     _check(lib().orc_merge_pixels(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
                                   ctypes.byref(p), wl, scale[0], scale[1], _ptr(xy, ctypes.c_int32),
                                   xy.shape[0], _ptr(out, ctypes.c_double), n_threads), "merge_pixels")
@@ -295,3 +308,33 @@ def snr_tuning(mean: float, noise_a: float, noise_b: float) -> dict:
     out["tile"] = 64 if s < 10.0 else (32 if s < 14.0 else 16)
     out["snr"] = snr
     return out
+
+
+
+# ---------------------------------------------------------------------------------------
+# Monte-Carlo noise statistics (Sec. 5.2.2): sigma_md^2 and d_md^2 per brightness level
+# ---------------------------------------------------------------------------------------
+NOISE_LEVELS = 129
+NOISE_TRIALS = 4096
+
+
+def noise_table(noise_a: float, noise_b: float, wl: int = 4095) -> np.ndarray:
+    """double [NOISE_LEVELS, 4]: per brightness level i WL / (NOISE_LEVELS - 1), the trial
+    means of {3x3 population variance red/blue, green; squared difference of two patch
+    means red/blue, green} (orc_noise_table).  noise_a / noise_b are promoted from float32,
+    as the CUDA path sees them."""
+    L = lib()
+    out = np.empty((NOISE_LEVELS, 4), dtype=np.float64)
+    L.orc_noise_table(float(np.float32(noise_a)), float(np.float32(noise_b)), int(wl),
+                      _ptr(out, ctypes.c_double))
+    return out
+
+
+def philox(ctr, key) -> tuple:
+    """Philox-4x32-10 of the 4-word counter under the 2-word key (orc_philox)."""
+    L = lib()
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    L.orc_philox(c, k, o)
+    return tuple(o)

@@ -291,6 +291,31 @@ typedef struct {
  *  - the colour difference and sigma are vectors over (R, G, B); the ratio in Eq. 5 is
  *    |d|^2 / max(|sigma|^2, 1e-12 WL^2).
  *  - R is clamped to [0, 1] (a weight of one merges fully, zero rejects). */
+/* Modelled statistics of one guide channel at brightness mu (Eq. 6): the variance
+ * sigma_md^2 expected of a 3x3 patch of constant brightness and d_md^2, the expected
+ * squared difference of two such patches' means.  Closed form (var = a x + b per raw
+ * sample, halved for the green mean of two; d_md^2 = 2 var / 9), or the Monte-Carlo table
+ * interpolated linearly between brightness levels. */
+static void modelled_stats(const orc_params *p, int wl, double mu, int c, double *var_md, double *dmd2)
+{
+    if (p->noise_table) {
+        double t = clampd(mu, 0.0, (double)wl) * (double)(ORC_NOISE_LEVELS - 1) / (double)wl;
+        int i = (int)floor(t);
+        if (i > ORC_NOISE_LEVELS - 2) i = ORC_NOISE_LEVELS - 2;
+        double f = t - (double)i;
+        int k = (c == 1) ? 1 : 0;
+        const double *a = p->noise_table + 4 * i, *b = a + 4;
+        *var_md = (1.0 - f) * a[k] + f * b[k];
+        *dmd2 = (1.0 - f) * a[2 + k] + f * b[2 + k];
+        return;
+    }
+    double gs = (c == 1) ? 2.0 : 1.0;
+    double v = (p->noise_a * clampd(mu, 0.0, (double)wl) + p->noise_b) / gs;
+    if (v < 0.0) v = 0.0;
+    *var_md = v;
+    *dmd2 = 2.0 * v / 9.0;
+}
+
 static double robustness_at(const uint16_t *base, const uint16_t *alt, const float *motion_alt,
                             const double *s_tile, const rob_geom *g, int u, int v)
 {
@@ -311,12 +336,11 @@ static double robustness_at(const uint16_t *base, const uint16_t *alt, const flo
         double sigma_ms = sqrt(var_ms);
         double mu_n = mean_bilinear(alt, g->h, g->w, fx, fy, c);
         double d_ms = mu - mu_n;
-        double var_md = (p->noise_a * clampd(mu, 0.0, (double)g->wl) + p->noise_b) / gs;
-        if (var_md < 0.0) var_md = 0.0;
+        double var_md, dmd2;
+        modelled_stats(p, g->wl, mu, c, &var_md, &dmd2);
         double sigma_md = sqrt(var_md);
-        double d_md = sqrt(2.0 * var_md / 9.0);
         double sigma = sigma_ms > sigma_md ? sigma_ms : sigma_md;       /* Eq. 6 */
-        double den = d_ms * d_ms + d_md * d_md;
+        double den = d_ms * d_ms + dmd2;
         double d = den > 0.0 ? d_ms * (d_ms * d_ms) / den : 0.0;        /* Eq. 6 */
         dd += d * d;
         ss += sigma * sigma;
@@ -924,10 +948,9 @@ static double robustness_grad_at(const uint16_t *base, const uint16_t *alt, cons
         double dmu_dfx = (1.0 - ay) * (m10 - m00) + ay * (m11 - m01);
         double dmu_dfy = (1.0 - ax) * (m01 - m00) + ax * (m11 - m10);
         double d_ms = mu - mu_n;
-        double var_md = (p->noise_a * clampd(mu, 0.0, (double)g->wl) + p->noise_b) / gs;
-        if (var_md < 0.0) var_md = 0.0;
+        double var_md, m;
+        modelled_stats(p, g->wl, mu, c, &var_md, &m);
         double sigma_md = sqrt(var_md);
-        double m = 2.0 * var_md / 9.0;
         double sigma = sigma_ms > sigma_md ? sigma_ms : sigma_md;
         double den = d_ms * d_ms + m;
         double d = den > 0.0 ? d_ms * (d_ms * d_ms) / den : 0.0;
@@ -1201,4 +1224,88 @@ unsigned long long orc_merge_fingerprint(const uint16_t *burst, int n, int h, in
     free(Rpl);
     free_ctx(&m);
     return hsh;
+}
+
+
+/* ======================================================================================
+ * Monte-Carlo noise statistics (Sec. 5.2.2)
+ * ==================================================================================== */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    /* Philox-4x32 with 10 rounds: per round two 32x32 -> 64-bit products by the fixed
+     * multipliers, the halves recombined with the other counter words and the round key,
+     * the key bumped by the Weyl constants between rounds */
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* the j-th normal of trial `trial` at level `level`: 12 uniforms (r + 1/2) 2^-32 from
+ * three Philox blocks, summed exactly, minus 6 */
+static double noise_normal(int level, int trial, int j)
+{
+    static const uint32_t key[2] = {0x19050327u, 0x5EED0001u};
+    uint64_t s = 0;
+    for (int b = 0; b < 3; ++b) {
+        uint32_t ctr[4] = {(uint32_t)(3 * j + b), (uint32_t)trial, (uint32_t)level, 0u}, out[4];
+        orc_philox(ctr, key, out);
+        s += (uint64_t)out[0] + out[1] + out[2] + out[3];
+    }
+    return ((double)s + 6.0) * (1.0 / 4294967296.0) - 6.0;
+}
+
+static double noise_sample(double x, double sigma, int wl, int level, int trial, int j)
+{
+    double v = floor(x + sigma * noise_normal(level, trial, j) + 0.5);
+    return clampd(v, 0.0, (double)wl);
+}
+
+void orc_noise_table(double noise_a, double noise_b, int wl, double *table)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < ORC_NOISE_LEVELS; ++i) {
+        double x = (double)i * (double)wl / (double)(ORC_NOISE_LEVELS - 1);
+        double var = noise_a * x + noise_b;
+        double sigma = var > 0.0 ? sqrt(var) : 0.0;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = 0; t < ORC_NOISE_TRIALS; ++t) {
+            /* normals 0..8: patch 1 red/blue; 9..26: patch 1 green pairs;
+             * 27..35: patch 2 red/blue; 36..53: patch 2 green pairs */
+            double rb[2][9], gr[2][9];
+            for (int q = 0; q < 2; ++q)
+                for (int k = 0; k < 9; ++k) {
+                    rb[q][k] = noise_sample(x, sigma, wl, i, t, 27 * q + k);
+                    gr[q][k] = 0.5 * (noise_sample(x, sigma, wl, i, t, 27 * q + 9 + 2 * k) +
+                                      noise_sample(x, sigma, wl, i, t, 27 * q + 10 + 2 * k));
+                }
+            double mean[2][2], var1[2];
+            for (int ch = 0; ch < 2; ++ch) {
+                for (int q = 0; q < 2; ++q) {
+                    double s = 0.0;
+                    for (int k = 0; k < 9; ++k) s += ch ? gr[q][k] : rb[q][k];
+                    mean[ch][q] = s / 9.0;
+                }
+                double ss = 0.0;
+                for (int k = 0; k < 9; ++k) {
+                    double d = (ch ? gr[0][k] : rb[0][k]) - mean[ch][0];
+                    ss += d * d;
+                }
+                var1[ch] = ss / 9.0;
+            }
+            acc[0] += var1[0];
+            acc[1] += var1[1];
+            acc[2] += (mean[0][0] - mean[0][1]) * (mean[0][0] - mean[0][1]);
+            acc[3] += (mean[1][0] - mean[1][1]) * (mean[1][0] - mean[1][1]);
+        }
+        for (int k = 0; k < 4; ++k) table[4 * i + k] = acc[k] / (double)ORC_NOISE_TRIALS;
+    }
 }

@@ -29,7 +29,26 @@ typedef struct {
     double k_detail, k_denoise, d_th, d_tr, k_stretch, k_shrink;
     double t, s1, s2, m_th;
     double noise_a, noise_b;   /* noise variance = noise_a * x + noise_b (DN^2) */
+    /* NULL: the closed-form noise statistics; else ORC_NOISE_LEVELS x 4 values from
+     * orc_noise_table (Monte-Carlo sigma_md^2 and d_md^2 per brightness level) */
+    const double *noise_table;
 } orc_params;
+
+/* Monte-Carlo noise statistics (Sec. 5.2.2: sigma_md and d_md "through a series of Monte
+ * Carlo simulations for different brightness levels", with sensor clipping).  Level i of
+ * ORC_NOISE_LEVELS is brightness x_i = i WL / (ORC_NOISE_LEVELS - 1).  Each of
+ * ORC_NOISE_TRIALS trials draws two independent constant patches of 3x3 guide pixels:
+ * red/blue guide = one raw sample, green guide = the mean of two; a raw sample is
+ * clamp(floor(x + sqrt(a x + b) z + 1/2), 0, WL) with z an Irwin-Hall normal (sum of 12
+ * uniforms - 6) from Philox-4x32-10.  Per level, table[4 i ..] = the trial means of
+ * {population variance of patch 1, red/blue; the same, green; (mean of patch 1 - mean of
+ * patch 2)^2, red/blue; the same, green}. */
+#define ORC_NOISE_LEVELS 129
+#define ORC_NOISE_TRIALS 4096
+void orc_noise_table(double noise_a, double noise_b, int wl, double *table);
+
+/* Philox-4x32-10 (Salmon et al., SC 2011) of counter ctr[4] under key[2] into out[4]. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 /* Half-res luminance Lq(u,v) = sum of the 4 Bayer samples of quad (u,v) (Sec. 5.1.2). */
 int orc_luma(const uint16_t *raw, int h, int w, int32_t *lq);

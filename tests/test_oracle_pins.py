@@ -520,3 +520,60 @@ def test_tuning_midpoint_and_monotone():
 def test_tuning_tile_steps(snr, tile):
     # b = 0: SNR = sqrt(mean / a), so mean = a SNR^2 hits the SNR exactly
     assert oracle.snr_tuning(snr * snr, 1.0, 0.0)["tile"] == tile
+
+
+# --------------------------------------------------------------------------------------
+# Monte-Carlo noise statistics (Sec. 5.2.2: sigma_md and d_md simulated per brightness,
+# with sensor clipping): the simulation against closed forms where they exist
+# --------------------------------------------------------------------------------------
+def _unclipped(var):
+    # rounding to whole DN adds 1/12 (Sheppard); a 3x3 population variance expects 8/9
+    # of the sample variance; two independent 9-sample means differ by 2 var / 9
+    v = var + 1.0 / 12.0
+    return np.array([8.0 / 9.0 * v, 8.0 / 9.0 * (var / 2.0 + 1.0 / 24.0), 2.0 * v / 9.0, (var / 2.0 + 1.0 / 24.0) * 2.0 / 9.0])
+
+
+def test_noise_table_matches_closed_forms_away_from_clipping():
+    a, b, wl = 4.0, 36.0, 4095
+    tab = oracle.noise_table(a, b, wl)
+    trials = oracle.NOISE_TRIALS
+    # 4 standard errors: a 3x3 population variance has relative spread sqrt(2 / 8), a
+    # squared difference of means sqrt(2)
+    tol = 4.0 * np.array([0.5, 0.5, 2 ** 0.5, 2 ** 0.5]) / trials ** 0.5
+    for i in (32, 48, 64, 80, 96):
+        x = i * wl / (oracle.NOISE_LEVELS - 1)
+        want = _unclipped(a * x + b)
+        assert np.all(np.abs(tab[i] / want - 1.0) < tol), (i, tab[i], want)
+
+
+def test_noise_table_clips_at_the_white_point():
+    # at x = WL half the samples clip: a normal censored at its mean keeps
+    # 1/2 - 1/(2 pi) of its variance (sigma there is 128 DN, so rounding is negligible)
+    a, b, wl = 4.0, 36.0, 4095
+    tab = oracle.noise_table(a, b, wl)
+    var = a * wl + b
+    ratio = tab[-1, 0] / (8.0 / 9.0 * var)
+    assert abs(ratio - (0.5 - 1.0 / (2.0 * np.pi))) < 0.03  # ~4 standard errors of the trial mean
+    # and the clipped end is far below the unclipped model
+    assert tab[-1, 0] < 0.4 * _unclipped(var)[0]
+
+
+def test_noise_table_noise_free_and_deterministic():
+    assert np.array_equal(oracle.noise_table(0.0, 0.0), np.zeros((oracle.NOISE_LEVELS, 4)))
+    t1, t2 = oracle.noise_table(1.5, 9.0), oracle.noise_table(1.5, 9.0)
+    assert np.array_equal(t1, t2)
+    # the generator: distinct counters give distinct words, and its bits are balanced
+    words = np.array([oracle.philox((c, 7, 3, 0), (0x19050327, 0x5EED0001)) for c in range(2000)], dtype=np.uint64)
+    assert len({tuple(w) for w in words.tolist()}) == 2000
+    bits = np.unpackbits(words.astype(np.uint32).view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 4.0 * 0.5 / bits.size ** 0.5
+
+
+def test_robustness_with_noise_table_keeps_identical_frames():
+    # identical frames have no colour difference, whatever the noise statistics
+    rng = np.random.default_rng(1905_03277 + 53)
+    frame = rng.integers(0, 4096, size=(48, 64), dtype=np.uint16)
+    mv = np.zeros((3, 4, 2), dtype=np.float32)
+    p = MergeParams(noise_a=4.0, noise_b=36.0)
+    R, _ = oracle.robustness(frame, frame, mv, 16, p, noise_table=oracle.noise_table(4.0, 36.0))
+    assert np.all(R == 1.0)
