@@ -315,6 +315,16 @@ def run_gpu(args):
               "hbm_frac": frame_bytes / sum_us / 1e3 / ((measured_peaks() or {}).get("hbm_gbs", FALLBACK_HBM_GBS)),
               "kernel": "k_frame_sum (hmfsr_frame_sum), 24.4 MB per 12-MP frame",
               "per_call": "the zeroing memset and the kernel, launched from Python back to back"}
+    # Monte-Carlo noise statistics: the table for this burst's noise model (once per model)
+    hm.noise_table(b["gain"], b["read"] ** 2, device=dev)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    ntab = hm.noise_table(b["gain"], b["read"] ** 2, device=dev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    tuning["noise_table_ms"] = t0.elapsed_time(t1)
+    tuning["noise_table"] = (f"{ntab.shape[0]} levels x 4096 trials x 54 Philox-4x32-10 Irwin-Hall normals "
+                             "(FP64 samples, rounding and clipping)")
 
     # adjoint (fitting workload: 8 x 1024x1024 at 1.5x): forward with den, then backward
     fb = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 3 + 1000 * rank, device=dev)

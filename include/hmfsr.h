@@ -221,6 +221,34 @@ void hmfsr_batch_free(hmfsr_batch_plan plan);
 hmfsr_status hmfsr_frame_sum(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, int frame,
                              unsigned long long *sum_dev, void *stream);
 
+/* ---- Monte-Carlo noise statistics (Sec. 5.2.2: the modelled sigma_md and d_md are
+ * obtained "through a series of Monte Carlo simulations for different brightness
+ * levels", so that clipping near the white point is accounted for).  ---- */
+#define HMFSR_NOISE_LEVELS 129
+#define HMFSR_NOISE_TRIALS 4096
+
+/* Fills table_dev (device, 16-byte aligned, HMFSR_NOISE_LEVELS x 4 floats) for the noise
+ * model var(x) = noise_a x + noise_b and white level WL.  Level i is brightness
+ * x_i = i WL / (HMFSR_NOISE_LEVELS - 1); each of HMFSR_NOISE_TRIALS trials draws two
+ * independent constant 3x3 patches of guide pixels (red/blue: one raw sample; green: the
+ * mean of two), each raw sample clamp(floor(x + sqrt(var(x)) z + 1/2), 0, WL) with z an
+ * Irwin-Hall normal (12 uniforms - 6) from Philox-4x32-10.  Entry i holds the trial means
+ * {3x3 population variance of patch 1, red/blue; the same, green; squared difference of
+ * the two patch means, red/blue; the same, green}: sigma_md^2 and d_md^2 of Eq. 6.
+ * Asynchronous; deterministic up to the order of FP64 sums.  HMFSR_ERR_INVALID_ARG for a
+ * NULL or misaligned table, a negative or non-finite coefficient, or WL outside 1..65535. */
+hmfsr_status hmfsr_noise_table(float noise_a, float noise_b, int white_level, float *table_dev, void *stream);
+
+/* hmfsr_merge with the robustness's modelled statistics (Eq. 6) taken from a table made
+ * by hmfsr_noise_table (for this burst's noise model and white level), linearly
+ * interpolated at the base frame's local mean, instead of the closed form.  Same
+ * arguments, workspace size (HMFSR_OP_MERGE) and errors as hmfsr_merge; noise_table_dev
+ * must be non-NULL and 16-byte aligned. */
+hmfsr_status hmfsr_merge_noise(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                               const hmfsr_merge_params *params, const float *noise_table_dev, int scale_num,
+                               int scale_den, float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes,
+                               void *stream);
+
 /* Host-only (no GPU): from the base frame's mean sample value `mean` (DN) and the noise
  * model var(x) = noise_a * x + noise_b, SNR = mean / sqrt(noise_a * mean + noise_b) (one
  * raw sample of one frame; +infinity for a noise-free model), then every parameter of

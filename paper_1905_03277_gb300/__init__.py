@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import build  # noqa: F401  (re-exported)
 
 __all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "AlignMergePipeline", "build",
-           "workspace_size", "out_size", "n_tiles", "frame_sum", "snr_tuning", "auto_params"]
+           "workspace_size", "out_size", "n_tiles", "frame_sum", "snr_tuning", "auto_params", "noise_table", "merge_noise"]
 
 
 @dataclass
@@ -299,6 +299,36 @@ def auto_params(burst: torch.Tensor, noise_a: float, noise_b: float, ref: int = 
     the SNR, and the SNR every parameter.  Returns (MergeParams, AlignParams, snr)."""
     n, h, w = burst.shape
     return snr_tuning(frame_sum(burst, ref, stream) / (h * w), noise_a, noise_b)
+
+
+def noise_table(noise_a: float, noise_b: float, white_level: int = 4095, device=None, stream=None) -> torch.Tensor:
+    """Monte-Carlo noise statistics (hmfsr_noise_table): float32 [129, 4] on the device,
+    per brightness level {sigma_md^2 red/blue, green; d_md^2 red/blue, green}."""
+    L = _lib.load()
+    dev = torch.device(device or "cuda")
+    tab = torch.empty((_lib.NOISE_LEVELS, 4), dtype=torch.float32, device=dev)
+    _lib.check(L.hmfsr_noise_table(float(noise_a), float(noise_b), int(white_level), _ptr(tab), _stream(dev, stream)),
+               "hmfsr_noise_table")
+    return tab
+
+
+def merge_noise(burst: torch.Tensor, motion: torch.Tensor, table: torch.Tensor, params: MergeParams | None = None,
+                scale=(1, 1), ref: int = 0, with_den: bool = False, white_level: int = 4095, stream=None):
+    """`merge` with the robustness's noise statistics from a `noise_table` (hmfsr_merge_noise)."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ho, wo = out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_noise(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(table), scale[0],
+                                   scale[1], _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
+               "hmfsr_merge_noise")
+    return (rgb, den) if with_den else rgb
 
 
 def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,

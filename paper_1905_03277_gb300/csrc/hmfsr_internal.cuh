@@ -67,9 +67,15 @@ struct MergePlanes {
     int4 *geo;           // [n][ty*tx] window geometry for the output scale {floor(Q v), Q v - floor(Q v)}
 };
 
+// brightness levels of a Monte-Carlo noise table: level i is i WL / (kNoiseLevels - 1)
+constexpr int kNoiseLevels = 129, kNoiseTrials = 4096;
+
 struct MergeConsts {
     float k_detail, k_denoise, d_th, d_tr, k_stretch, k_shrink;
     float t, s1, s2, m_th, noise_a, noise_b;
+    // nullptr: the closed-form noise statistics; else kNoiseLevels entries
+    // {sigma_md^2 red/blue, sigma_md^2 green, d_md^2 red/blue, d_md^2 green}
+    const float4 *noise_table;
 };
 
 // ---------------------------------------------------------------------------------------

@@ -489,9 +489,22 @@ __device__ __forceinline__ float4 base_stats_of(const uint32_t (&S1)[3], const u
         const float igs = (ch == 1) ? 0.5f : 1.f;
         float var_ms = fmaxf((float)num * (igs * igs * (1.f / 81.f)), 0.f);
         float mu = (float)S1[ch] * (igs * (1.f / 9.f));
-        float var_md = fmaxf(fmaf(c.noise_a, fminf(fmaxf(mu, 0.f), (float)wl), c.noise_b) * igs, 0.f);
+        float var_md;
+        if (c.noise_table) {
+            // Monte-Carlo statistics, linear between the brightness levels around mu
+            const float tp = fminf(fmaxf(mu, 0.f), (float)wl) * ((float)(kNoiseLevels - 1) / (float)wl);
+            const int i = min((int)tp, kNoiseLevels - 2);
+            const float f = tp - (float)i;
+            const float4 t0 = __ldg(c.noise_table + i), t1 = __ldg(c.noise_table + i + 1);
+            const float v0 = ch == 1 ? t0.y : t0.x, v1 = ch == 1 ? t1.y : t1.x;
+            const float d0 = ch == 1 ? t0.w : t0.z, d1 = ch == 1 ? t1.w : t1.z;
+            var_md = fmaf(f, v1 - v0, v0);
+            dmd2[ch] = fmaf(f, d1 - d0, d0);
+        } else {
+            var_md = fmaxf(fmaf(c.noise_a, fminf(fmaxf(mu, 0.f), (float)wl), c.noise_b) * igs, 0.f);
+            dmd2[ch] = var_md * (2.f / 9.f);
+        }
         sig2 += fmaxf(var_ms, var_md);
-        dmd2[ch] = var_md * (2.f / 9.f);
     }
     float eps = 1e-12f * (float)wl * (float)wl;
     return make_float4(fmaxf(sig2, eps), dmd2[0], dmd2[1], dmd2[2]);

@@ -169,3 +169,20 @@ def test_tuning_entry_points_reject_bad_arguments(L):
     assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), -1, ctypes.c_void_p(256), None) == -1
     assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), 0, ctypes.c_void_p(260), None) == -1
     assert L.hmfsr_frame_sum(None, ctypes.byref(d), 0, ctypes.c_void_p(256), None) == -1
+
+
+def test_noise_table_entry_points_reject_bad_arguments(L):
+    # fake, never dereferenced pointers: every case returns before any launch
+    assert L.hmfsr_noise_table(1.0, 4.0, 4095, None, None) == -1
+    assert L.hmfsr_noise_table(1.0, 4.0, 4095, ctypes.c_void_p(264), None) == -1      # not 16-byte aligned
+    assert L.hmfsr_noise_table(-1.0, 4.0, 4095, ctypes.c_void_p(256), None) == -1
+    assert L.hmfsr_noise_table(1.0, float("inf"), 4095, ctypes.c_void_p(256), None) == -1
+    assert L.hmfsr_noise_table(1.0, 4.0, 0, ctypes.c_void_p(256), None) == -1
+    d, p = desc(), hm.MergeParams().c()
+
+    def call(table):
+        return L.hmfsr_merge_noise(ctypes.c_void_p(16), ctypes.byref(d), ctypes.c_void_p(16), ctypes.byref(p),
+                                   table, 1, 1, ctypes.c_void_p(16), None, ctypes.c_void_p(256), 1 << 40, None)
+
+    assert call(None) == -1
+    assert call(ctypes.c_void_p(264)) == -1

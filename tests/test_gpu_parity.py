@@ -276,3 +276,34 @@ def test_auto_params_match_the_oracle(dev, tiny_burst):
     motion = oracle.align(raw.numpy(), ref=0, tile=mp.tile)[1].astype(np.float32)
     rgb = hm.merge(raw.to(dev), torch.from_numpy(motion).to(dev), mp).cpu().numpy()
     assert_merge_close(rgb, oracle.merge(raw.numpy(), motion, oparams(mp), tile=mp.tile), "auto parameters")
+
+
+# --------------------------------------------------------------------------------------
+# Monte-Carlo noise statistics (Sec. 5.2.2)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("a,b,wl", [(4.0, 36.0, 4095), (0.5, 4.0, 4095), (8.0, 100.0, 7281), (0.0, 0.0, 4095)])
+def test_noise_table_matches_the_oracle(dev, a, b, wl):
+    got = hm.noise_table(a, b, wl, device=dev).cpu().numpy()
+    want = oracle.noise_table(a, b, wl)
+    # the same per-trial values on both sides; only the order of the FP64 sums differs
+    assert np.allclose(got, want.astype(np.float32), rtol=1e-6, atol=1e-9)
+
+
+def test_merge_with_noise_table(dev):
+    # a bright burst: its highlights reach the white point, where the simulated
+    # statistics depart from the closed form
+    b = burstgen.make_burst("tiny")
+    raw = np.minimum(b["raw"].numpy().astype(np.int64) * 3, 4095).astype(np.uint16)
+    rt = torch.from_numpy(raw)
+    a_, b_ = b["gain"], b["read"] ** 2
+    p = hm.MergeParams(noise_a=a_, noise_b=b_)
+    motion = oracle.align(raw, ref=0, tile=16)[1].astype(np.float32)
+    mv = torch.from_numpy(motion).to(dev)
+    table = hm.noise_table(a_, b_, 4095, device=dev)
+    otab = oracle.noise_table(a_, b_, 4095)
+    for scale in [(1, 1), (3, 2)]:
+        got = hm.merge_noise(rt.to(dev), mv, table, p, scale).cpu().numpy()
+        want = oracle.merge(raw, motion, oparams(p), scale=scale, noise_table=otab)
+        assert_merge_close(got, want, f"noise table, scale {scale}")
+    closed = hm.merge(rt.to(dev), mv, p).cpu().numpy()
+    assert not np.array_equal(closed, hm.merge_noise(rt.to(dev), mv, table, p).cpu().numpy())
