@@ -323,6 +323,19 @@ def run_gpu(args):
     t1.record(stream)
     torch.cuda.synchronize()
     tuning["noise_table_ms"] = t0.elapsed_time(t1)
+    # the whole merge with the closed form and with the table (inputs resident)
+    tmotion = hm.align(raw, 0, ap)
+    for fn in ("merge_ms", "merge_noise_ms"):
+        call = (lambda: hm.merge(raw, tmotion, p, scale)) if fn == "merge_ms" else (
+            lambda: hm.merge_noise(raw, tmotion, ntab, p, scale))
+        call()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(5):
+            call()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        tuning[fn] = t0.elapsed_time(t1) / 5
     tuning["noise_table"] = (f"{ntab.shape[0]} levels x 4096 trials x 54 Philox-4x32-10 Irwin-Hall normals "
                              "(FP64 samples, rounding and clipping)")
 
