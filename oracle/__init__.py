@@ -338,3 +338,53 @@ def philox(ctr, key) -> tuple:
     o = (ctypes.c_uint32 * 4)()
     L.orc_philox(c, k, o)
     return tuple(o)
+
+
+# ---------------------------------------------------------------------------------------
+# Subpixel alignment by a quadratic fit to the block-matching error (Sec. 3.2: the variant
+# the paper explored before settling on Lucas-Kanade)
+# ---------------------------------------------------------------------------------------
+def parabola_vertex(em: int, e0: int, ep: int) -> float:
+    """Vertex offset of the parabola through (-1, em), (0, e0), (1, ep): (em - ep) /
+    (2 (em - 2 e0 + ep)), 0 when the curvature is not positive, clamped to [-1/2, 1/2]."""
+    den = 2 * (em - 2 * e0 + ep)
+    if den <= 0:
+        return 0.0
+    return min(max(float(em - ep) / float(den), -0.5), 0.5)
+
+
+def tile_ssd(lq_ref: np.ndarray, lq_alt: np.ndarray, x0: int, y0: int, t: int, ox: int, oy: int) -> int:
+    """Exact SSD of the t x t tile at (x0, y0) of the base level against the other frame
+    displaced by (ox, oy), reads clamped as in the block-matching search."""
+    lh, lw = lq_ref.shape
+    ys = np.minimum(np.arange(y0, y0 + t), lh - 1)
+    xs = np.minimum(np.arange(x0, x0 + t), lw - 1)
+    r = lq_ref[np.ix_(ys, xs)].astype(np.int64)
+    a = lq_alt[np.ix_(np.clip(ys + oy, 0, lh - 1), np.clip(xs + ox, 0, lw - 1))].astype(np.int64)
+    return int(((r - a) ** 2).sum())
+
+
+def align_quadfit(burst, ref: int = 0, tile: int = 16, n_levels: int = 4, radius=(1, 4, 4, 4)):
+    """(motion_int int32 [n,ty,tx,2], motion float32 [n,ty,tx,2] raw px): the pyramid
+    search's integer vectors, refined per axis by the vertex of the parabola through the
+    level-0 SSD at the vector and its two neighbours on that axis (FP64, then float32)."""
+    burst = _u16(burst)
+    n, h, w = burst.shape
+    mi, _, _, _ = align(burst, ref, tile, n_levels, radius, lk_iters=0)
+    lq = [luma(burst[f]) for f in range(n)]
+    t = tile // 2
+    ty, tx = n_tiles(h, w, tile)
+    mf = np.zeros((n, ty, tx, 2), np.float32)
+    for f in range(n):
+        if f == ref:
+            continue
+        for j in range(ty):
+            for i in range(tx):
+                ux, uy = int(mi[f, j, i, 0]), int(mi[f, j, i, 1])
+                e = lambda dx, dy: tile_ssd(lq[ref], lq[f], i * t, j * t, t, ux + dx, uy + dy)
+                e0 = e(0, 0)
+                dx = parabola_vertex(e(-1, 0), e0, e(1, 0))
+                dy = parabola_vertex(e(0, -1), e0, e(0, 1))
+                mf[f, j, i, 0] = np.float32(2.0 * (ux + dx))
+                mf[f, j, i, 1] = np.float32(2.0 * (uy + dy))
+    return mi, mf

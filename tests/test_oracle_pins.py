@@ -577,3 +577,56 @@ def test_robustness_with_noise_table_keeps_identical_frames():
     p = MergeParams(noise_a=4.0, noise_b=36.0)
     R, _ = oracle.robustness(frame, frame, mv, 16, p, noise_table=oracle.noise_table(4.0, 36.0))
     assert np.all(R == 1.0)
+
+
+# --------------------------------------------------------------------------------------
+# quadratic-fit subpixel alignment (Sec. 3.2): the parabola vertex and the tile SSDs
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("d", [-0.4, -0.125, 0.0, 0.2, 0.375])
+def test_parabola_vertex_of_an_exact_parabola(d):
+    e = lambda x: 6.0 * (x - d) ** 2 + 11.0
+    assert oracle.parabola_vertex(e(-1), e(0), e(1)) == pytest.approx(d, abs=1e-15)
+
+
+def test_parabola_vertex_degenerate_and_clamped():
+    assert oracle.parabola_vertex(5, 5, 5) == 0.0                 # flat: no curvature
+    assert oracle.parabola_vertex(3, 5, 3) == 0.0                 # concave
+    assert oracle.parabola_vertex(100, 0, 0) == 0.5               # vertex beyond the sample: clamped
+    assert oracle.parabola_vertex(0, 0, 100) == -0.5
+
+
+def test_tile_ssd_is_the_plain_sum():
+    rng = np.random.default_rng(1905_03277 + 54)
+    a = rng.integers(0, 16000, size=(20, 24))
+    b = rng.integers(0, 16000, size=(20, 24))
+    for (x0, y0, ox, oy) in [(0, 0, 1, -1), (16, 12, 3, 5), (8, 16, -9, 2)]:
+        tot = 0
+        for j in range(8):
+            for i in range(8):
+                y, x = min(y0 + j, 19), min(x0 + i, 23)
+                ya, xa = min(max(y + oy, 0), 19), min(max(x + ox, 0), 23)
+                tot += (int(a[y, x]) - int(b[ya, xa])) ** 2
+        assert oracle.tile_ssd(a, b, x0, y0, 8, ox, oy) == tot
+
+
+def test_quadfit_recovers_subpixel_shifts_of_a_smooth_scene():
+    # a smooth scene shifted by known subpixel amounts: the fit lands near them, and, as
+    # the paper found, less accurately than three Lucas-Kanade iterations
+    from scipy import ndimage
+    rng = np.random.default_rng(1905_03277 + 55)
+    base = ndimage.gaussian_filter(rng.random((160, 160)), 4.0) * 12000 + 800
+    shifts = (0.0, 0.5, 1.25)  # half-res px along x (0.6 of it along y)
+    frames = [np.clip(ndimage.shift(base, (0.6 * s, s), order=3, mode="nearest"), 0, 4 * 4095 - 1) for s in shifts]
+    raw = np.stack([np.kron(f / 4.0, np.ones((2, 2))) for f in frames]).astype(np.uint16)[:, :128, :128]
+    _, mq = oracle.align_quadfit(raw, ref=0, tile=32, n_levels=1, radius=(4,))
+    _, ml, _, _ = oracle.align(raw, ref=0, tile=32, n_levels=1, radius=(4,), lk_iters=3)
+    err_q, err_l = [], []
+    for f in (1, 2):
+        # content moved by +s half-res px: the base -> frame displacement is +2 s raw px
+        want = np.array([2.0 * shifts[f], 1.2 * shifts[f]])
+        q = np.median(mq[f, 1:-1, 1:-1].reshape(-1, 2), axis=0)
+        lk = np.median(ml[f, 1:-1, 1:-1].reshape(-1, 2), axis=0)
+        assert np.all(np.abs(q - want) < 0.35), (q, want)
+        err_q.append(np.abs(q - want).max())
+        err_l.append(np.abs(lk - want).max())
+    assert max(err_l) < max(err_q)
