@@ -355,11 +355,11 @@ def parabola_vertex(em: int, e0: int, ep: int) -> float:
 
 def tile_ssd(lq_ref: np.ndarray, lq_alt: np.ndarray, x0: int, y0: int, t: int, ox: int, oy: int) -> int:
     """Exact SSD of the t x t tile at (x0, y0) of the base level against the other frame
-    displaced by (ox, oy), reads clamped as in the block-matching search."""
+    displaced by (ox, oy), reads clamped as in the block-matching search: the base at the
+    clamped tile pixel, the other frame at the clamped displaced (unclamped) pixel."""
     lh, lw = lq_ref.shape
-    ys = np.minimum(np.arange(y0, y0 + t), lh - 1)
-    xs = np.minimum(np.arange(x0, x0 + t), lw - 1)
-    r = lq_ref[np.ix_(ys, xs)].astype(np.int64)
+    ys, xs = np.arange(y0, y0 + t), np.arange(x0, x0 + t)
+    r = lq_ref[np.ix_(np.minimum(ys, lh - 1), np.minimum(xs, lw - 1))].astype(np.int64)
     a = lq_alt[np.ix_(np.clip(ys + oy, 0, lh - 1), np.clip(xs + ox, 0, lw - 1))].astype(np.int64)
     return int(((r - a) ** 2).sum())
 

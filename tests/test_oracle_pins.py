@@ -599,12 +599,14 @@ def test_tile_ssd_is_the_plain_sum():
     rng = np.random.default_rng(1905_03277 + 54)
     a = rng.integers(0, 16000, size=(20, 24))
     b = rng.integers(0, 16000, size=(20, 24))
-    for (x0, y0, ox, oy) in [(0, 0, 1, -1), (16, 12, 3, 5), (8, 16, -9, 2)]:
+    # the last two tiles overhang the 20 x 24 level: the base reads its edge pixel, the
+    # other frame the clamped displaced position
+    for (x0, y0, ox, oy) in [(0, 0, 1, -1), (16, 12, 3, 5), (8, 16, -9, 2), (20, 16, -3, -2)]:
         tot = 0
         for j in range(8):
             for i in range(8):
                 y, x = min(y0 + j, 19), min(x0 + i, 23)
-                ya, xa = min(max(y + oy, 0), 19), min(max(x + ox, 0), 23)
+                ya, xa = min(max(y0 + j + oy, 0), 19), min(max(x0 + i + ox, 0), 23)
                 tot += (int(a[y, x]) - int(b[ya, xa])) ** 2
         assert oracle.tile_ssd(a, b, x0, y0, 8, ox, oy) == tot
 
