@@ -87,6 +87,17 @@ hmfsr_status hmfsr_align(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
                          const hmfsr_align_params *params, float *motion_dev, int32_t *motion_int_dev,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* hmfsr_align with the subpixel step the paper explored before Lucas-Kanade (Sec. 3.2): a
+ * quadratic fit to the block-matching error.  After the same pyramid search, each tile's
+ * exact level-0 SSD at its integer vector u and at the two neighbours along each axis give
+ * per axis the vertex of the parabola through the three, (E- - E+) / (2 (E- - 2 E0 + E+)),
+ * 0 unless that curvature is positive, clamped to [-1/2, 1/2]; motion = 2 (u + vertex)
+ * raw px, computed in FP64.  params->lk_iters is ignored; everything else as hmfsr_align,
+ * with the same workspace (HMFSR_OP_ALIGN). */
+hmfsr_status hmfsr_align_quadfit(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                                 const hmfsr_align_params *params, float *motion_dev, int32_t *motion_int_dev,
+                                 void *ws, size_t ws_bytes, void *stream);
+
 /* merge(burst, motion, params, scale) -> RGB (Sec. 5, Eq. 1-9 and supplement S.1): per
  * frame, kernel covariances from the half-res structure tensor (Eq. 3-4), robustness from
  * local statistics, the noise model and the motion prior (Eq. 5-9), then per-channel

@@ -106,9 +106,10 @@ def workspace_size(op: int, burst_shape, tile: int, scale=(1, 1), white_level: i
 
 
 def align(burst: torch.Tensor, ref: int = 0, params: AlignParams | None = None, with_int: bool = False,
-          white_level: int = 4095, stream=None):
+          white_level: int = 4095, stream=None, subpixel: str = "lk"):
     """Tile motion field float32 [n, TY, TX, 2] in raw px (base -> frame), computed by
-    hmfsr_align.  With `with_int`, also the integer block-matching vectors (half-res px)."""
+    hmfsr_align (subpixel="lk") or hmfsr_align_quadfit (subpixel="quadfit").  With
+    `with_int`, also the integer block-matching vectors (half-res px)."""
     L = _lib.load()
     params = params or AlignParams()
     if not burst.is_cuda:
@@ -121,8 +122,11 @@ def align(burst: torch.Tensor, ref: int = 0, params: AlignParams | None = None, 
     nbytes = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(d), params.tile, 1, 1)
     ws = _workspace(burst.device, nbytes)
     pc = params.c()
-    _lib.check(L.hmfsr_align(_ptr(burst), ctypes.byref(d), ctypes.byref(pc), _ptr(motion), _ptr(mint), _ptr(ws),
-                             ws.numel(), _stream(burst.device, stream)), "hmfsr_align")
+    if subpixel not in ("lk", "quadfit"):
+        raise ValueError("subpixel must be 'lk' (Lucas-Kanade) or 'quadfit' (quadratic fit to the matching error)")
+    fn = L.hmfsr_align if subpixel == "lk" else L.hmfsr_align_quadfit
+    _lib.check(fn(_ptr(burst), ctypes.byref(d), ctypes.byref(pc), _ptr(motion), _ptr(mint), _ptr(ws), ws.numel(),
+                  _stream(burst.device, stream)), "hmfsr_align")
     return (motion, mint) if with_int else motion
 
 

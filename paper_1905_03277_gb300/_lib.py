@@ -86,7 +86,7 @@ EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_pr
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
            "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
-           "hmfsr_noise_table", "hmfsr_merge_noise",
+           "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit",
            "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
@@ -141,6 +141,8 @@ def load(path: str | None = None):
     L.hmfsr_snr_tuning.argtypes = [ctypes.c_double, ctypes.c_float, ctypes.c_float, P(MergeParamsC), P(AlignParamsC),
                                    P(ctypes.c_double)]
     L.hmfsr_snr_tuning.restype = ci
+    L.hmfsr_align_quadfit.argtypes = [vp, P(BurstDesc), P(AlignParamsC), vp, vp, vp, sz, vp]
+    L.hmfsr_align_quadfit.restype = ci
     L.hmfsr_noise_table.argtypes = [ctypes.c_float, ctypes.c_float, ci, vp, vp]
     L.hmfsr_noise_table.restype = ci
     L.hmfsr_merge_noise.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, ci, ci, vp, vp, vp, sz, vp]

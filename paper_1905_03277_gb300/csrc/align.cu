@@ -41,6 +41,14 @@ __global__ void __launch_bounds__(128) k_ssd_split(const uint16_t *__restrict__ 
 }
 
 template <int T>
+__global__ void __launch_bounds__(128) k_quadfit(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                                 const int2 *__restrict__ vec0, int ref, float *__restrict__ motion,
+                                                 int32_t *__restrict__ motion_int) {
+    stage::quadfit<T>(L0, lh, lw, lty, ltx, vec0, ref, motion, motion_int, blockIdx.x * blockDim.x + threadIdx.x,
+                      blockIdx.y);
+}
+
+template <int T>
 __global__ void k_lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
                            const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
                            int32_t *__restrict__ motion_int) {
@@ -107,6 +115,29 @@ static void run_search(const Geom &g, const hmfsr_align_params &p, const AlignLe
     else
         k_lk<T><<<dim3(div_up(tiles0 * 32, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
                                                            L.vec[0], g.ref, p.lk_iters, motion, motion_int);
+}
+
+template <int T>
+static void launch_quadfit(const Geom &g, const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s) {
+    const int tiles0 = L.lty[0] * L.ltx[0];
+    k_quadfit<T><<<dim3(div_up(tiles0, 128), g.n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
+                                                               L.vec[0], g.ref, motion, motion_int);
+}
+
+cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p,
+                                 const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s) {
+    hmfsr_align_params q = p;
+    q.lk_iters = 0;  // the search's vectors; the fit below replaces the Lucas-Kanade step
+    cudaError_t e = launch_align(burst, g, q, L, motion, motion_int, s);
+    if (e != cudaSuccess) return e;
+    switch (p.tile) {
+        case 8: launch_quadfit<4>(g, L, motion, motion_int, s); break;
+        case 16: launch_quadfit<8>(g, L, motion, motion_int, s); break;
+        case 32: launch_quadfit<16>(g, L, motion, motion_int, s); break;
+        case 64: launch_quadfit<32>(g, L, motion, motion_int, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,

@@ -172,6 +172,22 @@ hmfsr_status hmfsr_align(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
     return cuda_status(launch_align(burst_dev, g, *params, L, motion_dev, motion_int_dev, (cudaStream_t)stream));
 }
 
+hmfsr_status hmfsr_align_quadfit(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                                 const hmfsr_align_params *params, float *motion_dev, int32_t *motion_int_dev,
+                                 void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !aligned4(burst_dev) || !valid_align_params(params)) return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    AlignLevels L;
+    size_t need = carve_align(nullptr, g, params->tile, params->n_levels, &L);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_align(ws, g, params->tile, params->n_levels, &L);
+    return cuda_status(launch_align_quadfit(burst_dev, g, *params, L, motion_dev, motion_int_dev,
+                                            (cudaStream_t)stream));
+}
+
 hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
                          const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
                          float *den_dev, void *ws, size_t ws_bytes, void *stream) {

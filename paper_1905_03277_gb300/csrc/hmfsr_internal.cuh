@@ -91,6 +91,9 @@ struct AlignLevels {
 };
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s);
+// the same search, then the quadratic-fit subpixel step instead of Lucas-Kanade
+cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p,
+                                 const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s);
 
 // merge
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,

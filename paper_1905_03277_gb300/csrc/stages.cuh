@@ -472,6 +472,56 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
     }
 }
 
+// Subpixel refinement by a quadratic fit (Sec. 3.2: the variant the paper explored before
+// Lucas-Kanade), one thread per level-0 tile: the exact SSD at the integer vector and at
+// its neighbours along each axis, and per axis the vertex of the parabola through the
+// three, (E- - E+) / (2 (E- - 2 E0 + E+)), 0 unless the curvature is positive, clamped to
+// [-1/2, 1/2].  FP64 from exact integers, so the result is the same bits as an FP64
+// restatement on the CPU.
+__device__ __forceinline__ double parabola_vertex(long long em, long long e0, long long ep) {
+    const long long den = 2 * (em - 2 * e0 + ep);
+    if (den <= 0) return 0.0;
+    return fmin(fmax(__ddiv_rn((double)(em - ep), (double)den), -0.5), 0.5);
+}
+
+template <int T>
+__device__ __forceinline__ void quadfit(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                        const int2 *__restrict__ vec0, int ref, float *__restrict__ motion,
+                                        int32_t *__restrict__ motion_int, int tile, int f) {
+    if (tile >= lty * ltx) return;
+    const size_t o = (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        motion[2 * o] = 0.f;
+        motion[2 * o + 1] = 0.f;
+        if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+        return;
+    }
+    const int ty = tile / ltx, tx = tile - ty * ltx;
+    const uint16_t *R = L0 + (size_t)ref * lh * lw;
+    const uint16_t *A = L0 + (size_t)f * lh * lw;
+    const int2 u = vec0[o];
+    const int x0 = tx * T, y0 = ty * T;
+    auto ssd_at = [&](int dx, int dy) -> long long {
+        long long e = 0;
+        for (int j = 0; j < T; ++j) {
+            const uint16_t *rr = R + min(y0 + j, lh - 1) * lw;
+            const uint16_t *ar = A + clampi(y0 + j + u.y + dy, 0, lh - 1) * lw;
+#pragma unroll
+            for (int i = 0; i < T; ++i) {
+                const int d = (int)__ldg(rr + min(x0 + i, lw - 1)) - (int)__ldg(ar + clampi(x0 + i + u.x + dx, 0, lw - 1));
+                e += (long long)(d * d);
+            }
+        }
+        return e;
+    };
+    const long long e0 = ssd_at(0, 0);
+    const double dx = parabola_vertex(ssd_at(-1, 0), e0, ssd_at(1, 0));
+    const double dy = parabola_vertex(ssd_at(0, -1), e0, ssd_at(0, 1));
+    motion[2 * o] = (float)__dmul_rn(2.0, __dadd_rn((double)u.x, dx));
+    motion[2 * o + 1] = (float)__dmul_rn(2.0, __dadd_rn((double)u.y, dy));
+    if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+}
+
 // ======================================================================================
 // merge preparation (Sec. 5.1.2, 5.2)
 // ======================================================================================

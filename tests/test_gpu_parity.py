@@ -307,3 +307,15 @@ def test_merge_with_noise_table(dev):
         assert_merge_close(got, want, f"noise table, scale {scale}")
     closed = hm.merge(rt.to(dev), mv, p).cpu().numpy()
     assert not np.array_equal(closed, hm.merge_noise(rt.to(dev), mv, table, p).cpu().numpy())
+
+
+# --------------------------------------------------------------------------------------
+# quadratic-fit subpixel alignment (Sec. 3.2): exact SSDs and FP64 vertex on both sides
+# --------------------------------------------------------------------------------------
+def test_align_quadfit_bit_exact(dev, tiny_burst):
+    b = burstgen.make_burst(dict(n=4, h=136, w=200, gain=1.0, read=2.0, motion="global", scale=(1, 1)), seed=21)
+    for raw, ref, tile in [(tiny_burst["raw"], 0, 16), (b["raw"], 2, 16), (b["raw"], 1, 32), (b["raw"], 3, 8)]:
+        g_motion, g_int = hm.align(raw.to(dev), ref, hm.AlignParams(tile=tile), with_int=True, subpixel="quadfit")
+        mi, mf = oracle.align_quadfit(raw.numpy(), ref=ref, tile=tile)
+        assert np.array_equal(g_int.cpu().numpy(), mi)
+        assert np.array_equal(g_motion.cpu().numpy(), mf)
