@@ -495,6 +495,92 @@ def run_fit(args):
     return 0
 
 
+def run_study_corruption(args):
+    """Motion-robustness efficacy (Sec. 7.3) on synthetic bursts with ground truth: the
+    PSNR of the merge, with the robustness and with it off (t = -1, so R = 1), as the
+    alignment is corrupted in the two ways the paper describes.  Also the quadratic-fit
+    subpixel step against Lucas-Kanade on the clean field.  One JSON line."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import burstgen
+    import paper_1905_03277_gb300 as hm
+
+    dev = torch.device("cuda", 0)
+    hm.build()
+    scale, tile, crop = (3, 2), 16, 24
+    ps, sigmas = (0.1, 0.2, 0.3, 0.4, 0.5), (0.05, 0.1, 0.15, 0.2, 0.25)
+    rng = np.random.default_rng(burstgen.SEED_BASE + 70)
+
+    def psnr(rgb, gt):
+        d = (rgb - gt)[:, crop:-crop, crop:-crop].double()
+        return 10.0 * math.log10(4095.0 ** 2 / float((d * d).mean()))
+
+    def replace_tiles(m, frac, ref):
+        # a fraction of each non-base frame's tiles get a vector that points at a different
+        # area: displaced by one to three tiles along some axis
+        m = m.copy()
+        n, ty, tx, _ = m.shape
+        for f in range(n):
+            if f == ref:
+                continue
+            idx = rng.choice(ty * tx, size=int(round(frac * ty * tx)), replace=False)
+            d = rng.integers(-3 * tile, 3 * tile + 1, size=(idx.size, 2))
+            small = np.abs(d).max(axis=1) < tile
+            while small.any():
+                d[small] = rng.integers(-3 * tile, 3 * tile + 1, size=(int(small.sum()), 2))
+                small = np.abs(d).max(axis=1) < tile
+            flat = m[f].reshape(-1, 2)
+            flat[idx] += d.astype(np.float32)
+        return m
+
+    def add_noise(m, sigma, ref):
+        m = m.copy()
+        keep = m[ref].copy()
+        m += rng.normal(0.0, sigma, size=m.shape).astype(np.float32)
+        m[ref] = keep
+        return m
+
+    rows = {"clean": [], "quadfit": [], "replace": {p: [] for p in ps}, "noise": {s: [] for s in sigmas}}
+    n_bursts = 4
+    for k in range(n_bursts):
+        b = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 60 + k, device=dev, with_gt=True)
+        raw, gt = b["raw"], b["gt"]
+        on = hm.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2)
+        off = hm.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2, t=-1.0)
+        ap = hm.AlignParams(tile=tile)
+        mv = hm.align(raw, 0, ap).cpu().numpy()
+
+        def both(m):
+            mt = torch.from_numpy(m).to(dev)
+            return (psnr(hm.merge(raw, mt, on, scale), gt), psnr(hm.merge(raw, mt, off, scale), gt))
+
+        rows["clean"].append(both(mv))
+        rows["quadfit"].append(both(hm.align(raw, 0, ap, subpixel="quadfit").cpu().numpy()))
+        for p in ps:
+            rows["replace"][p].append(both(replace_tiles(mv, p, 0)))
+        for sg in sigmas:
+            rows["noise"][sg].append(both(add_noise(mv, sg, 0)))
+
+    def mean2(v):
+        a = np.array(v)
+        return {"psnr_robust_db": float(a[:, 0].mean()), "psnr_no_robustness_db": float(a[:, 1].mean())}
+
+    print(json.dumps({
+        "study": "motion robustness efficacy (Sec. 7.3) on synthetic bursts",
+        "workload": f"{n_bursts} bursts x 8 x 1024x1024 RGGB (fit workload), 1.5x, PSNR against the rendered "
+                    f"ground truth inside a {crop}-px border",
+        "clean_lk": mean2(rows["clean"]), "clean_quadfit": mean2(rows["quadfit"]),
+        "tile_replacement": [dict(p=p, **mean2(rows["replace"][p])) for p in ps],
+        "vector_noise_px": [dict(sigma=sg, **mean2(rows["noise"][sg])) for sg in sigmas],
+        "corruption": "replacement: the tile's vector displaced by 1-3 tiles along some axis (a different area); "
+                      "noise: N(0, sigma^2) raw px added to each component of each non-base tile's vector"}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,6 +593,7 @@ def main():
     ap.add_argument("--batch-bursts", type=int, default=64)
     ap.add_argument("--fit-steps", type=int, default=200)
     ap.add_argument("--fit-bursts", type=int, default=16)
+    ap.add_argument("--study", choices=("corruption",), help="run an evaluation study instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -514,6 +601,8 @@ def main():
         return run_reference(args)
     if args.fit:
         return run_fit(args)
+    if args.study == "corruption":
+        return run_study_corruption(args)
     return run_gpu(args)
 
 
