@@ -35,7 +35,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
-        "t", "s1", "s2", "m_th", "noise_a", "noise_b")] + [("noise_table", ctypes.c_void_p)]
+        "t", "s1", "s2", "m_th", "noise_a", "noise_b")] + [("noise_table", ctypes.c_void_p),
+                                                            ("hf_loss", ctypes.c_double)]
 
 
 @dataclass
@@ -54,11 +55,13 @@ class MergeParams:
     noise_a: float = 1.0
     noise_b: float = 4.0
 
-    def c(self, noise_table=None) -> _Params:
+    def c(self, noise_table=None, hf_loss: float = 0.0) -> _Params:
         """The C struct; `noise_table` (NOISE_LEVELS x 4, from noise_table()) replaces the
-        closed-form noise statistics."""
+        closed-form noise statistics; `hf_loss` > 0 switches on the high-frequency
+        rejection with that threshold."""
         # promote the float32 values the CUDA path sees
-        p = _Params(*[float(np.float32(getattr(self, f.name))) for f in fields(self)], None)
+        p = _Params(*[float(np.float32(getattr(self, f.name))) for f in fields(self)], None,
+                    float(np.float32(hf_loss)))
         if noise_table is not None:
             tab = np.ascontiguousarray(noise_table, dtype=np.float64)
             if tab.shape != (NOISE_LEVELS, 4):
@@ -168,13 +171,13 @@ def tile_strength(motion_frame, params: MergeParams):
     return M, s
 
 
-def robustness(base, alt, motion_alt, tile: int, params: MergeParams, wl: int = 4095, noise_table=None):
+def robustness(base, alt, motion_alt, tile: int, params: MergeParams, wl: int = 4095, noise_table=None, hf_loss: float = 0.0):
     base, alt = _u16(base), _u16(alt)
     h, w = base.shape
     mv = np.ascontiguousarray(motion_alt, dtype=np.float32)
     R = np.empty((h // 2, w // 2), np.float64)
     Rh = np.empty((h // 2, w // 2), np.float64)
-    p = params.c(noise_table)
+    p = params.c(noise_table, hf_loss)
     _check(lib().orc_robustness(_ptr(base, ctypes.c_uint16), _ptr(alt, ctypes.c_uint16), h, w,
                                 _ptr(mv, ctypes.c_float), tile, ctypes.byref(p), wl,
                                 _ptr(R, ctypes.c_double), _ptr(Rh, ctypes.c_double)), "robustness")
@@ -187,7 +190,7 @@ def out_size(h: int, w: int, scale) -> tuple:
 
 
 def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: int = 16, wl: int = 4095,
-          rows=None, with_den: bool = False, n_threads: int = 0, noise_table=None):
+          rows=None, with_den: bool = False, n_threads: int = 0, noise_table=None, hf_loss: float = 0.0):
     """Oracle merge of output rows [y0, y1) (all rows by default): double [3, rows, Wo]."""
     burst = _u16(burst)
     n, h, w = burst.shape
@@ -199,7 +202,7 @@ def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: 
     y0, y1 = (0, ho) if rows is None else rows
     out = np.empty((3, y1 - y0, wo), np.float64)
     den = np.empty((3, y1 - y0, wo), np.float64) if with_den else None
-    p = params.c(noise_table)
+    p = params.c(noise_table, hf_loss)
     _check(lib().orc_merge_rows(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
                                 ctypes.byref(p), wl, scale[0], scale[1], y0, y1, _ptr(out, ctypes.c_double),
                                 _ptr(den, ctypes.c_double) if den is not None else None, n_threads), "merge")
@@ -207,14 +210,14 @@ def merge(burst, motion, params: MergeParams, scale=(1, 1), ref: int = 0, tile: 
 
 
 def merge_pixels(burst, motion, params: MergeParams, xy, scale=(1, 1), ref: int = 0, tile: int = 16,
-                 wl: int = 4095, n_threads: int = 0, noise_table=None) -> np.ndarray:
+                 wl: int = 4095, n_threads: int = 0, noise_table=None, hf_loss: float = 0.0) -> np.ndarray:
     """Oracle merge of the output pixels xy[k] = (X, Y): double [k, 3]."""
     burst = _u16(burst)
     n, h, w = burst.shape
     mv = np.ascontiguousarray(motion, dtype=np.float32)
     xy = np.ascontiguousarray(xy, dtype=np.int32)
     out = np.empty((xy.shape[0], 3), np.float64)
-    p = params.c(noise_table)
+    p = params.c(noise_table, hf_loss)
     _check(lib().orc_merge_pixels(_ptr(burst, ctypes.c_uint16), n, h, w, ref, _ptr(mv, ctypes.c_float), tile,
                                   ctypes.byref(p), wl, scale[0], scale[1], _ptr(xy, ctypes.c_int32),
                                   xy.shape[0], _ptr(out, ctypes.c_double), n_threads), "merge_pixels")
@@ -388,3 +391,24 @@ def align_quadfit(burst, ref: int = 0, tile: int = 16, n_levels: int = 4, radius
                 mf[f, j, i, 0] = np.float32(2.0 * (ux + dx))
                 mf[f, j, i, 1] = np.float32(2.0 * (uy + dy))
     return mi, mf
+
+
+
+def hf_loss_map(base, kappa: float) -> np.ndarray:
+    """bool [H/2, W/2]: the high-frequency test of every base texel, restated in NumPy from
+    exact integer sums (the variance of the 3x3 local means against kappa times the 3x3
+    variance, R and B at full weight, green at a quarter)."""
+    base = _u16(base).astype(np.int64)
+    q = {0: base[0::2, 0::2], 1: base[0::2, 1::2] + base[1::2, 0::2], 2: base[1::2, 1::2]}
+    hh, wh = q[0].shape
+    pad = lambda a: np.pad(a, 1, mode="edge")
+    def box(a):
+        p = pad(a)
+        return sum(p[j:j + hh, i:i + wh] for j in range(3) for i in range(3))
+    A = np.zeros((hh, wh), np.int64)
+    B = np.zeros((hh, wh), np.int64)
+    for c, wgt in ((0, 4), (1, 1), (2, 4)):
+        s1, s2 = box(q[c]), box(q[c] * q[c])
+        B += wgt * (9 * s2 - s1 * s1)
+        A += wgt * (9 * box(s1 * s1) - box(s1) ** 2)
+    return (B > 0) & (A.astype(np.float64) < float(np.float32(kappa)) * (81.0 * B.astype(np.float64)))

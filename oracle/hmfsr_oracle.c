@@ -316,12 +316,42 @@ static void modelled_stats(const orc_params *p, int wl, double mu, int c, double
     *dmd2 = 2.0 * v / 9.0;
 }
 
+/* High-frequency artifact test (supplement, High Frequency Artifacts Removal) at base
+ * texel (u, v): the local variance lost to the low-pass.  "Before" is the 3x3 population
+ * variance of the guide, summed over R, G, B; "after" is the population variance of the
+ * 3x3 local means over the 3x3 texels around (u, v) (clamped to the grid).  With the
+ * green guide at half scale, 4 x both variances times 81 and 6561 are the exact integers
+ * B = sum_c w_c (9 S2 - S1^2) and A = sum_c w_c (9 sum_k S1_k^2 - (sum_k S1_k)^2),
+ * w = (4, 1, 4): the loss is A < kappa 81 B, decided in FP64 from exact integers. */
+static int hf_loss_at(const uint16_t *base, int h, int w, int u, int v, double kappa)
+{
+    static const int64_t wgt[3] = {4, 1, 4};
+    int64_t A = 0, B = 0;
+    for (int c = 0; c < 3; ++c) {
+        int64_t s1 = box_sum(base, h, w, u, v, c, 0), s2 = box_sum(base, h, w, u, v, c, 1);
+        B += wgt[c] * (9 * s2 - s1 * s1);
+        int64_t t1 = 0, t2 = 0;
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+                int64_t m = box_sum(base, h, w, clampi(u + i, 0, w / 2 - 1), clampi(v + j, 0, h / 2 - 1), c, 0);
+                t1 += m;
+                t2 += m * m;
+            }
+        A += wgt[c] * (9 * t2 - t1 * t1);
+    }
+    return B > 0 && (double)A < kappa * (81.0 * (double)B);
+}
+
 static double robustness_at(const uint16_t *base, const uint16_t *alt, const float *motion_alt,
                             const double *s_tile, const rob_geom *g, int u, int v)
 {
     const orc_params *p = g->p;
     int tyi = clampi((2 * v) / g->tile, 0, g->ty - 1);
     int txi = clampi((2 * u) / g->tile, 0, g->tx - 1);
+    /* high-frequency regions with a large local motion span are rejected outright */
+    if (p->hf_loss > 0.0 && tile_M(motion_alt, g->ty, g->tx, tyi, txi) > p->m_th &&
+        hf_loss_at(base, g->h, g->w, u, v, p->hf_loss))
+        return 0.0;
     const float *mv = motion_alt + ((size_t)tyi * g->tx + txi) * 2;
     double fx = (double)u + 0.5 * (double)mv[0];
     double fy = (double)v + 0.5 * (double)mv[1];

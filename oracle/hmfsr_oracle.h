@@ -32,6 +32,10 @@ typedef struct {
     /* NULL: the closed-form noise statistics; else ORC_NOISE_LEVELS x 4 values from
      * orc_noise_table (Monte-Carlo sigma_md^2 and d_md^2 per brightness level) */
     const double *noise_table;
+    /* 0: off; else the high-frequency rejection threshold kappa (supplement, High
+     * Frequency Artifacts Removal): R = 0 where the variance of the 3x3 local means is
+     * below kappa times the local variance and the tile's motion span M exceeds m_th */
+    double hf_loss;
 } orc_params;
 
 /* Monte-Carlo noise statistics (Sec. 5.2.2: sigma_md and d_md "through a series of Monte

@@ -632,3 +632,43 @@ def test_quadfit_recovers_subpixel_shifts_of_a_smooth_scene():
         err_q.append(np.abs(q - want).max())
         err_l.append(np.abs(lk - want).max())
     assert max(err_l) < max(err_q)
+
+
+# --------------------------------------------------------------------------------------
+# high-frequency artifact rejection (supplement, High Frequency Artifacts Removal)
+# --------------------------------------------------------------------------------------
+def _hf_scene(h=64, w=96):
+    # left: a pattern at the guide's Nyquist frequency (4 raw px period); right: a smooth ramp
+    y, x = np.mgrid[0:h, 0:w]
+    hf = 2000 + 1500 * np.where(((x // 2) + (y // 2)) % 2 == 0, 1, -1)
+    smooth = 500 + 20 * x + 10 * y
+    return np.where(x < w // 2, hf, smooth).astype(np.uint16)
+
+
+def test_hf_loss_map_flags_nyquist_content_only():
+    m = oracle.hf_loss_map(_hf_scene(), 0.03)
+    hh, wh = m.shape
+    assert m[2:-2, 2:wh // 2 - 2].all()          # the pattern lost its variance to the 3x3 means
+    assert not m[:, wh // 2 + 2:].any()          # a ramp keeps it
+    assert not oracle.hf_loss_map(_hf_scene(), 0.0).any()
+
+
+def test_hf_rejection_in_the_robustness_matches_the_restatement():
+    base = _hf_scene()
+    rng = np.random.default_rng(1905_03277 + 56)
+    alt = np.clip(base.astype(np.int64) + rng.integers(-3, 4, size=base.shape), 0, 4095).astype(np.uint16)
+    ty, tx = 4, 6
+    p = MergeParams(noise_a=1.0, noise_b=4.0)
+    # checkerboard of +-0.5 px tile vectors: every tile's motion span exceeds m_th
+    mv = np.zeros((ty, tx, 2), np.float32)
+    mv[..., 0] = np.where((np.add.outer(np.arange(ty), np.arange(tx)) % 2) == 0, 0.5, -0.5)
+    R_off, _ = oracle.robustness(base, alt, mv, 16, p)
+    R_on, _ = oracle.robustness(base, alt, mv, 16, p, hf_loss=0.03)
+    flag = oracle.hf_loss_map(base, 0.03)
+    assert flag.any()
+    assert np.all(R_on[flag] == 0.0)
+    assert np.array_equal(R_on[~flag], R_off[~flag])
+    # with no motion span nothing is rejected, whatever the content
+    R_still, _ = oracle.robustness(base, alt, np.zeros_like(mv), 16, p, hf_loss=0.03)
+    R_still_off, _ = oracle.robustness(base, alt, np.zeros_like(mv), 16, p)
+    assert np.array_equal(R_still, R_still_off)
