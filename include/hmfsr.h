@@ -260,6 +260,27 @@ hmfsr_status hmfsr_merge_noise(const uint16_t *burst_dev, const hmfsr_burst_desc
                                int scale_den, float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes,
                                void *stream);
 
+/* ---- Options of the merge beyond hmfsr_merge_params.  ---- */
+typedef struct {
+    /* NULL: the closed-form noise statistics of Eq. 6; else a table from
+     * hmfsr_noise_table (device, 16-byte aligned) for this burst's noise model and WL */
+    const float *noise_table;
+    /* 0: off; else kappa of the high-frequency artifact rejection (supplement, High
+     * Frequency Artifacts Removal): a base texel whose 3x3 local means keep less than
+     * kappa of its 3x3 local variance (R, G, B summed, exact integer sums, FP64 test) is
+     * rejected (R = 0) in every frame whose tile there has a motion span M > m_th
+     * (Eq. 7).  0.03 sits between a pattern at the guide's Nyquist frequency (~0.012) and
+     * pure noise (~0.05). */
+    float hf_loss;
+} hmfsr_merge_options;
+
+/* hmfsr_merge with the options above (all zero: exactly hmfsr_merge).  Same arguments,
+ * workspace size (HMFSR_OP_MERGE) and errors; HMFSR_ERR_INVALID_ARG also for a NULL
+ * `opts`, a misaligned table or a negative or non-finite hf_loss. */
+hmfsr_status hmfsr_merge_ex(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                            const hmfsr_merge_params *params, const hmfsr_merge_options *opts, int scale_num,
+                            int scale_den, float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes, void *stream);
+
 /* Host-only (no GPU): from the base frame's mean sample value `mean` (DN) and the noise
  * model var(x) = noise_a * x + noise_b, SNR = mean / sqrt(noise_a * mean + noise_b) (one
  * raw sample of one frame; +infinity for a noise-free model), then every parameter of

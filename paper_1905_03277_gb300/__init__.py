@@ -20,7 +20,7 @@ from . import _lib
 from ._lib import build  # noqa: F401  (re-exported)
 
 __all__ = ["MergeParams", "AlignParams", "align", "merge", "merge_stages", "align_merge", "AlignMergePipeline", "build",
-           "workspace_size", "out_size", "n_tiles", "frame_sum", "snr_tuning", "auto_params", "noise_table", "merge_noise"]
+           "workspace_size", "out_size", "n_tiles", "frame_sum", "snr_tuning", "auto_params", "noise_table", "merge_noise", "merge_ex"]
 
 
 @dataclass
@@ -332,6 +332,29 @@ def merge_noise(burst: torch.Tensor, motion: torch.Tensor, table: torch.Tensor, 
     _lib.check(L.hmfsr_merge_noise(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(table), scale[0],
                                    scale[1], _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
                "hmfsr_merge_noise")
+    return (rgb, den) if with_den else rgb
+
+
+def merge_ex(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
+             noise_table: torch.Tensor | None = None, hf_loss: float = 0.0, with_den: bool = False,
+             white_level: int = 4095, stream=None):
+    """`merge` with the options of hmfsr_merge_ex: Monte-Carlo noise statistics from
+    `noise_table` (from noise_table()) and the high-frequency rejection with threshold
+    `hf_loss` (0: off)."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ho, wo = out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
+    ws = _workspace(burst.device, nbytes)
+    pc = params.c()
+    opts = _lib.MergeOptionsC(noise_table.data_ptr() if noise_table is not None else None, float(hf_loss))
+    _lib.check(L.hmfsr_merge_ex(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), ctypes.byref(opts),
+                                scale[0], scale[1], _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(),
+                                _stream(burst.device, stream)), "hmfsr_merge_ex")
     return (rgb, den) if with_den else rgb
 
 

@@ -74,6 +74,10 @@ class AlignParamsC(ctypes.Structure):
                 ("lk_iters", ctypes.c_int)]
 
 
+class MergeOptionsC(ctypes.Structure):
+    _fields_ = [("noise_table", ctypes.c_void_p), ("hf_loss", ctypes.c_float)]
+
+
 class MergeParamsC(ctypes.Structure):
     _fields_ = [(n, ctypes.c_float) for n in ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
                                               "t", "s1", "s2", "m_th", "noise_a", "noise_b")] + [
@@ -86,7 +90,7 @@ EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_pr
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
            "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
-           "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit",
+           "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit", "hmfsr_merge_ex",
            "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
@@ -143,6 +147,8 @@ def load(path: str | None = None):
     L.hmfsr_snr_tuning.restype = ci
     L.hmfsr_align_quadfit.argtypes = [vp, P(BurstDesc), P(AlignParamsC), vp, vp, vp, sz, vp]
     L.hmfsr_align_quadfit.restype = ci
+    L.hmfsr_merge_ex.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), P(MergeOptionsC), ci, ci, vp, vp, vp, sz, vp]
+    L.hmfsr_merge_ex.restype = ci
     L.hmfsr_noise_table.argtypes = [ctypes.c_float, ctypes.c_float, ci, vp, vp]
     L.hmfsr_noise_table.restype = ci
     L.hmfsr_merge_noise.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, ci, ci, vp, vp, vp, sz, vp]

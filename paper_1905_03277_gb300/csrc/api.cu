@@ -107,6 +107,7 @@ size_t carve_merge(void *ws, const Geom &g, MergePlanes *P) {
     P->rhat = c.take<float>(g.n * hw);
     P->s_tile = c.take<float>((size_t)g.n * g.ty * g.tx);
     P->geo = c.take<int4>((size_t)g.n * g.ty * g.tx);
+    P->hf_flag = c.take<unsigned char>(hw);
     return c.off;
 }
 
@@ -116,6 +117,7 @@ MergeConsts consts_of(const hmfsr_merge_params *p) {
     c.k_stretch = p->k_stretch; c.k_shrink = p->k_shrink; c.t = p->t; c.s1 = p->s1; c.s2 = p->s2;
     c.m_th = p->m_th; c.noise_a = p->noise_a; c.noise_b = p->noise_b;
     c.noise_table = nullptr;
+    c.hf_loss = 0.f;
     return c;
 }
 
@@ -228,6 +230,31 @@ hmfsr_status hmfsr_merge_noise(const uint16_t *burst_dev, const hmfsr_burst_desc
     cudaStream_t s = (cudaStream_t)stream;
     MergeConsts c = consts_of(params);
     c.noise_table = reinterpret_cast<const float4 *>(noise_table_dev);
+    cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
+    if (e != cudaSuccess) return HMFSR_ERR_CUDA;
+    return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
+}
+
+hmfsr_status hmfsr_merge_ex(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                            const hmfsr_merge_params *params, const hmfsr_merge_options *opts, int scale_num,
+                            int scale_den, float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!opts || (reinterpret_cast<uintptr_t>(opts->noise_table) & 15) || !isfinite(opts->hf_loss) || opts->hf_loss < 0.f)
+        return HMFSR_ERR_INVALID_ARG;
+    if (!burst_dev || !motion_dev || !rgb_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params) ||
+        !valid_scale(scale_num, scale_den))
+        return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, params->tile);
+    MergePlanes P;
+    size_t need = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_merge(ws, g, &P);
+    cudaStream_t s = (cudaStream_t)stream;
+    MergeConsts c = consts_of(params);
+    c.noise_table = reinterpret_cast<const float4 *>(opts->noise_table);
+    c.hf_loss = opts->hf_loss;
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));

@@ -65,6 +65,7 @@ struct MergePlanes {
     float *rhat;         // [n][hh*wh] final robustness (base grid); unused for the base frame
     float *s_tile;       // [n][ty*tx] robustness scale from the motion prior
     int4 *geo;           // [n][ty*tx] window geometry for the output scale {floor(Q v), Q v - floor(Q v)}
+    unsigned char *hf_flag;  // [hh*wh] high-frequency flag of the base texels (when that test is on)
 };
 
 // brightness levels of a Monte-Carlo noise table: level i is i WL / (kNoiseLevels - 1)
@@ -76,6 +77,8 @@ struct MergeConsts {
     // nullptr: the closed-form noise statistics; else kNoiseLevels entries
     // {sigma_md^2 red/blue, sigma_md^2 green, d_md^2 red/blue, d_md^2 green}
     const float4 *noise_table;
+    // 0: off; else the high-frequency rejection threshold kappa
+    float hf_loss;
 };
 
 // ---------------------------------------------------------------------------------------

@@ -27,10 +27,16 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
 // (blockIdx.z runs over the frames other than the base frame)
 __global__ void __launch_bounds__(128) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                              const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                             Geom g, float t_thr, float *__restrict__ rhat) {
+                                             Geom g, float t_thr, float *__restrict__ rhat,
+                                             const unsigned char *__restrict__ hf_flag, float m_th) {
     const int frame = (int)blockIdx.z < g.ref ? (int)blockIdx.z : (int)blockIdx.z + 1;
     stage::rob_strip(s1, base_stats, motion, s_tile, g, t_thr, rhat, (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut,
-                     blockIdx.y * stage::kRobStrip, frame, threadIdx.x & 31);
+                     blockIdx.y * stage::kRobStrip, frame, threadIdx.x & 31, hf_flag, m_th);
+}
+
+__global__ void k_hf_flag(const uint16_t *__restrict__ burst, const uint2 *__restrict__ s1, Geom g, float kappa,
+                          unsigned char *__restrict__ flag) {
+    stage::hf_flag_px(burst, s1, g, kappa, flag, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
 __global__ void k_geo(const float2 *__restrict__ motion, int n, int ntl, int ref, int Q, int4 *__restrict__ geo) {
@@ -89,9 +95,14 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
     int nt = g.n * g.ty * g.tx;
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
+    const unsigned char *hf = nullptr;
+    if (c.hf_loss > 0.f && g.n > 1) {
+        k_hf_flag<<<dim3(div_up(g.wh, 128), g.hh), 128, 0, s>>>(burst, P.s1, g, c.hf_loss, P.hf_flag);
+        hf = P.hf_flag;
+    }
     if (g.n > 1)
         k_rob<<<dim3(div_up(g.wh, 4 * stage::kRobOut), div_up(g.hh, stage::kRobStrip), g.n - 1), 128, 0, s>>>(
-            P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat);
+            P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, hf, c.m_th);
     return cudaGetLastError();
 }
 

@@ -730,12 +730,10 @@ __device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, c
 // --------------------------------------------------------------------------------------
 // motion prior (Eq. 7-8): robustness scale per tile, decided in exact FP64
 // --------------------------------------------------------------------------------------
-__device__ __forceinline__ void strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1,
-                                         float s2, float *__restrict__ s_tile, int i) {
-    if (i >= n * ty * tx) return;
-    int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
-    const float2 *mv = motion + (size_t)f * ty * tx;
-    // min / max are exact in FP32; the span, its length and the threshold are FP64
+// the motion span M of tile (x, y) and its 3x3 tile neighbourhood exceeds m_th (Eq. 7);
+// min / max are exact in FP32; the span, its length and the threshold are FP64
+__device__ __forceinline__ bool motion_span_exceeds(const float2 *__restrict__ mv, int ty, int tx, int y, int x,
+                                                    float m_th) {
     float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
     for (int j = -1; j <= 1; ++j)
         for (int k = -1; k <= 1; ++k) {
@@ -747,7 +745,58 @@ __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int 
         }
     double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
     double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
-    s_tile[i] = (M > (double)m_th) ? s1 : s2;
+    return M > (double)m_th;
+}
+
+__device__ __forceinline__ void strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1,
+                                         float s2, float *__restrict__ s_tile, int i) {
+    if (i >= n * ty * tx) return;
+    int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
+    s_tile[i] = motion_span_exceeds(motion + (size_t)f * ty * tx, ty, tx, y, x, m_th) ? s1 : s2;
+}
+
+// --------------------------------------------------------------------------------------
+// high-frequency artifact test (supplement, High Frequency Artifacts Removal) of base
+// texel (u, v): the 3x3 local means keep less than kappa of the local variance.  With
+// the green guide at half scale, 4 x the two variances times 81 and 6561 are the exact
+// integers B = sum_c w_c (9 S2 - S1^2) at the texel and A = sum_c w_c (9 sum_k S1_k^2 -
+// (sum_k S1_k)^2) over its 3x3 texels (clamped to the grid), w = (4, 1, 4); the test
+// A < kappa 81 B is taken in FP64 from exact integers, as a CPU restatement takes it.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void hf_flag_px(const uint16_t *__restrict__ burst, const uint2 *__restrict__ s1,
+                                           const Geom &g, float kappa, unsigned char *__restrict__ flag, int u, int v) {
+    if (u >= g.wh || v >= g.hh) return;
+    const uint16_t *fr = burst + (size_t)g.ref * g.h * g.pitch;
+    const uint2 *S = s1 + (size_t)g.ref * g.hh * g.wh;
+    long long sq[3] = {0, 0, 0};  // 3x3 sums of squared guide values at (u, v)
+    for (int j = -1; j <= 1; ++j)
+        for (int i = -1; i <= 1; ++i) {
+            const uint16_t *q = fr + (size_t)(2 * clampi(v + j, 0, g.hh - 1)) * g.pitch + 2 * clampi(u + i, 0, g.wh - 1);
+            const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(q));
+            const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(q + g.pitch));
+            const long long R = a & 0xffffu, G = (a >> 16) + (b & 0xffffu), B = b >> 16;
+            sq[0] += R * R; sq[1] += G * G; sq[2] += B * B;
+        }
+    long long t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+    for (int j = -1; j <= 1; ++j)
+        for (int i = -1; i <= 1; ++i) {
+            const uint2 m = __ldg(S + (size_t)clampi(v + j, 0, g.hh - 1) * g.wh + clampi(u + i, 0, g.wh - 1));
+            const long long k[3] = {(long long)(m.x & 0xffffu), (long long)m.y, (long long)(m.x >> 16)};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                t1[c] += k[c];
+                t2[c] += k[c] * k[c];
+                if (i == 0 && j == 0) c1[c] = k[c];
+            }
+        }
+    const long long wgt[3] = {4, 1, 4};
+    long long A = 0, B = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        B += wgt[c] * (9 * sq[c] - c1[c] * c1[c]);
+        A += wgt[c] * (9 * t2[c] - t1[c] * t1[c]);
+    }
+    flag[(size_t)v * g.wh + u] = (B > 0 && (double)A < __dmul_rn((double)kappa, __dmul_rn(81.0, (double)B))) ? 1 : 0;
 }
 
 // --------------------------------------------------------------------------------------
@@ -770,10 +819,13 @@ __device__ __forceinline__ float wiener_add(float d, float dmd2, float dd) {
     return fmaf(w, w, dd);
 }
 
+// hf_flag: nullptr, or the base texels' high-frequency flags, which reject (R = 0) where
+// the tile's motion span exceeds m_th
 __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
                                           const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
-                                          int frame, int lane) {
+                                          int frame, int lane, const unsigned char *__restrict__ hf_flag = nullptr,
+                                          float m_th = 0.f) {
     const size_t hw = (size_t)g.hh * g.wh;
     const int wh = g.wh, u = u0 - 2 + lane;
     const bool col_ok = u >= 0 && u < wh;
@@ -789,6 +841,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
     const int vfirst = max(v0 - 2, 0);
     int tq = vfirst / ht, tr = vfirst - tq * ht;
     int cur_tile = -1, fly = 0, x0 = 0, x1 = 0;
+    bool span = false;  // the tile's motion span exceeds m_th (high-frequency rejection only)
     float b00 = 0.f, b10 = 0.f, b01 = 0.f, b11 = 0.f, sc = 0.f;
     uint2 nt0 = make_uint2(0u, 0u), nt1 = nt0, nb0 = nt0, nb1 = nt0;  // sums at the top / bottom neighbours
     bool have_prev = false;
@@ -812,6 +865,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
                 x0 = clampi(uc + (int)flx, 0, wh - 1);
                 x1 = clampi(uc + (int)flx + 1, 0, wh - 1);
                 have_prev = false;
+                if (hf_flag) span = motion_span_exceeds(motion + (size_t)frame * g.ty * g.tx, g.ty, g.tx, tyi, txi, m_th);
             }
             if (++tr == ht) { tr = 0; ++tq; }
             const int iy = v + fly;
@@ -827,7 +881,9 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
             nb0 = S1n[o1 + x0];
             nb1 = S1n[o1 + x1];
             have_prev = true;
-            if (col_ok) {
+            if (col_ok && span && hf_flag[off]) {
+                R = 0.f;  // high-frequency content with a large local motion span: rejected
+            } else if (col_ok) {
                 const uint2 sb = S1b[off];
                 const float4 st = base_stats[off];
                 // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9, from exact

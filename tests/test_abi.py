@@ -186,3 +186,17 @@ def test_noise_table_entry_points_reject_bad_arguments(L):
 
     assert call(None) == -1
     assert call(ctypes.c_void_p(264)) == -1
+
+
+def test_merge_ex_rejects_bad_options(L):
+    d, p = desc(), hm.MergeParams().c()
+
+    def call(opts):
+        return L.hmfsr_merge_ex(ctypes.c_void_p(16), ctypes.byref(d), ctypes.c_void_p(16), ctypes.byref(p),
+                                ctypes.byref(opts) if opts is not None else None, 1, 1, ctypes.c_void_p(16), None,
+                                ctypes.c_void_p(256), 1 << 40, None)
+
+    assert call(None) == -1
+    assert call(_lib.MergeOptionsC(264, 0.0)) == -1          # misaligned table
+    assert call(_lib.MergeOptionsC(None, -0.1)) == -1
+    assert call(_lib.MergeOptionsC(None, float("nan"))) == -1

@@ -319,3 +319,29 @@ def test_align_quadfit_bit_exact(dev, tiny_burst):
         mi, mf = oracle.align_quadfit(raw.numpy(), ref=ref, tile=tile)
         assert np.array_equal(g_int.cpu().numpy(), mi)
         assert np.array_equal(g_motion.cpu().numpy(), mf)
+
+
+# --------------------------------------------------------------------------------------
+# high-frequency artifact rejection (supplement, High Frequency Artifacts Removal)
+# --------------------------------------------------------------------------------------
+def test_merge_with_high_frequency_rejection(dev):
+    # four noisy frames of a scene half Nyquist pattern, half ramp, under a motion field
+    # whose tiles alternate by 1 px (every tile's motion span exceeds m_th)
+    rng = np.random.default_rng(1905_03277 + 57)
+    h, w, n = 96, 128, 4
+    y, x = np.mgrid[0:h, 0:w]
+    scene = np.where(x < w // 2, 2000 + 1500 * np.where(((x // 2) + (y // 2)) % 2 == 0, 1, -1), 500 + 20 * x + 10 * y)
+    raw = np.clip(scene[None] + rng.normal(0, 8, size=(n, h, w)), 0, 4095).astype(np.uint16)
+    ty, tx = h // 16, w // 16
+    motion = np.zeros((n, ty, tx, 2), np.float32)
+    motion[1:, ..., 0] = np.where((np.add.outer(np.arange(ty), np.arange(tx)) % 2) == 0, 0.5, -0.5)
+    p = hm.MergeParams(noise_a=1.0, noise_b=64.0)
+    rt, mv = torch.from_numpy(raw).to(dev), torch.from_numpy(motion).to(dev)
+    assert oracle.hf_loss_map(raw[0], 0.03).any()
+    for scale in [(1, 1), (2, 1)]:
+        got = hm.merge_ex(rt, mv, p, scale, hf_loss=0.03).cpu().numpy()
+        want = oracle.merge(raw, motion, oparams(p), scale=scale, hf_loss=0.03)
+        assert_merge_close(got, want, f"high-frequency rejection, scale {scale}")
+        off = hm.merge_ex(rt, mv, p, scale).cpu().numpy()
+        assert np.array_equal(off, hm.merge(rt, mv, p, scale).cpu().numpy())   # no options: hmfsr_merge
+        assert not np.array_equal(off, got)
