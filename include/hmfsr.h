@@ -210,8 +210,8 @@ hmfsr_status hmfsr_batch_configure(hmfsr_batch_plan plan, int merge_tile_w, int 
 hmfsr_status hmfsr_batch_set_mode(hmfsr_batch_plan plan, int streams);
 
 /* Autotuner: times the batch on the given buffers for 8 candidates -- the persistent
- * kernel with accumulation tiles 32x4 / 16x8, register budgets 64 / 80 and stage-major or
- * wavefront queues, and the per-burst graph on 1, 2, 4 and 8 branches -- keeps the
+ * kernel with accumulation tiles 32x4 / 16x8 and register budgets 64 / 80 / 128 (the
+ * stage-major queue), and the per-burst graph on 1, 2, 4 and 8 branches -- keeps the
  * fastest in the plan and returns its time (ms) in *best_ms and every candidate's time
  * in tune_log[8] (both nullable).  Overwrites the outputs. */
 hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *bursts_dev, float *const *motion_dev,

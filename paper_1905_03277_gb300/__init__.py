@@ -548,7 +548,7 @@ class BatchPlan:
                                                  spin_limit, int(inject_stall)), "hmfsr_batch_configure")
 
     TUNE_CANDIDATES = ("persistent 32x4 64reg", "persistent 16x8 64reg", "persistent 32x4 80reg",
-                       "persistent 32x4 64reg wavefront", "graph 1 branch", "graph 2 branches", "graph 4 branches",
+                       "persistent 32x4 128reg", "graph 1 branch", "graph 2 branches", "graph 4 branches",
                        "graph 8 branches")
 
     def set_mode(self, streams: int):

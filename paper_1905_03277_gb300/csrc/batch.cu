@@ -660,7 +660,7 @@ hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *burs
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HMFSR_ERR_CUDA;
     // candidates: {mode, merge tile width, register variant, queue order}
-    static const int kCand[][4] = {{0, 32, 2, 0}, {0, 16, 2, 0}, {0, 32, 1, 0}, {0, 32, 2, 2},
+    static const int kCand[][4] = {{0, 32, 2, 0}, {0, 16, 2, 0}, {0, 32, 1, 0}, {0, 32, 0, 0},
                                    {1, 32, 2, 0}, {2, 32, 2, 0}, {4, 32, 2, 0}, {8, 32, 2, 0}};
     float best = 1e30f;
     int best_i = 0;

@@ -25,13 +25,16 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
 
 // 4 warps side by side: 4 x kRobOut texel columns x kRobStrip rows of one frame
 // (blockIdx.z runs over the frames other than the base frame)
+// kHF: with the high-frequency rejection (hf_flag, m_th)
+template <bool kHF>
 __global__ void __launch_bounds__(128) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                              const float2 *__restrict__ motion, const float *__restrict__ s_tile,
                                              Geom g, float t_thr, float *__restrict__ rhat,
                                              const unsigned char *__restrict__ hf_flag, float m_th) {
     const int frame = (int)blockIdx.z < g.ref ? (int)blockIdx.z : (int)blockIdx.z + 1;
-    stage::rob_strip(s1, base_stats, motion, s_tile, g, t_thr, rhat, (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut,
-                     blockIdx.y * stage::kRobStrip, frame, threadIdx.x & 31, hf_flag, m_th);
+    stage::rob_strip<kHF>(s1, base_stats, motion, s_tile, g, t_thr, rhat,
+                          (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut, blockIdx.y * stage::kRobStrip, frame,
+                          threadIdx.x & 31, hf_flag, m_th);
 }
 
 __global__ void k_hf_flag(const uint16_t *__restrict__ burst, const uint2 *__restrict__ s1, Geom g, float kappa,
@@ -100,9 +103,13 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
         k_hf_flag<<<dim3(div_up(g.wh, 128), g.hh), 128, 0, s>>>(burst, P.s1, g, c.hf_loss, P.hf_flag);
         hf = P.hf_flag;
     }
-    if (g.n > 1)
-        k_rob<<<dim3(div_up(g.wh, 4 * stage::kRobOut), div_up(g.hh, stage::kRobStrip), g.n - 1), 128, 0, s>>>(
-            P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, hf, c.m_th);
+    if (g.n > 1) {
+        const dim3 grid(div_up(g.wh, 4 * stage::kRobOut), div_up(g.hh, stage::kRobStrip), g.n - 1);
+        if (hf)
+            k_rob<true><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, hf, c.m_th);
+        else
+            k_rob<false><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, nullptr, c.m_th);
+    }
     return cudaGetLastError();
 }
 

@@ -819,8 +819,9 @@ __device__ __forceinline__ float wiener_add(float d, float dmd2, float dd) {
     return fmaf(w, w, dd);
 }
 
-// hf_flag: nullptr, or the base texels' high-frequency flags, which reject (R = 0) where
-// the tile's motion span exceeds m_th
+// kHF: hf_flag holds the base texels' high-frequency flags, which reject (R = 0) where
+// the tile's motion span exceeds m_th (otherwise both are unused)
+template <bool kHF = false>
 __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
                                           const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
@@ -865,7 +866,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
                 x0 = clampi(uc + (int)flx, 0, wh - 1);
                 x1 = clampi(uc + (int)flx + 1, 0, wh - 1);
                 have_prev = false;
-                if (hf_flag) span = motion_span_exceeds(motion + (size_t)frame * g.ty * g.tx, g.ty, g.tx, tyi, txi, m_th);
+                if (kHF) span = motion_span_exceeds(motion + (size_t)frame * g.ty * g.tx, g.ty, g.tx, tyi, txi, m_th);
             }
             if (++tr == ht) { tr = 0; ++tq; }
             const int iy = v + fly;
@@ -881,7 +882,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
             nb0 = S1n[o1 + x0];
             nb1 = S1n[o1 + x1];
             have_prev = true;
-            if (col_ok && span && hf_flag[off]) {
+            if (kHF && col_ok && span && hf_flag[off]) {
                 R = 0.f;  // high-frequency content with a large local motion span: rejected
             } else if (col_ok) {
                 const uint2 sb = S1b[off];
