@@ -16,6 +16,26 @@ namespace {
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
 constexpr int kBwdW = 32, kBwdH = 4, kBwdThreads = kBwdW * kBwdH;
 
+// Block sums in a fixed order without FP64 arithmetic per element (FP64 is scarce on this
+// GPU): each warp adds its lanes' values by butterflies carrying the exact rounding error
+// of every FP32 addition (two-sum), lane 0 stores the warp's (sum, error) pair; the
+// caller's thread 0 then adds the warps' pairs in FP64 in warp order.
+template <int K>
+__device__ __forceinline__ void warp_sums_comp(float (&v)[K], float (&e)[K]) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) e[q] = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float a = v[q], b = __shfl_xor_sync(0xffffffffu, v[q], o);
+            const float t = a + b, bp = t - a;
+            const float err = (a - (t - bp)) + (b - bp);
+            e[q] = (e[q] + __shfl_xor_sync(0xffffffffu, e[q], o)) + err;
+            v[q] = t;
+        }
+}
+
 // ---------------------------------------------------------------------------------------
 // per texel: what the kernel-shape derivative needs {A, sqrt(l1_norm), cos 2t, sin 2t}
 // ---------------------------------------------------------------------------------------
@@ -317,18 +337,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_merge_bwd(
             rhbar_pix[of] = (f == g.ref) ? 0.f : rhb;
         }
     }
-    // block sums of the six kernel-parameter gradients, in FP64 and a fixed order
+    // block sums of the six kernel-parameter gradients, in a fixed order
     const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll 1
-    for (int q = 0; q < 6; ++q) {
-        s_red[tid] = (double)pb[q];
-        __syncthreads();
-        for (int sstep = kBwdThreads / 2; sstep > 0; sstep >>= 1) {
-            if (tid < sstep) s_red[tid] += s_red[tid + sstep];
-            __syncthreads();
+    float pe[6];
+    warp_sums_comp<6>(pb, pe);
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            s_red[(tid >> 5) * 12 + 2 * q] = (double)pb[q];
+            s_red[(tid >> 5) * 12 + 2 * q + 1] = (double)pe[q];
         }
-        if (tid == 0) partials[(size_t)bid * 6 + q] = s_red[0];
-        __syncthreads();
+    __syncthreads();
+    if (tid < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < kBwdThreads / 32; ++w) acc += s_red[w * 12 + 2 * tid] + s_red[w * 12 + 2 * tid + 1];
+        partials[(size_t)bid * 6 + tid] = acc;
     }
 }
 
@@ -355,6 +378,20 @@ __global__ void k_rhat_gather(const float *__restrict__ rhbar_pix, Geom g, int s
     xrange(u, g.wh, wo, xlo, xhi);
     xrange(v, g.hh, ho, ylo, yhi);
     const size_t po = (size_t)ho * wo;
+    // the columns' weights once (the same for every row); a clamped border texel can
+    // collect more columns than fit, which then take the per-row path
+    constexpr int kMaxCols = 16;
+    float wxs[kMaxCols];
+    const bool cached = xhi - xlo < kMaxCols;
+    auto col_weight = [&](int X) -> float {
+        const int Px = 2 * sden * X + sden - snum;
+        const int rx = floor_div(Px - snum, Q2);
+        const float fx = (float)(Px - snum - rx * Q2) * inv2Q;
+        const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
+        return (rx0 == u ? 1.f - fx : 0.f) + (rx1 == u ? fx : 0.f);
+    };
+    if (cached)
+        for (int X = xlo; X <= xhi; ++X) wxs[X - xlo] = col_weight(X);
     float acc = 0.f;
     for (int Y = ylo; Y <= yhi; ++Y) {
         const int Py = 2 * sden * Y + sden - snum;
@@ -363,14 +400,11 @@ __global__ void k_rhat_gather(const float *__restrict__ rhbar_pix, Geom g, int s
         const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
         const float wy = (ry0 == v ? 1.f - fy : 0.f) + (ry1 == v ? fy : 0.f);
         if (wy == 0.f) continue;
+        const float *row = rhbar_pix + (size_t)f * po + (size_t)Y * wo;
         for (int X = xlo; X <= xhi; ++X) {
-            const int Px = 2 * sden * X + sden - snum;
-            const int rx = floor_div(Px - snum, Q2);
-            const float fx = (float)(Px - snum - rx * Q2) * inv2Q;
-            const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
-            const float wx = (rx0 == u ? 1.f - fx : 0.f) + (rx1 == u ? fx : 0.f);
+            const float wx = cached ? wxs[X - xlo] : col_weight(X);
             if (wx == 0.f) continue;
-            acc += wx * wy * rhbar_pix[(size_t)f * po + (size_t)Y * wo + X];
+            acc += wx * wy * row[X];
         }
     }
     rhbar_tex[(size_t)f * g.hh * g.wh + (size_t)v * g.wh + u] = acc;
@@ -408,20 +442,20 @@ __global__ void __launch_bounds__(kRpThreads) k_rpath(const float *__restrict__ 
         }
     }
     const int tid = threadIdx.x;
-    s_red[0][tid] = (double)ps;
-    s_red[1][tid] = (double)pt;
-    __syncthreads();
-    for (int sstep = kRpThreads / 2; sstep > 0; sstep >>= 1) {
-        if (tid < sstep) {
-            s_red[0][tid] += s_red[0][tid + sstep];
-            s_red[1][tid] += s_red[1][tid + sstep];
-        }
-        __syncthreads();
+    float pv[2] = {ps, pt}, pe[2];
+    warp_sums_comp<2>(pv, pe);
+    if ((tid & 31) == 0) {
+        s_red[0][(tid >> 5) * 2] = (double)pv[0];
+        s_red[0][(tid >> 5) * 2 + 1] = (double)pe[0];
+        s_red[1][(tid >> 5) * 2] = (double)pv[1];
+        s_red[1][(tid >> 5) * 2 + 1] = (double)pe[1];
     }
-    if (tid == 0) {
+    __syncthreads();
+    if (tid < 2) {
+        double acc = 0.0;
+        for (int w = 0; w < kRpThreads / 32; ++w) acc += s_red[tid][2 * w] + s_red[tid][2 * w + 1];
         const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[bid * 2] = s_red[0][0];
-        partials[bid * 2 + 1] = s_red[1][0];
+        partials[bid * 2 + tid] = acc;
     }
 }
 
@@ -437,48 +471,56 @@ __device__ __forceinline__ int tile_first(int k, int ntiles, int nout, int snum,
 
 constexpr int kRedThreads = 128;
 
-// one block per (frame, tile): output-pixel and texel contributions of that tile
+// Neumaier's compensated sum in FP32: s + c carries the exact error of every addition
+__device__ __forceinline__ void comp_add(float &s, float &c, float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+// one warp per (frame, tile): the output-pixel and texel contributions of that tile, each
+// lane over every 32nd element in a fixed order (compensated FP32: FP64 arithmetic is
+// scarce on this GPU), then the lanes in FP64 by a fixed butterfly -- deterministic
 __global__ void __launch_bounds__(kRedThreads) k_motion_reduce(const float2 *__restrict__ vbar_pix,
                                                                const float2 *__restrict__ vbar_tex, Geom g, int snum,
                                                                int sden, int ho, int wo, float *__restrict__ grad_motion) {
-    __shared__ double s_red[2][kRedThreads];
-    const int txi = blockIdx.x, tyi = blockIdx.y, f = blockIdx.z, tid = threadIdx.x;
-    double sx = 0.0, sy = 0.0;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (kRedThreads / 32) + (threadIdx.x >> 5);  // (frame, tile) index
+    if (t >= g.n * g.ty * g.tx) return;  // the whole warp
+    const int f = t / (g.ty * g.tx), r = t - f * g.ty * g.tx, tyi = r / g.tx, txi = r - tyi * g.tx;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     if (f != g.ref) {
         const int X0 = tile_first(txi, g.tx, wo, snum, sden, g.tile), X1 = tile_first(txi + 1, g.tx, wo, snum, sden, g.tile);
         const int Y0 = tile_first(tyi, g.ty, ho, snum, sden, g.tile), Y1 = tile_first(tyi + 1, g.ty, ho, snum, sden, g.tile);
-        const int tw = X1 - X0, npix = tw * (Y1 - Y0);
         const size_t po = (size_t)ho * wo;
-        for (int k = tid; k < npix; k += kRedThreads) {
-            const float2 vb = vbar_pix[(size_t)f * po + (size_t)(Y0 + k / tw) * wo + X0 + k % tw];
-            sx += vb.x;
-            sy += vb.y;
-        }
+        const float2 *vp = vbar_pix + (size_t)f * po;
+        for (int Y = Y0; Y < Y1; ++Y)
+            for (int X = X0 + lane; X < X1; X += 32) {
+                const float2 vb = vp[(size_t)Y * wo + X];
+                comp_add(sx, cx, vb.x);
+                comp_add(sy, cy, vb.y);
+            }
         const int ht = g.tile / 2;
         const int u0 = txi * ht, v0 = tyi * ht;
         const int u1 = (txi == g.tx - 1) ? g.wh : min(u0 + ht, g.wh), v1 = (tyi == g.ty - 1) ? g.hh : min(v0 + ht, g.hh);
-        const int twt = u1 - u0, nt = twt * (v1 - v0);
-        const size_t hw = (size_t)g.hh * g.wh;
-        for (int k = tid; k < nt; k += kRedThreads) {
-            const float2 vb = vbar_tex[(size_t)f * hw + (size_t)(v0 + k / twt) * g.wh + u0 + k % twt];
-            sx += vb.x;
-            sy += vb.y;
-        }
+        const float2 *vt = vbar_tex + (size_t)f * g.hh * g.wh;
+        for (int v = v0; v < v1; ++v)
+            for (int u = u0 + lane; u < u1; u += 32) {
+                const float2 vb = vt[(size_t)v * g.wh + u];
+                comp_add(sx, cx, vb.x);
+                comp_add(sy, cy, vb.y);
+            }
     }
-    s_red[0][tid] = sx;
-    s_red[1][tid] = sy;
-    __syncthreads();
-    for (int sstep = kRedThreads / 2; sstep > 0; sstep >>= 1) {
-        if (tid < sstep) {
-            s_red[0][tid] += s_red[0][tid + sstep];
-            s_red[1][tid] += s_red[1][tid + sstep];
-        }
-        __syncthreads();
+    double dx = (double)sx + (double)cx, dy = (double)sy + (double)cy;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dx += __shfl_xor_sync(0xffffffffu, dx, o);
+        dy += __shfl_xor_sync(0xffffffffu, dy, o);
     }
-    if (tid == 0) {
+    if (lane == 0) {
         const size_t o = (((size_t)f * g.ty + tyi) * g.tx + txi) * 2;
-        grad_motion[o] = (float)s_red[0][0];
-        grad_motion[o + 1] = (float)s_red[1][0];
+        grad_motion[o] = (float)dx;
+        grad_motion[o + 1] = (float)dy;
     }
 }
 
@@ -545,8 +587,8 @@ cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, co
     k_rhat_gather<<<tex_grid, 128, 0, s>>>(B.rhbar_pix, g, snum, sden, ho, wo, B.rhbar_tex);
     k_rpath<<<dim3(div_up(g.wh, kRpThreads), g.hh, g.n), kRpThreads, 0, s>>>(B.rhbar_tex, B.flags, B.rb, g,
                                                                            B.vbar_tex, B.part2);
-    k_motion_reduce<<<dim3(g.tx, g.ty, g.n), kRedThreads, 0, s>>>(B.vbar_pix, B.vbar_tex, g, snum, sden, ho, wo,
-                                                                  grad_motion);
+    k_motion_reduce<<<div_up(g.n * g.ty * g.tx, kRedThreads / 32), kRedThreads, 0, s>>>(B.vbar_pix, B.vbar_tex, g, snum,
+                                                                                      sden, ho, wo, grad_motion);
     k_param_reduce<<<8, kRedThreads, 0, s>>>(B.part6, B.n_bwd_blocks, B.part2, B.n_rp_blocks, grad_params);
     return cudaGetLastError();
 }
