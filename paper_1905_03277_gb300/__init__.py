@@ -453,11 +453,13 @@ def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParam
 class MergeFn(torch.autograd.Function):
     """rgb = merge(burst, motion, params) as a differentiable function of the eight tuning
     parameters (a float tensor in PARAM_NAMES order) and of the motion field; gradients
-    come from the hand-written adjoint (hmfsr_merge_backward)."""
+    come from the hand-written adjoint (hmfsr_merge_backward).  `values`, when given, are
+    theta's values already on the host (the launch takes the parameters by value), which
+    spares a device-to-host read per call."""
 
     @staticmethod
-    def forward(ctx, theta, motion, burst, base: MergeParams, scale=(1, 1), ref: int = 0):
-        vals = [float(x) for x in theta.detach().cpu().tolist()]
+    def forward(ctx, theta, motion, burst, base: MergeParams, scale=(1, 1), ref: int = 0, values=None):
+        vals = [float(x) for x in (values if values is not None else theta.detach().cpu().tolist())]
         p = MergeParams(**{**base.__dict__, **dict(zip(PARAM_NAMES, vals))})
         motion_c = motion.detach().contiguous()
         rgb, den = merge(burst, motion_c, p, scale, ref, with_den=True)
@@ -470,7 +472,7 @@ class MergeFn(torch.autograd.Function):
     def backward(ctx, grad_rgb):
         motion_c, rgb, den = ctx.saved_tensors
         gp, gm = merge_backward(ctx.burst, motion_c, ctx.p, rgb, den, grad_rgb, ctx.scale, ctx.ref)
-        return gp.to(ctx.theta_device), gm, None, None, None, None
+        return gp.to(ctx.theta_device), gm, None, None, None, None, None
 
 
 class BatchPlan:

@@ -34,14 +34,17 @@ def fit(bursts, gts, base: MergeParams | None = None, steps: int = 200, lr: floa
     history = []
     for step in range(steps):
         opt.zero_grad()
-        total = 0.0
+        # One host read of the parameters and one of the loss per step: the bursts' forward
+        # and adjoint launches queue back to back without a synchronisation between them.
+        theta = torch.exp(phi).float()
+        vals = theta.detach().cpu().tolist()
+        total = torch.zeros((), dtype=torch.float64, device=dev)
         for b, g, m in zip(bursts, gts, motions):
-            theta = torch.exp(phi).float()
-            rgb = MergeFn.apply(theta, m, b, base, scale, 0)
+            rgb = MergeFn.apply(theta, m, b, base, scale, 0, vals)
             loss = ((rgb - g) ** 2).mean() / len(bursts)
-            loss.backward()
-            total += float(loss.detach())
-        history.append(total)
+            loss.backward(retain_graph=True)
+            total += loss.detach()
+        history.append(float(total))
         opt.step()
         if log_every and step % log_every == 0:
             print(f"step {step}: loss {total:.4f}")
