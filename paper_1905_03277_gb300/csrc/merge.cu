@@ -2,6 +2,8 @@
 // (Eq. 5-9) and the kernel-regression accumulation (Eq. 1-2) with a fused
 // normalisation -- the per-burst kernels.  Their bodies (and the numerical design notes)
 // live in stages.cuh, shared with the batched persistent kernel.
+#include <atomic>
+
 #include "accumulate.cuh"
 
 namespace hmfsr {
@@ -10,12 +12,12 @@ namespace {
 using stage::kMergeW;
 using stage::kMergeH;
 
-// 4 warps side by side: 128 texel columns x kPrepStrip rows of one frame
+// 4 warps side by side: 128 texel columns x `rows` rows of one frame
 __global__ void __launch_bounds__(128) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
                                               uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                              float4 *__restrict__ kern) {
+                                              float4 *__restrict__ kern, int rows) {
     stage::prep_strip(burst, g, c, s1, base_stats, kern, blockIdx.x * 128 + (threadIdx.x & ~31),
-                      blockIdx.y * stage::kPrepStrip, blockIdx.z, threadIdx.x & 31);
+                      blockIdx.y * rows, blockIdx.z, threadIdx.x & 31, rows);
 }
 
 __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1, float s2,
@@ -23,18 +25,18 @@ __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int
     stage::strength(motion, n, ty, tx, m_th, s1, s2, s_tile, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// 4 warps side by side: 4 x kRobOut texel columns x kRobStrip rows of one frame
+// 4 warps side by side: 4 x kRobOut texel columns x `rows` rows of one frame
 // (blockIdx.z runs over the frames other than the base frame)
 // kHF: with the high-frequency rejection (hf_flag, m_th)
 template <bool kHF>
 __global__ void __launch_bounds__(128) k_rob(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
                                              const float2 *__restrict__ motion, const float *__restrict__ s_tile,
                                              Geom g, float t_thr, float *__restrict__ rhat,
-                                             const unsigned char *__restrict__ hf_flag, float m_th) {
+                                             const unsigned char *__restrict__ hf_flag, float m_th, int rows) {
     const int frame = (int)blockIdx.z < g.ref ? (int)blockIdx.z : (int)blockIdx.z + 1;
     stage::rob_strip<kHF>(s1, base_stats, motion, s_tile, g, t_thr, rhat,
-                          (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut, blockIdx.y * stage::kRobStrip, frame,
-                          threadIdx.x & 31, hf_flag, m_th);
+                          (blockIdx.x * 4 + (threadIdx.x >> 5)) * stage::kRobOut, blockIdx.y * rows, frame,
+                          threadIdx.x & 31, hf_flag, m_th, rows);
 }
 
 __global__ void k_hf_flag(const uint16_t *__restrict__ burst, const uint2 *__restrict__ s1, Geom g, float kappa,
@@ -89,12 +91,58 @@ __global__ void k_export(const float4 *__restrict__ kern, const float *__restric
     if (rhat_out) rhat_out[(size_t)f * hw + i] = (f == ref) ? 1.f : rhat[(size_t)f * hw + i];
 }
 
+// --------------------------------------------------------------------------------------
+// strip heights.  A strip kernel's blocks run in waves of (resident blocks per SM) x
+// (SMs); a last wave that is only partly filled costs as long as a full one.  Of the
+// even heights in [lo, hi], take the one with the least waves x (rows + halo): the rows
+// every block walks, halo included.  The occupancy of each kernel is queried once per
+// device; if a query fails, the default height stands.
+// --------------------------------------------------------------------------------------
+enum StripKernel { SK_PREP = 0, SK_ROB = 1, SK_ROB_HF = 2, SK_COUNT = 3 };
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_strip_slots[SK_COUNT][kMaxDevices];  // resident blocks on the device, 0: not yet known
+
+int strip_slots(StripKernel k, const void *kernel) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    int slots = g_strip_slots[k][dev].load(std::memory_order_relaxed);
+    if (slots > 0) return slots;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    slots = sms * per_sm;
+    g_strip_slots[k][dev].store(slots, std::memory_order_relaxed);
+    return slots;
+}
+
+// blocks_per_rows: blocks side by side (columns x frames) per strip of rows
+int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, int hi, int fallback) {
+    if (slots <= 0 || blocks_per_rows <= 0 || hh <= 0) return fallback;
+    int best = fallback;
+    long long best_cost = -1;
+    for (int rows = lo; rows <= hi; rows += 2) {
+        const long long blocks = blocks_per_rows * div_up(hh, rows);
+        const long long cost = ((blocks + slots - 1) / slots) * (rows + halo);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = rows; }
+        if (rows >= hh) break;  // one strip covers the frame: longer strips only add rows
+    }
+    return best;
+}
+
 }  // namespace
 
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
-    k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, stage::kPrepStrip), g.n), 128, 0, s>>>(burst, g, c, P.s1,
-                                                                                      P.base_stats, P.kern);
+    const int prep_rows = strip_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
+                                     g.hh, 2, 16, 256, stage::kPrepStrip);
+    k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
+                                                                                   P.kern, prep_rows);
     int nt = g.n * g.ty * g.tx;
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
@@ -104,11 +152,15 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
         hf = P.hf_flag;
     }
     if (g.n > 1) {
-        const dim3 grid(div_up(g.wh, 4 * stage::kRobOut), div_up(g.hh, stage::kRobStrip), g.n - 1);
+        const int slots = hf ? strip_slots(SK_ROB_HF, (const void *)k_rob<true>)
+                             : strip_slots(SK_ROB, (const void *)k_rob<false>);
+        const int cols = div_up(g.wh, 4 * stage::kRobOut);
+        const int rows = strip_rows(slots, (long long)cols * (g.n - 1), g.hh, 4, 8, 256, stage::kRobStrip);
+        const dim3 grid(cols, div_up(g.hh, rows), g.n - 1);
         if (hf)
-            k_rob<true><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, hf, c.m_th);
+            k_rob<true><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, hf, c.m_th, rows);
         else
-            k_rob<false><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, nullptr, c.m_th);
+            k_rob<false><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, nullptr, c.m_th, rows);
     }
     return cudaGetLastError();
 }

@@ -597,7 +597,7 @@ __device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, lon
 
 // --------------------------------------------------------------------------------------
 // merge preparation of one strip of half-res texels of one frame (Sec. 5.1.2, Sec. 5.2.2,
-// Eq. 3-4, supplement S.1): one warp, 32 consecutive texel columns, kPrepStrip rows.
+// Eq. 3-4, supplement S.1): one warp, 32 consecutive texel columns, a strip of rows.
 // Each lane builds the guide quad {R, G1+G2, B, Lq} of its column from the raw samples
 // row by row (the guide image never goes to memory); the left and right neighbours come
 // from the adjacent lanes (lanes 0 and 31 read the strip's halo quads), rows and
@@ -607,7 +607,7 @@ __device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, lon
 // 2x2 sub-squares) -> kernel covariance.  Raw rows are fetched two rows ahead.  The R
 // and B sums travel packed in one word: 9 x 7281 < 2^16, so the halves never carry.
 // --------------------------------------------------------------------------------------
-constexpr int kPrepStrip = 32;
+constexpr int kPrepStrip = 32;  // default strip height; per-burst launches choose theirs (strip_rows)
 
 struct PrepRow {
     uint32_t a, b;    // the lane's quad: {R, G1} and {G2, B}
@@ -635,7 +635,7 @@ __device__ __forceinline__ PrepRow prep_fetch(const uint16_t *__restrict__ fr, i
     return p;
 }
 
-// one raw row pair of the strip (strip row r = -1 .. kPrepStrip); emits texel row r - 1
+// one raw row pair of the strip (strip row r = -1 .. rows); emits texel row r - 1
 __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r, int lane, bool is_ref, bool out_col,
                                          int v0, const Geom &g, const MergeConsts &c, float inv_dtr, int u,
                                          uint2 *__restrict__ s1f, float4 *__restrict__ base_stats,
@@ -695,11 +695,12 @@ __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r,
     st.pa = pa; st.pb = pb; st.pc = pc;
 }
 
-// strip (u0 .. u0 + 31) x (v0 .. v0 + kPrepStrip - 1) of frame f; every lane of the warp
-// calls this (the strip's shuffles need them all)
+// strip (u0 .. u0 + 31) x (v0 .. v0 + rows - 1) of frame f (rows even); every lane of the
+// warp calls this (the strip's shuffles need them all)
 __device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, const Geom &g, const MergeConsts &c,
                                            uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                           float4 *__restrict__ kern, int u0, int v0, int f, int lane) {
+                                           float4 *__restrict__ kern, int u0, int v0, int f, int lane,
+                                           int rows = kPrepStrip) {
     const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
     const int u = u0 + lane, uc = min(u, g.wh - 1);
     const bool halo = (lane == 0 || lane == 31);
@@ -717,7 +718,7 @@ __device__ __forceinline__ void prep_strip(const uint16_t *__restrict__ burst, c
     st.pa = st.pb = st.pc = 0;
     PrepRow p0 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 - 1);
     PrepRow p1 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0);
-    for (int r = -1; r <= kPrepStrip; r += 2) {
+    for (int r = -1; r <= rows; r += 2) {
         const PrepRow cur0 = p0;
         p0 = prep_fetch(fr, g.pitch, g.hh, uc, uh, halo, v0 + r + 2);
         prep_row(cur0, st, r, lane, is_ref, out_col, v0, g, c, inv_dtr, u, s1f, base_stats, kernf);
@@ -801,14 +802,14 @@ __device__ __forceinline__ void hf_flag_px(const uint16_t *__restrict__ burst, c
 
 // --------------------------------------------------------------------------------------
 // robustness (Eq. 5, 6) and its 5x5 minimum (Eq. 9) on one strip of base texels of one
-// frame: one warp, kRobOut columns, kRobStrip rows.  Lane l evaluates R at column
-// u0 - 2 + l for the rows v0 - 2 .. v0 + kRobStrip + 1, walking down: within a motion
+// frame: one warp, kRobOut columns, `rows` rows.  Lane l evaluates R at column
+// u0 - 2 + l for the rows v0 - 2 .. v0 + rows + 1, walking down: within a motion
 // tile the bilinear neighbours of the row below are the bottom neighbours of this row,
 // so each row reads two new sums instead of four.  The 5-wide row minimum comes from
 // the next four lanes (lanes 0 .. kRobOut - 1 write); a rolling window of five row
 // minima gives the column minimum.  Every lane of the warp calls this.
 // --------------------------------------------------------------------------------------
-constexpr int kRobOut = 28, kRobStrip = 64;
+constexpr int kRobOut = 28, kRobStrip = 64;  // kRobStrip: default strip height, as for kPrepStrip
 constexpr float kLog2e = 1.44269504088896340736f;
 
 // Wiener-shrunk squared difference of one channel (Eq. 6): (d d^2 / (d^2 + dmd^2))^2 added
@@ -826,7 +827,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
                                           const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
                                           int frame, int lane, const unsigned char *__restrict__ hf_flag = nullptr,
-                                          float m_th = 0.f) {
+                                          float m_th = 0.f, int rows = kRobStrip) {
     const size_t hw = (size_t)g.hh * g.wh;
     const int wh = g.wh, u = u0 - 2 + lane;
     const bool col_ok = u >= 0 && u < wh;
@@ -848,7 +849,7 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
     bool have_prev = false;
     float h0 = kBig, h1 = kBig, h2 = kBig, h3 = kBig;  // row minima of the four rows above
     int off = (v0 - 2) * wh + uc;                        // this lane's texel in the row (32-bit offsets)
-    for (int e = 0; e < kRobStrip + 4; ++e, off += wh) {
+    for (int e = 0; e < rows + 4; ++e, off += wh) {
         const int v = v0 - 2 + e;
         float R = kBig;
         if (v >= 0 && v < g.hh) {  // the same for the whole warp
