@@ -5,9 +5,10 @@
 namespace hmfsr {
 namespace {
 
-__global__ void k_luma0(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh,
-                        uint16_t *__restrict__ out) {
-    stage::luma0(burst, h, pitch, hh, wh, out, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+__global__ void k_luma01(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh,
+                         uint16_t *__restrict__ out0, uint16_t *__restrict__ out1, int lh1, int lw1) {
+    stage::luma01(burst, h, pitch, hh, wh, out0, out1, lh1, lw1, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y,
+                  blockIdx.z);
 }
 
 __global__ void k_down(const uint16_t *__restrict__ src, int sh, int sw, uint16_t *__restrict__ dst, int dh, int dw,
@@ -31,12 +32,14 @@ __global__ void __launch_bounds__(64) k_ssd_rows(const uint16_t *__restrict__ im
                             blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
+// 4 warps of 32 / (2 RAD + 1) tiles each
 template <int T, int RAD>
-__global__ void __launch_bounds__(128) k_ssd_split(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+__global__ void __launch_bounds__(128) k_ssd_group(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                                    const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                                    int2 *__restrict__ vec) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    stage::ssd_split<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, t >> 4, threadIdx.x & 15,
+    constexpr int kG = 32 / (2 * RAD + 1);
+    const int warp = blockIdx.x * 4 + (threadIdx.x >> 5);
+    stage::ssd_group<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, warp * kG, threadIdx.x & 31,
                              blockIdx.y);
 }
 
@@ -67,9 +70,11 @@ __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, i
 
 static const int kFactors[3] = {2, 4, 4};
 
-// Block matching of one level: rows outermost for small radii and tiles; the offsets dy spread
-// over lanes when the level has too few tiles to fill the GPU one thread per tile.
-constexpr int kSplitBelow = 152 * 256;  // tiles x frames
+// Block matching of one level: rows outermost for small radii and tiles; the offsets dy
+// spread over the lanes of a group when the level has too few tiles to fill the GPU one
+// thread per tile (measured at 12 MP: one thread per tile is faster on level 1, 96k
+// tile-frames, where the grouped form's 110 registers hold 16 warps per SM).
+constexpr long long kGroupBelow = 152LL * 256;  // tiles x frames
 
 template <int T, int RAD>
 static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
@@ -80,8 +85,9 @@ static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, boo
         k_ssd_rows<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
                                                                      parent, pty, ptx, fsh, ref, L.vec[l]);
     } else {
-        if ((long long)tiles * n < kSplitBelow)
-            k_ssd_split<T, RAD><<<dim3(div_up(tiles * 16, 128), n), 128, 0, s>>>(
+        constexpr int kTilesPerBlock = 4 * (32 / (2 * RAD + 1));
+        if ((long long)tiles * n < kGroupBelow)
+            k_ssd_group<T, RAD><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
                 L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
         else
             k_ssd<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
@@ -143,8 +149,11 @@ cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmf
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s) {
     const int n = g.n;
-    k_luma0<<<dim3(div_up(g.wh, 4 * 128), g.hh, n), 128, 0, s>>>(burst, g.h, g.pitch, g.hh, g.wh, L.img[0]);
-    for (int l = 1; l < L.n_levels; ++l)
+    // levels 0 and 1 in one pass over the raw burst; the coarser levels from level 1
+    const bool two = L.n_levels > 1;
+    k_luma01<<<dim3(div_up(g.wh, 4 * 128), div_up(g.hh, 2), n), 128, 0, s>>>(
+        burst, g.h, g.pitch, g.hh, g.wh, L.img[0], two ? L.img[1] : nullptr, two ? L.lh[1] : 0, two ? L.lw[1] : 0);
+    for (int l = 2; l < L.n_levels; ++l)
         k_down<<<dim3(div_up(L.lw[l], 128), L.lh[l], n), 128, 0, s>>>(L.img[l - 1], L.lh[l - 1], L.lw[l - 1],
                                                                        L.img[l], L.lh[l], L.lw[l], kFactors[l - 1]);
     switch (p.tile) {

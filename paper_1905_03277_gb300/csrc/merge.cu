@@ -93,10 +93,11 @@ __global__ void k_export(const float4 *__restrict__ kern, const float *__restric
 
 // --------------------------------------------------------------------------------------
 // strip heights.  A strip kernel's blocks run in waves of (resident blocks per SM) x
-// (SMs); a last wave that is only partly filled costs as long as a full one.  Of the
-// even heights in [lo, hi], take the one with the least waves x (rows + halo): the rows
-// every block walks, halo included.  The occupancy of each kernel is queried once per
-// device; if a query fails, the default height stands.
+// (SMs).  For the latency-bound k_rob a last wave that is only partly filled costs as
+// long as a full one: of the even heights in [lo, hi], take the one with the least
+// waves x (rows + halo), the rows every block walks, halo included (strip_rows).  The
+// occupancy of each kernel is queried once per device; if a query fails, the default
+// height stands.
 // --------------------------------------------------------------------------------------
 enum StripKernel { SK_PREP = 0, SK_ROB = 1, SK_ROB_HF = 2, SK_COUNT = 3 };
 constexpr int kMaxDevices = 64;
@@ -121,6 +122,17 @@ int strip_slots(StripKernel k, const void *kernel) {
     return slots;
 }
 
+// The default height dflt, shortened by two rows at a time (down to lo) while the grid
+// fills less than one wave.  For a kernel that keeps the memory system busy, a partly
+// filled last wave of many costs little (measured for k_prep at 12 MP), but a grid of
+// less than one wave leaves SMs idle.
+int fill_rows(int slots, long long blocks_per_rows, int hh, int lo, int dflt) {
+    int rows = dflt;
+    if (slots <= 0 || blocks_per_rows <= 0 || hh <= 0) return rows;
+    while (rows - 2 >= lo && blocks_per_rows * div_up(hh, rows) < slots) rows -= 2;
+    return rows;
+}
+
 // blocks_per_rows: blocks side by side (columns x frames) per strip of rows
 int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, int hi, int fallback) {
     if (slots <= 0 || blocks_per_rows <= 0 || hh <= 0) return fallback;
@@ -139,8 +151,8 @@ int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, i
 
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
-    const int prep_rows = strip_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
-                                     g.hh, 2, 16, 256, stage::kPrepStrip);
+    const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
+                                    g.hh, 8, stage::kPrepStrip);
     k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
                                                                                    P.kern, prep_rows);
     int nt = g.n * g.ty * g.tx;

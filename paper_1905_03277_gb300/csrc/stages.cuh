@@ -45,6 +45,53 @@ __device__ __forceinline__ void luma0(const uint16_t *__restrict__ burst, int h,
     }
 }
 
+// Levels 0 and 1 together: one thread makes 4 texels in each of the level-0 rows 2 y and
+// 2 y + 1 (as luma0 does) and, from those 8, the 2 level-1 texels they cover (integer floor
+// mean of 2 x 2, as down with factor 2 does), so the first reduction needs no second pass
+// over level 0.  out1 = nullptr: level 0 only.
+__device__ __forceinline__ void luma01(const uint16_t *__restrict__ burst, int h, int pitch, int hh, int wh,
+                                       uint16_t *__restrict__ out0, uint16_t *__restrict__ out1, int lh1, int lw1,
+                                       int u4, int y, int f) {
+    const int u = 4 * u4;
+    if (u >= wh) return;
+    uint32_t sq[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int v = 2 * y + r;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sq[r][i] = 0u;
+        if (v >= hh) continue;
+        const uint16_t *r0 = burst + ((size_t)f * h + 2 * v) * pitch + 2 * u;
+        uint16_t *o = out0 + ((size_t)f * hh + v) * wh + u;
+        if (u + 4 <= wh && ((reinterpret_cast<uintptr_t>(r0) | reinterpret_cast<uintptr_t>(r0 + pitch)) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(r0));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(r0 + pitch));
+            sq[r][0] = (a.x & 0xffffu) + (a.x >> 16) + (b.x & 0xffffu) + (b.x >> 16);
+            sq[r][1] = (a.y & 0xffffu) + (a.y >> 16) + (b.y & 0xffffu) + (b.y >> 16);
+            sq[r][2] = (a.z & 0xffffu) + (a.z >> 16) + (b.z & 0xffffu) + (b.z >> 16);
+            sq[r][3] = (a.w & 0xffffu) + (a.w >> 16) + (b.w & 0xffffu) + (b.w >> 16);
+            *reinterpret_cast<uint2 *>(o) = make_uint2(sq[r][0] | (sq[r][1] << 16), sq[r][2] | (sq[r][3] << 16));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (u + i >= wh) break;
+                const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
+                const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
+                sq[r][i] = (a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16);
+                o[i] = (uint16_t)sq[r][i];
+            }
+        }
+    }
+    if (out1 == nullptr || y >= lh1) return;
+    uint16_t *o1 = out1 + ((size_t)f * lh1 + y) * lw1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int x = u / 2 + k;  // level-1 texel over level-0 columns 2 x, 2 x + 1
+        if (x < lw1) o1[x] = (uint16_t)((sq[0][2 * k] + sq[0][2 * k + 1] + sq[1][2 * k] + sq[1][2 * k + 1]) / 4u);
+    }
+}
+
 // Next level: integer floor mean of f x f blocks.
 __device__ __forceinline__ void down(const uint16_t *__restrict__ src, int sh, int sw, uint16_t *__restrict__ dst,
                                      int dh, int dw, int fct, int x, int y, int f) {
@@ -216,27 +263,29 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
     *out = make_int2(cc.x + bdx, cc.y + bdy);
 }
 
-// The same search with the offsets dy spread over the lanes of a 16-lane group (lane d
-// takes dy = d - RAD; lanes beyond 2 RAD only join the reduction), for levels with too
-// few tiles to fill the GPU one thread per tile.  The group's minimum key is taken by
-// butterfly shuffles; lane 0 of the group writes.  Every lane of the warp calls this; f
-// is the same for the whole warp.
+// The same search with the offsets dy spread over a group of 2 RAD + 1 lanes (lane d of
+// the group takes dy = d - RAD): a warp holds 32 / (2 RAD + 1) groups, one tile each, and
+// its remaining lanes idle.  Each lane gathers the group's keys by shuffles and takes
+// their minimum; the group's first lane writes.  Every lane of the warp calls this; f is
+// the same for the whole warp.
 template <int T, int RAD>
-__device__ __forceinline__ void ssd_split(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+__device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                           const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
-                                          int2 *__restrict__ vec, int tile, int lane16, int f) {
-    constexpr int kW = 2 * RAD + 1;
-    static_assert(kW <= 16, "one lane per dy");
-    const bool active = tile < lty * ltx;
+                                          int2 *__restrict__ vec, int tile0, int lane, int f) {
+    constexpr int kW = 2 * RAD + 1, kG = 32 / kW;
+    static_assert(kW <= 16, "at least two groups per warp");
+    const int grp = lane / kW, d = lane - grp * kW;
+    const int tile = tile0 + grp;
+    const bool active = grp < kG && tile < lty * ltx;
     if (f == ref) {
-        if (active && lane16 == 0) vec[(size_t)f * lty * ltx + tile] = make_int2(0, 0);
+        if (active && d == 0) vec[(size_t)f * lty * ltx + tile] = make_int2(0, 0);
         return;
     }
     const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
     const int2 cc = active ? ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f) : make_int2(0, 0);
     unsigned long long best = ~0ull;
-    if (active && lane16 < kW) {
-        const int dy = lane16 - RAD;
+    if (active) {
+        const int dy = d - RAD;
         const uint16_t *R = img + (size_t)ref * lh * lw;
         const uint16_t *A = img + (size_t)f * lh * lw;
         const int x0 = tx * T, y0 = ty * T;
@@ -260,13 +309,16 @@ __device__ __forceinline__ void ssd_split(const uint16_t *__restrict__ img, int 
             best = key < best ? key : best;
         }
     }
+    // idle lanes read the last group (their result is unused)
+    const int base = min(grp, kG - 1) * kW;
+    unsigned long long m = ~0ull;
 #pragma unroll
-    for (int m = 8; m > 0; m >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, m);
-        best = o < best ? o : best;
+    for (int k = 0; k < kW; ++k) {
+        const unsigned long long o = __shfl_sync(0xffffffffu, best, base + k);
+        m = o < m ? o : m;
     }
-    if (active && lane16 == 0) {
-        const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
+    if (active && d == 0) {
+        const int bdx = (int)(m & 15ull) - 7, bdy = (int)((m >> 4) & 15ull) - 7;
         vec[(size_t)f * lty * ltx + tile] = make_int2(cc.x + bdx, cc.y + bdy);
     }
 }
