@@ -434,6 +434,7 @@ def run_gpu(args):
                              f"+ oracle merge of all {ho} output rows ({t_merge:.2f} s)"}
         per_call = hm.launches_per_call(n, h, w, ap.n_levels)
         launches = args.steps * sum(per_call.values())
+        merge_only_ms = statistics.median([p_ + a_ for p_, a_ in zip(prep_ms, acc_ms)])
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -449,6 +450,9 @@ def run_gpu(args):
                 "gpu_launches": launches, "launches_per_step": per_call, "clocks": clocks,
                 "breakdown_ms": {"align": statistics.median(align_ms), "merge_prepare": statistics.median(prep_ms),
                                  "merge_accumulate": statistics.median(acc_ms)},
+                "merge_only": {"value": mp / (merge_only_ms / 1e3), "unit": UNIT, "ms_per_step": merge_only_ms,
+                               "of": "merge preparation + accumulation of each timed step (CUDA events), "
+                                     "alignment excluded"},
                 "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
                 "batched": batched,
                 "snr_tuning": tuning,

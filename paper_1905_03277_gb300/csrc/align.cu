@@ -17,14 +17,6 @@ __global__ void k_down(const uint16_t *__restrict__ src, int sh, int sw, uint16_
 }
 
 template <int T, int RAD>
-__global__ void __launch_bounds__(64) k_ssd(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
-                                            const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
-                                            int2 *__restrict__ vec) {
-    stage::ssd<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, blockIdx.x * blockDim.x + threadIdx.x,
-                       blockIdx.y);
-}
-
-template <int T, int RAD>
 __global__ void __launch_bounds__(64) k_ssd_rows(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                                  const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                                  int2 *__restrict__ vec) {
@@ -70,11 +62,9 @@ __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, i
 
 static const int kFactors[3] = {2, 4, 4};
 
-// Block matching of one level: rows outermost for small radii and tiles; the offsets dy
-// spread over the lanes of a group when the level has too few tiles to fill the GPU one
-// thread per tile (measured at 12 MP: one thread per tile is faster on level 1, 96k
-// tile-frames, where the grouped form's 110 registers hold 16 warps per SM).
-constexpr long long kGroupBelow = 152LL * 256;  // tiles x frames
+// Block matching of one level: rows outermost for small radii and tiles, else the offsets
+// dy spread over the lanes of a group (measured at 12 MP on level 1, 96k tile-frames: the
+// grouped form 9 us faster than one thread per tile, both at 64 registers).
 
 template <int T, int RAD>
 static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
@@ -86,12 +76,8 @@ static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, boo
                                                                      parent, pty, ptx, fsh, ref, L.vec[l]);
     } else {
         constexpr int kTilesPerBlock = 4 * (32 / (2 * RAD + 1));
-        if ((long long)tiles * n < kGroupBelow)
-            k_ssd_group<T, RAD><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
-                L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
-        else
-            k_ssd<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
-                                                                    parent, pty, ptx, fsh, ref, L.vec[l]);
+        k_ssd_group<T, RAD><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
+            L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
     }
 }
 

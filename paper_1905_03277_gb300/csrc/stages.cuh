@@ -151,6 +151,29 @@ __device__ __forceinline__ int2 ssd_centre(const int2 *__restrict__ parent, int 
     return make_int2(pv.x << fsh, pv.y << fsh);
 }
 
+// N consecutive values of one level row from column x.  inside: every column lies in the
+// row, so the reads index one base pointer.  Otherwise each column is clamped to the row;
+// an opaque copy of x makes the clamps be recomputed at each call instead of all N clamped
+// offsets being held in registers across the caller's loop.
+template <int N>
+__device__ __forceinline__ void load_row(const uint16_t *__restrict__ row, int x, int lw, bool inside, int (&v)[N]) {
+    if (inside) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = __ldg(row + x + i);
+    } else {
+        int xb = x;
+        asm volatile("" : "+r"(xb));
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = __ldg(row + clampi(xb + i, 0, lw - 1));
+    }
+}
+
+// the tile's columns x0 .. x0 + T - 1 and its candidates' xa .. xa + T + 2 RAD - 1 all lie
+// inside a level row of lw texels
+__device__ __forceinline__ bool ssd_inside(int x0, int xa, int T, int RAD, int lw) {
+    return xa >= 0 && xa + T + 2 * RAD <= lw && x0 + T <= lw;
+}
+
 // One thread per tile of one level: exhaustive integer SSD over offsets |d| <= RAD
 // around the candidate (the parent's vector times the level factor).  For each dy the
 // thread streams the tile's rows (L1-cached reads, clamped at the border) and keeps the
@@ -173,7 +196,8 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
     const int cx = cc.x, cy = cc.y;
     const uint16_t *R = img + (size_t)ref * lh * lw;
     const uint16_t *A = img + (size_t)f * lh * lw;
-    const int x0 = tx * T, y0 = ty * T;
+    const int x0 = tx * T, y0 = ty * T, xa = x0 + cx - RAD;
+    const bool inside = ssd_inside(x0, xa, T, RAD, lw);
     unsigned long long best = ~0ull;
     for (int dy = -RAD; dy <= RAD; ++dy) {
         unsigned long long acc[kW];
@@ -183,10 +207,8 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
             const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
             const uint16_t *arow = A + (size_t)clampi(y0 + j + cy + dy, 0, lh - 1) * lw;
             int rv[T], av[T + 2 * RAD];
-#pragma unroll
-            for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
-#pragma unroll
-            for (int i = 0; i < T + 2 * RAD; ++i) av[i] = __ldg(arow + clampi(x0 + cx - RAD + i, 0, lw - 1));
+            load_row(rrow, x0, lw, inside, rv);
+            load_row(arow, xa, lw, inside, av);
 #pragma unroll
             for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
         }
@@ -218,7 +240,8 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
     const int2 cc = ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
     const uint16_t *R = img + (size_t)ref * lh * lw;
     const uint16_t *A = img + (size_t)f * lh * lw;
-    const int x0 = tx * T, y0 = ty * T;
+    const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD;
+    const bool inside = ssd_inside(x0, xa, T, RAD, lw);
     unsigned long long acc[kW][kW];
 #pragma unroll
     for (int a = 0; a < kW; ++a)
@@ -228,20 +251,13 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
 #pragma unroll
     for (int d = 0; d < kW - 1; ++d) {
         const uint16_t *arow = A + (size_t)clampi(y0 + d - RAD + cc.y, 0, lh - 1) * lw;
-#pragma unroll
-        for (int i = 0; i < kA; ++i) av[d][i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
+        load_row(arow, xa, lw, inside, av[d]);
     }
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-        {
-            const uint16_t *arow = A + (size_t)clampi(y0 + j + RAD + cc.y, 0, lh - 1) * lw;
-#pragma unroll
-            for (int i = 0; i < kA; ++i) av[kW - 1][i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
-        }
-        const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
+        load_row(A + (size_t)clampi(y0 + j + RAD + cc.y, 0, lh - 1) * lw, xa, lw, inside, av[kW - 1]);
         int rv[T];
-#pragma unroll
-        for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
+        load_row(R + (size_t)min(y0 + j, lh - 1) * lw, x0, lw, inside, rv);
 #pragma unroll
         for (int d = 0; d < kW; ++d)
 #pragma unroll
@@ -288,7 +304,8 @@ __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int 
         const int dy = d - RAD;
         const uint16_t *R = img + (size_t)ref * lh * lw;
         const uint16_t *A = img + (size_t)f * lh * lw;
-        const int x0 = tx * T, y0 = ty * T;
+        const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD;
+        const bool inside = ssd_inside(x0, xa, T, RAD, lw);
         unsigned long long acc[kW];
 #pragma unroll
         for (int k = 0; k < kW; ++k) acc[k] = 0;
@@ -296,10 +313,8 @@ __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int 
             const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
             const uint16_t *arow = A + (size_t)clampi(y0 + j + cc.y + dy, 0, lh - 1) * lw;
             int rv[T], av[T + 2 * RAD];
-#pragma unroll
-            for (int i = 0; i < T; ++i) rv[i] = __ldg(rrow + min(x0 + i, lw - 1));
-#pragma unroll
-            for (int i = 0; i < T + 2 * RAD; ++i) av[i] = __ldg(arow + clampi(x0 + cc.x - RAD + i, 0, lw - 1));
+            load_row(rrow, x0, lw, inside, rv);
+            load_row(arow, xa, lw, inside, av);
 #pragma unroll
             for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
         }
