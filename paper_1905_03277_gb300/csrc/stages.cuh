@@ -12,9 +12,6 @@ namespace stage {
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
 constexpr float kBig = 1.0e30f;
 
-// exact uint16 -> float on the FMA pipe (v < 2^23)
-__device__ __forceinline__ float u16f(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.0f; }
-
 // ======================================================================================
 // alignment (Sec. 3.2)
 // ======================================================================================
