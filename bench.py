@@ -42,6 +42,30 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of every rank's x: a step of the whole job lasts as long as its
+    slowest rank.  One rank: x itself."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mps(mp_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: each of `world` ranks merges its own burst of mp_per_rank
+    frames x MP per step (replicas), all in ms_per_step (the slowest rank's)."""
+    return world * mp_per_rank / (ms_per_step / 1e3)
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of the burst rank `rank` merges: every rank works on its own input."""
+    import burstgen
+    return burstgen.SEED_BASE + 1 + 1000 * rank
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -202,7 +226,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     hm.build()
 
-    b = burstgen.make_burst(WORKLOAD, seed=burstgen.SEED_BASE + 1 + 1000 * rank, device=dev)
+    b = burstgen.make_burst(WORKLOAD, seed=rank_seed(rank), device=dev)
     raw = b["raw"]
     n, h, w = raw.shape
     scale = b["scale"]
@@ -248,14 +272,10 @@ def run_gpu(args):
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier()
-    elapsed = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(t_start.elapsed_time(t_end), world, dev)
     ms_step = elapsed / args.steps
     mp = n * h * w / 1e6
-    value = world * mp / (ms_step / 1e3)
+    value = whole_job_mps(mp, world, ms_step)
 
     # per-phase durations on the launching stream (separate pass, same work)
     for _ in range(min(args.steps, 10)):
@@ -287,11 +307,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     del pipe
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * mp / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = whole_job_mps(mp, world, e2e_ms)
 
     # noise-dependent tuning: the exact sum of a frame on the GPU (HBM-bound; the calls
     # rotate over the 8 frames, 195 MB > L2), then the parameters the base frame selects
