@@ -89,12 +89,17 @@ def _stream(device, stream):
 _ws_cache: dict = {}
 
 
-def _workspace(device: torch.device, nbytes: int) -> torch.Tensor:
-    """A reusable, 256-byte aligned scratch buffer per device (grown on demand)."""
-    key = (device.type, device.index)
+def _workspace(device: torch.device, nbytes: int, stream=None) -> torch.Tensor:
+    """A reusable, 256-byte aligned scratch buffer per (device, stream), grown on demand.
+    Calls on one stream run in order and share it; calls on different streams get their
+    own, so concurrent calls never race on scratch.  The buffer is allocated on that
+    stream, so the caching allocator orders its reuse after the stream's work."""
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    key = (device.type, device.index, s.cuda_stream)
     buf = _ws_cache.get(key)
     if buf is None or buf.numel() < nbytes + 256:
-        _ws_cache[key] = buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        with torch.cuda.stream(s):
+            _ws_cache[key] = buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
     off = (-buf.data_ptr()) % 256
     return buf[off:off + max(nbytes, 1)]
 
@@ -120,7 +125,7 @@ def align(burst: torch.Tensor, ref: int = 0, params: AlignParams | None = None, 
     motion = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
     mint = torch.empty((n, ty, tx, 2), dtype=torch.int32, device=burst.device) if with_int else None
     nbytes = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(d), params.tile, 1, 1)
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     if subpixel not in ("lk", "quadfit"):
         raise ValueError("subpixel must be 'lk' (Lucas-Kanade) or 'quadfit' (quadratic fit to the matching error)")
@@ -147,7 +152,7 @@ def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None 
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     _lib.check(L.hmfsr_merge(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
                              _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
@@ -166,7 +171,7 @@ def merge_stages(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams 
     omega = torch.empty((n, 3, h // 2, w // 2), dtype=torch.float32, device=burst.device)
     rhat = torch.empty((n, h // 2, w // 2), dtype=torch.float32, device=burst.device)
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     _lib.check(L.hmfsr_merge_stages(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(omega),
                                     _ptr(rhat), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
@@ -327,7 +332,7 @@ def merge_noise(burst: torch.Tensor, motion: torch.Tensor, table: torch.Tensor, 
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     _lib.check(L.hmfsr_merge_noise(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(table), scale[0],
                                    scale[1], _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
@@ -349,7 +354,7 @@ def merge_ex(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | No
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     opts = _lib.MergeOptionsC(noise_table.data_ptr() if noise_table is not None else None, float(hf_loss))
     _lib.check(L.hmfsr_merge_ex(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), ctypes.byref(opts),
@@ -359,14 +364,24 @@ def merge_ex(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | No
 
 
 def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
-                  white_level: int = 4095, stream=None) -> torch.Tensor:
-    """First half of `merge` (hmfsr_merge_prepare): per-frame planes into the device's
-    cached workspace, which `merge_accumulate` then reads."""
+                  white_level: int = 4095, stream=None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """First half of `merge` (hmfsr_merge_prepare): per-frame planes into a workspace,
+    returned for `merge_accumulate` to read.  By default that is the stream's cached
+    workspace, which the next call of this module on the same stream reuses; a caller
+    that interleaves other calls passes its own `workspace` (uint8, 256-byte aligned, at
+    least workspace_size(OP_MERGE_STAGES, ...) bytes)."""
     L = _lib.load()
     params = params or MergeParams()
     d = _desc(burst, ref, white_level)
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
-    ws = _workspace(burst.device, nbytes)
+    if workspace is None:
+        ws = _workspace(burst.device, nbytes, stream)
+    else:
+        if (workspace.dtype != torch.uint8 or workspace.device != burst.device or workspace.numel() < nbytes
+                or workspace.data_ptr() % 256 or not workspace.is_contiguous()):
+            raise ValueError(f"workspace must be a contiguous, 256-byte aligned uint8 tensor of >= {nbytes} bytes "
+                             "on the burst's device")
+        ws = workspace
     pc = params.c()
     _lib.check(L.hmfsr_merge_prepare(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), _ptr(ws),
                                      ws.numel(), _stream(burst.device, stream)), "hmfsr_merge_prepare")
@@ -443,7 +458,7 @@ def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParam
     gm = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
     grad_rgb = grad_rgb.contiguous().float()
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_BACKWARD, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes)
+    ws = _workspace(burst.device, nbytes, stream)
     pc = params.c()
     _lib.check(L.hmfsr_merge_backward(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0],
                                       scale[1], _ptr(rgb), _ptr(den), _ptr(grad_rgb), _ptr(gp), _ptr(gm), _ptr(ws),
