@@ -8,7 +8,9 @@
  * hmfsr_workspace_size().  `stream` is a cudaStream_t passed as void* (NULL = legacy
  * default stream).  Calls are asynchronous on `stream`: arguments are validated on the
  * host before any launch (errors return without touching the GPU); a failed launch
- * returns HMFSR_ERR_CUDA.
+ * returns HMFSR_ERR_CUDA.  The first merge call on a device also queries two kernels'
+ * occupancy (host-side, once; no allocation, no synchronisation) to choose launch
+ * shapes; results never depend on them.
  *
  * Image conventions (all calls):
  *   raw frames  uint16, RGGB Bayer: pixel (x, y) is R when x, y are both even, B when both
