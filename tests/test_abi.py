@@ -93,6 +93,24 @@ def test_merge_rejects_bad_arguments_on_host(L):
     assert _merge_call(L, desc(), ws_bytes=1000) == -3     # too small
 
 
+def test_merge_rejects_empty_and_oversized_bursts_on_host(L):
+    # sizes the 32-bit in-frame offsets and 16-bit guide sums cannot hold, and empty or
+    # degenerate bursts: all rejected before any launch
+    assert _merge_call(L, desc(n=0)) == -1
+    assert _merge_call(L, desc(n=4097)) == -1
+    assert _merge_call(L, desc(h=2)) == -1
+    assert _merge_call(L, desc(w=0)) == -1
+    assert _merge_call(L, desc(h=-256)) == -1
+    assert _merge_call(L, desc(w=65538)) == -1              # wider than 65536
+    assert _merge_call(L, desc(h=32768, w=65536)) == -1     # 2^31 samples in one frame
+    assert _merge_call(L, desc(h=4096, w=4096, pitch=524288)) == -1
+    assert _merge_call(L, desc(ref=-1)) == -1
+    assert _merge_call(L, desc(wl=0)) == -1
+    assert _merge_call(L, desc(wl=7282)) == -1              # 9 x WL must fit 16 bits
+    assert L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(desc(w=65538)), 16, 1, 1) == 0
+    assert L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(desc(n=0)), 16, 1, 1) == 0
+
+
 def test_align_rejects_bad_arguments_on_host(L):
     d = desc()
 
