@@ -569,6 +569,17 @@ def test_noise_table_noise_free_and_deterministic():
     assert abs(bits.mean() - 0.5) < 4.0 * 0.5 / bits.size ** 0.5
 
 
+def test_philox_matches_the_published_known_answers():
+    # Philox-4x32-10 (Salmon et al., SC'11) known-answer vectors of the Random123
+    # distribution: (counter, key) -> output words
+    kat = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+           ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+           ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+            (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in kat:
+        assert tuple(oracle.philox(ctr, key)) == want
+
+
 def test_robustness_with_noise_table_keeps_identical_frames():
     # identical frames have no colour difference, whatever the noise statistics
     rng = np.random.default_rng(1905_03277 + 53)
