@@ -30,11 +30,16 @@ sys.path.insert(0, ROOT)
 METRIC = "merged raw MP/s (frames x MP / s) at 12MP x 8, align + merge"
 UNIT = "MP/s"
 WORKLOAD = "12mp"
-# Per output pixel and frame, the arithmetic the method defines for the accumulation
-# (Eq. 1-2 and the bilinear Omega / Rhat sampling); see the design notes for the count.
-ACC_FP32_OPS_PER_UNIT = 120
+# Per output pixel and frame, the arithmetic the method defines for the accumulation, one
+# FP32 instruction per add, multiply or fused multiply-add:
+#   per sample (9): offset d (2), products dx^2, dx dy, dy^2 (3), the quadratic form of
+#     Eq. 2 (3), its exponent scale (1), numerator and denominator sums (2)    9 x 11 = 99
+#   per frame: sampling position and window centre (4), bilinear Omega: weights (6) and
+#     3 entries x 4 terms (12), its inverse (5), bilinear Rhat at the pixel's weights (4),
+#     Rhat applied to the three channel sums (6)                                     37
+# and 9 exponentials + 1 reciprocal on the MUFU.
+ACC_FP32_OPS_PER_UNIT = 136
 ACC_MUFU_PER_UNIT = 10
-N_SM, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -141,6 +146,53 @@ def kernel_traffic(name: str):
         return None
 
 
+def bench_config(n: int, h: int, w: int, tile: int, world: int) -> dict:
+    """The workload as both arms print it."""
+    return {"workload": "12mp: 8 x 4032x3024 RGGB uint16 (12-bit), 1x RGB float32 output, align + merge",
+            "frames": n, "height": h, "width": w, "scale": "1/1", "tile": tile,
+            "l2": "no flush: the 195 MB burst read each step is larger than L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def measure_pipe_peaks(dev, n_sm: int, gpu_index: int) -> dict:
+    """This GPU's FP32 FMA and MUFU ex2 issue rates (hmfsr_pipe_probe, CUDA events,
+    2048 threads per SM, 10 launches of ~20 ms each per pipe), with the SM clock sampled
+    meanwhile.  Lane-operations per second; per SM per clock = rate / (SMs x MHz)."""
+    import ctypes
+
+    import torch
+
+    from paper_1905_03277_gb300 import _lib
+    L = _lib.load()
+    sink = torch.zeros(256, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, pipe, iters in (("fp32_fma", _lib.PIPE_FP32_FMA, 20000), ("mufu_ex2", _lib.PIPE_MUFU_EX2, 2500)):
+        ops = ctypes.c_double()
+        launch = lambda: _lib.check(L.hmfsr_pipe_probe(pipe, n_sm * 8, iters, ctypes.c_void_p(sink.data_ptr()),
+                                                       ctypes.byref(ops), ctypes.c_void_p(stream.cuda_stream)),
+                                    "hmfsr_pipe_probe")
+        launch()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        with ClockSampler(gpu_index) as clk:
+            e0.record(stream)
+            for _ in range(reps):
+                launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        rate = ops.value * reps / (e0.elapsed_time(e1) / 1e3)
+        c = clk.summary() or {}
+        mhz = c.get("sm_mhz")
+        out[name] = {"lane_ops_per_s": rate, "sm_mhz": mhz, "reasons": c.get("reasons"),
+                     "per_sm_per_clk": rate / (n_sm * mhz * 1e6) if mhz else None}
+    out["n_sm"] = n_sm
+    out["how"] = ("hmfsr_pipe_probe: 8 blocks of 256 threads per SM, 8 independent chains of 16 dependent "
+                  "operations per loop step per thread; 10 launches timed with CUDA events")
+    return out
+
+
 # -----------------------------------------------------------------------------------------
 # CPU oracle (reference arm and cpu_baseline)
 # -----------------------------------------------------------------------------------------
@@ -164,6 +216,9 @@ def oracle_merge_rows_time(raw_np, motion, params, scale, rows, cores):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper's method written out plainly) on the
+    host cores, one whole step per step -- the alignment of the 8-frame 12-MP burst and
+    the merge of every output row -- on the GPU arm's workload and config."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
@@ -172,7 +227,7 @@ def run_reference(args):
     import torch
     # the input is rendered on the GPU when there is one (input generation only)
     gen_dev = "cuda" if torch.cuda.is_available() else "cpu"
-    b = burstgen.make_burst(WORKLOAD, device=gen_dev)
+    b = burstgen.make_burst(WORKLOAD, seed=rank_seed(0), device=gen_dev)
     raw_np = b["raw"].cpu().numpy()
     n, h, w = raw_np.shape
     scale = b["scale"]
@@ -180,27 +235,20 @@ def run_reference(args):
     p = oracle.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2)
     cores = host_cores()
     mp = n * h * w / 1e6
-    # The oracle's alignment of the whole burst is timed once; one step is the oracle
-    # merge of a band of output rows plus the same fraction of the alignment time, with
-    # the band sized so that all steps together take about two minutes.
-    motion, t_align = oracle_align_time(raw_np, cores)
-    t16 = oracle_merge_rows_time(raw_np, motion, p, scale, 16, cores)
-    budget = max(1.0, 120.0 / max(1, args.steps + args.warmup))
-    rows = int(max(16, min(ho, 16 * budget / max(t16, 1e-3))))
     times = []
     for i in range(args.warmup + args.steps):
-        dt = oracle_merge_rows_time(raw_np, motion, p, scale, rows, cores) + t_align * rows / ho
+        motion, t_align = oracle_align_time(raw_np, cores)
+        dt = t_align + oracle_merge_rows_time(raw_np, motion, p, scale, ho, cores)
         if i >= args.warmup:
             times.append(dt)
-    value = (mp * rows / ho) / statistics.mean(times)
-    sample = (f"per step: oracle merge of {rows} of {ho} output rows (all {n} frames) plus {rows}/{ho} of the "
-              f"oracle's whole-burst alignment time ({t_align:.2f} s); value = {rows}/{ho} of the burst's "
-              f"frames x MP / step time")
+    ms = 1000 * statistics.mean(times)
+    value = mp / (ms / 1e3)
+    sample = (f"whole steps: per step, oracle alignment of the {n}-frame burst and oracle merge of all {ho} "
+              f"output rows, on {cores} host threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "12mp: 8 x 4032x3024 RGGB uint16, 1x RGB output, align + merge",
-                       "frames": n, "height": h, "width": w, "scale": "1/1"},
+            "config": bench_config(n, h, w, 16, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -224,6 +272,7 @@ def run_gpu(args):
         raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     hm.build()
 
     b = burstgen.make_burst(WORKLOAD, seed=rank_seed(rank), device=dev)
@@ -425,18 +474,25 @@ def run_gpu(args):
                    "mode": min(tune_log, key=tune_log.get)}
         del plan, brgb, prgb, braw, rb
 
+    pipe_peaks = measure_pipe_peaks(dev, n_sm, local) if rank == 0 else None
+
     if rank == 0:
         units = ho * wo * n
         acc_s = statistics.median(acc_ms) / 1e3
         achieved = ACC_FP32_OPS_PER_UNIT * units / acc_s / 1e12
-        peak = N_SM * FP32_LANES * MAX_SM_MHZ * 1e6 / 1e12
         clocks = clk.summary()
+        fma, ex2 = pipe_peaks["fp32_fma"], pipe_peaks["mufu_ex2"]
+        peak = fma["lane_ops_per_s"] / 1e12
+        mufu_peak = ex2["lane_ops_per_s"] / 1e12
         roof = {"bound": "alu", "kernel": "k_merge (hmfsr_merge_accumulate)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": kernel_traffic("k_merge_12mp"),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock (FP32 lane-ops/s)",
+                "unit": "T lane-ops/s", "frac": achieved / peak, "traffic": kernel_traffic("k_merge_12mp"),
+                "peak_source": (f"measured: FP32 FMA issue rate of hmfsr_pipe_probe on this GPU ({n_sm} SMs, "
+                                f"{fma['sm_mhz']} MHz sampled; {fma['per_sm_per_clk']:.1f} lane-ops per SM per clock)"),
                 "ops_per_unit": ACC_FP32_OPS_PER_UNIT, "units_per_launch": units,
-                "mufu": {"achieved": ACC_MUFU_PER_UNIT * units / acc_s / 1e12,
-                         "peak": N_SM * 16 * MAX_SM_MHZ * 1e6 / 1e12}}
+                "unit_of_work": "output pixel x frame; one lane-op per FP32 add, multiply or fused multiply-add",
+                "mufu": {"achieved": ACC_MUFU_PER_UNIT * units / acc_s / 1e12, "peak": mufu_peak,
+                         "frac": ACC_MUFU_PER_UNIT * units / acc_s / 1e12 / mufu_peak,
+                         "peak_source": f"measured: ex2 issue rate of hmfsr_pipe_probe ({ex2['sm_mhz']} MHz sampled)"}}
         peaks = measured_peaks()
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -455,11 +511,9 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "12mp: 8 x 4032x3024 RGGB uint16 (12-bit), 1x RGB float32 output, "
-                                       "align + merge", "frames": n, "height": h, "width": w, "scale": "1/1",
-                           "tile": p.tile, "l2": "no flush: the 195 MB burst read each step is larger than L2",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                "config": bench_config(n, h, w, p.tile, world),
                 "roofline": roof, "cpu_baseline": cpu,
+                "fp32_peak_measured": fma, "mufu_peak_measured": ex2,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_burst.numel() * 2),
                         "d2h_bytes_per_step": int(host_out.numel() * 4), "ms_per_step": e2e_ms,
                         "steps": e2e_steps, "api": "AlignMergePipeline (hmfsr_align + hmfsr_merge), 2 device slots: "

@@ -158,7 +158,10 @@ hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_d
  * exits).  Bursts whose merge needs more scratch than that, as hmfsr_workspace_size
  * (HMFSR_OP_MERGE, ...) reports, are rejected with HMFSR_ERR_WORKSPACE before any launch
  * (8 frames of 768 x 512 fit).  The first call on a device looks up the array's device
- * address; make that first call before capturing a stream into a CUDA graph.  All calls
+ * address; make that first call before capturing a stream into a CUDA graph.  The
+ * address is kept for the life of the process, so after cudaDeviceReset on a device (a
+ * reset ends the context the address belongs to) this entry point must not be called
+ * on that device again.  All calls
  * share the one array: calls that overlap on the GPU (other streams, other host threads)
  * race and must be serialised by the caller.  Arguments and results are otherwise those
  * of hmfsr_merge. */
@@ -197,6 +200,15 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
  * HMFSR_ERR_TIMEOUT if a block's bounded wait for a dependency ran out (the kernel then
  * stops early and the outputs are incomplete; the device stays usable). */
 hmfsr_status hmfsr_batch_wait(hmfsr_batch_plan plan, void *ws, void *stream);
+
+/* The integer block-matching vectors (Sec. 3.2, level 0, in half-res px) that the last
+ * run of the plan on workspace `ws` computed for burst `burst`: int32
+ * [n_frames][TY][TX][2] into motion_int_dev (4-byte aligned, caller-owned), as
+ * hmfsr_align's motion_int_dev.  An asynchronous device-to-device copy on `stream`,
+ * ordered after the run when given the run's stream.  HMFSR_ERR_INVALID_ARG for a NULL
+ * plan, workspace or destination, or a burst index outside the plan. */
+hmfsr_status hmfsr_batch_vectors(hmfsr_batch_plan plan, const void *ws, int burst, int32_t *motion_int_dev,
+                                 void *stream);
 
 /* Settings: accumulation work item of merge_tile_w x (128 / merge_tile_w) output pixels
  * (merge_tile_w divides 128), ctas_per_sm persistent blocks per SM (0 = as many as fit),
@@ -283,19 +295,36 @@ hmfsr_status hmfsr_merge_ex(const uint16_t *burst_dev, const hmfsr_burst_desc *d
                             const hmfsr_merge_params *params, const hmfsr_merge_options *opts, int scale_num,
                             int scale_den, float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes, void *stream);
 
-/* Host-only (no GPU): from the base frame's mean sample value `mean` (DN) and the noise
- * model var(x) = noise_a * x + noise_b, SNR = mean / sqrt(noise_a * mean + noise_b) (one
- * raw sample of one frame; +infinity for a noise-free model), then every parameter of
+/* Host-only (no GPU): from the base frame's mean sample value, mean = sample_sum /
+ * sample_count in DN (sample_sum from hmfsr_frame_sum, sample_count = height x width;
+ * the quotient is taken here, correctly rounded in FP64), and the noise model var(x) =
+ * noise_a * x + noise_b, SNR = mean / sqrt(noise_a * mean + noise_b) (one raw sample of
+ * one frame; +infinity for a noise-free model), then every parameter of
  * *mparams and *aparams:
  *   k_detail 0.33 -> 0.25, k_denoise 5 -> 3, d_th 0.010 -> 0.001, d_tr 0.020 -> 0.006,
  *   linear in SNR from SNR <= 6 (the denoising end) to SNR >= 30 (the detail end);
  *   tile 64 for SNR < 10, 32 for SNR < 14, else 16 (both structs);
  *   k_stretch 4, k_shrink 2, t 0.12, s1 12, s2 2, m_th 0.8, noise_a/b as given;
  *   alignment: 4 levels, radii 1 (finest), 4, 4, 4, 3 Lucas-Kanade iterations.
- * `snr` may be NULL.  HMFSR_ERR_INVALID_ARG for a negative or non-finite mean or noise
- * coefficient, or a NULL struct. */
-hmfsr_status hmfsr_snr_tuning(double mean, float noise_a, float noise_b, hmfsr_merge_params *mparams,
-                              hmfsr_align_params *aparams, double *snr);
+ * `snr` may be NULL.  HMFSR_ERR_INVALID_ARG for sample_count 0, a sum or count of 2^53 or
+ * more, a negative or non-finite noise coefficient, or a NULL struct. */
+hmfsr_status hmfsr_snr_tuning(uint64_t sample_sum, uint64_t sample_count, float noise_a, float noise_b,
+                              hmfsr_merge_params *mparams, hmfsr_align_params *aparams, double *snr);
+
+/* ---- Measurement aid (not part of the method).  The accumulation (Eq. 1-2) is bound
+ * by FP32 and MUFU issue rather than by HBM, so its roofline divides by this GPU's
+ * measured FP32 fused-multiply-add rate and ex2 rate.  ---- */
+enum { HMFSR_PIPE_FP32_FMA = 0, HMFSR_PIPE_MUFU_EX2 = 1 };
+
+/* Enqueues one issue-rate probe on `stream`: `blocks` blocks of 256 threads, each thread
+ * running 8 independent chains of `iters` x 16 dependent operations (pipe
+ * HMFSR_PIPE_FP32_FMA: fmaf; HMFSR_PIPE_MUFU_EX2: ex2.approx.ftz).  *lane_ops (nullable)
+ * receives the operations the launch performs (blocks x 256 x iters x 128); the caller
+ * times the launch with events on `stream`.  sink_dev: 256 floats of device memory
+ * (4-byte aligned), written only on a branch no input takes.  HMFSR_ERR_INVALID_ARG for
+ * an unknown pipe, blocks outside [1, 2^20], iters outside [1, 2^24] or a NULL or
+ * misaligned sink. */
+hmfsr_status hmfsr_pipe_probe(int pipe, int blocks, int iters, float *sink_dev, double *lane_ops, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *hmfsr_status_string(hmfsr_status s);

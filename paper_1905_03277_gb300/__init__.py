@@ -77,6 +77,25 @@ def _desc(burst: torch.Tensor, ref: int, white_level: int) -> _lib.BurstDesc:
     return _lib.BurstDesc(n, h, w, burst.stride(1), ref, 0, white_level, 0)
 
 
+def _merge_inputs(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams, ref: int, white_level: int,
+                  *others: torch.Tensor | None) -> _lib.BurstDesc:
+    """The checks every merge-family call makes before handing pointers to the library:
+    burst and motion (and any other given tensors) on one CUDA device, the burst's layout,
+    and motion contiguous float32 [n, TY, TX, 2] for the params' tile.  Raises before any
+    launch; returns the burst descriptor."""
+    if not (burst.is_cuda and motion.is_cuda) or motion.device != burst.device:
+        raise ValueError("burst and motion must be on the same CUDA device")
+    for t in others:
+        if t is not None and (not t.is_cuda or t.device != burst.device):
+            raise ValueError("every tensor argument must be on the burst's CUDA device")
+    d = _desc(burst, ref, white_level)
+    n, h, w = burst.shape
+    ty, tx = n_tiles(h, w, params.tile)
+    if motion.dtype != torch.float32 or tuple(motion.shape) != (n, ty, tx, 2) or not motion.is_contiguous():
+        raise ValueError(f"motion must be contiguous float32 [{n},{ty},{tx},2]")
+    return d
+
+
 def _ptr(t: torch.Tensor | None):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -141,13 +160,8 @@ def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None 
     per-channel log2 of Eq. 1's denominator."""
     L = _lib.load()
     params = params or MergeParams()
-    if not (burst.is_cuda and motion.is_cuda):
-        raise ValueError("burst and motion must be on a CUDA device")
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level)
     n, h, w = burst.shape
-    ty, tx = n_tiles(h, w, params.tile)
-    if motion.dtype != torch.float32 or tuple(motion.shape) != (n, ty, tx, 2) or not motion.is_contiguous():
-        raise ValueError(f"motion must be contiguous float32 [{n},{ty},{tx},2]")
     ho, wo = out_size(h, w, scale)
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
@@ -166,7 +180,7 @@ def merge_stages(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams 
     final robustness Rhat float32 [n, H/2, W/2] on the base grid (Eq. 9)."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level)
     n, h, w = burst.shape
     omega = torch.empty((n, 3, h // 2, w // 2), dtype=torch.float32, device=burst.device)
     rhat = torch.empty((n, h // 2, w // 2), dtype=torch.float32, device=burst.device)
@@ -290,13 +304,14 @@ def frame_sum(burst: torch.Tensor, frame: int = 0, stream=None, out: torch.Tenso
     return dst if out is not None else int(dst.item())
 
 
-def snr_tuning(mean: float, noise_a: float, noise_b: float):
-    """(MergeParams, AlignParams, snr) for a base frame of mean brightness `mean` in DN and
+def snr_tuning(sample_sum: int, sample_count: int, noise_a: float, noise_b: float):
+    """(MergeParams, AlignParams, snr) for a base frame whose samples sum to `sample_sum`
+    over `sample_count` samples (mean brightness in DN = their quotient, taken in C) and
     the noise model var = noise_a * x + noise_b (hmfsr_snr_tuning; host arithmetic)."""
     L = _lib.load()
     mp, ap, snr = _lib.MergeParamsC(), _lib.AlignParamsC(), ctypes.c_double()
-    _lib.check(L.hmfsr_snr_tuning(float(mean), float(noise_a), float(noise_b), ctypes.byref(mp), ctypes.byref(ap),
-                                  ctypes.byref(snr)), "hmfsr_snr_tuning")
+    _lib.check(L.hmfsr_snr_tuning(int(sample_sum), int(sample_count), float(noise_a), float(noise_b),
+                                  ctypes.byref(mp), ctypes.byref(ap), ctypes.byref(snr)), "hmfsr_snr_tuning")
     m = MergeParams(**{f.name: getattr(mp, f.name) for f in fields(MergeParams)})
     a = AlignParams(tile=ap.tile, n_levels=ap.n_levels, radius=tuple(ap.radius), lk_iters=ap.lk_iters)
     return m, a, snr.value
@@ -307,7 +322,7 @@ def auto_params(burst: torch.Tensor, noise_a: float, noise_b: float, ref: int = 
     brightness (one device reduction and an 8-byte read back) and the noise model give
     the SNR, and the SNR every parameter.  Returns (MergeParams, AlignParams, snr)."""
     n, h, w = burst.shape
-    return snr_tuning(frame_sum(burst, ref, stream) / (h * w), noise_a, noise_b)
+    return snr_tuning(frame_sum(burst, ref, stream), h * w, noise_a, noise_b)
 
 
 def noise_table(noise_a: float, noise_b: float, white_level: int = 4095, device=None, stream=None) -> torch.Tensor:
@@ -326,7 +341,9 @@ def merge_noise(burst: torch.Tensor, motion: torch.Tensor, table: torch.Tensor, 
     """`merge` with the robustness's noise statistics from a `noise_table` (hmfsr_merge_noise)."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level, table)
+    if table.dtype != torch.float32 or tuple(table.shape) != (_lib.NOISE_LEVELS, 4) or not table.is_contiguous():
+        raise ValueError(f"noise table must be contiguous float32 [{_lib.NOISE_LEVELS},4]")
     n, h, w = burst.shape
     ho, wo = out_size(h, w, scale)
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
@@ -348,7 +365,10 @@ def merge_ex(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | No
     `hf_loss` (0: off)."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level, noise_table)
+    if noise_table is not None and (noise_table.dtype != torch.float32 or not noise_table.is_contiguous()
+                                    or tuple(noise_table.shape) != (_lib.NOISE_LEVELS, 4)):
+        raise ValueError(f"noise table must be contiguous float32 [{_lib.NOISE_LEVELS},4]")
     n, h, w = burst.shape
     ho, wo = out_size(h, w, scale)
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
@@ -366,16 +386,20 @@ def merge_ex(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | No
 def merge_prepare(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
                   white_level: int = 4095, stream=None, workspace: torch.Tensor | None = None) -> torch.Tensor:
     """First half of `merge` (hmfsr_merge_prepare): per-frame planes into a workspace,
-    returned for `merge_accumulate` to read.  By default that is the stream's cached
-    workspace, which the next call of this module on the same stream reuses; a caller
-    that interleaves other calls passes its own `workspace` (uint8, 256-byte aligned, at
-    least workspace_size(OP_MERGE_STAGES, ...) bytes)."""
+    returned for `merge_accumulate` to read.  By default the planes get a buffer of their
+    own (from PyTorch's caching allocator, on the call's stream), so no later call of this
+    module can overwrite them; a caller may pass its own `workspace` instead (uint8,
+    contiguous, 256-byte aligned, at least workspace_size(OP_MERGE_STAGES, ...) bytes)."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level, workspace)
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
     if workspace is None:
-        ws = _workspace(burst.device, nbytes, stream)
+        s = stream if stream is not None else torch.cuda.current_stream(burst.device)
+        with torch.cuda.stream(s):
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=burst.device)
+        off = (-buf.data_ptr()) % 256
+        ws = buf[off:off + nbytes]
     else:
         if (workspace.dtype != torch.uint8 or workspace.device != burst.device or workspace.numel() < nbytes
                 or workspace.data_ptr() % 256 or not workspace.is_contiguous()):
@@ -394,9 +418,15 @@ def merge_accumulate(burst: torch.Tensor, motion: torch.Tensor, ws: torch.Tensor
     """Second half of `merge` (hmfsr_merge_accumulate) from the planes in `ws`."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level, ws, out, den)
     n, h, w = burst.shape
     ho, wo = out_size(h, w, scale)
+    nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_STAGES, ctypes.byref(d), params.tile, 1, 1)
+    if ws.dtype != torch.uint8 or ws.numel() < nbytes or ws.data_ptr() % 256 or not ws.is_contiguous():
+        raise ValueError(f"ws must be the planes merge_prepare returned (>= {nbytes} aligned bytes)")
+    for t, what in ((out, "out"), (den, "den")):
+        if t is not None and (t.dtype != torch.float32 or tuple(t.shape) != (3, ho, wo) or not t.is_contiguous()):
+            raise ValueError(f"{what} must be contiguous float32 [3,{ho},{wo}]")
     if out is None:
         out = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     pc = params.c()
@@ -431,7 +461,7 @@ def merge_static(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams 
     overlap on the GPU race)."""
     L = _lib.load()
     params = params or MergeParams()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level)
     n, h, w = burst.shape
     ho, wo = out_size(h, w, scale)
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
@@ -451,9 +481,16 @@ def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParam
     order, dL/dmotion float32 [n, TY, TX, 2]) for grad_rgb = dL/drgb, given the forward's
     rgb and den (merge(..., with_den=True))."""
     L = _lib.load()
-    d = _desc(burst, ref, white_level)
+    d = _merge_inputs(burst, motion, params, ref, white_level, rgb, den, grad_rgb)
     n, h, w = burst.shape
     ty, tx = n_tiles(h, w, params.tile)
+    ho, wo = out_size(h, w, scale)
+    for t, what in ((rgb, "rgb"), (den, "den"), (grad_rgb, "grad_rgb")):
+        if tuple(t.shape) != (3, ho, wo):
+            raise ValueError(f"{what} must be [3,{ho},{wo}]")
+    for t, what in ((rgb, "rgb"), (den, "den")):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{what} must be contiguous float32 (the forward's output)")
     gp = torch.empty(8, dtype=torch.float32, device=burst.device)
     gm = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
     grad_rgb = grad_rgb.contiguous().float()
@@ -554,6 +591,17 @@ class BatchPlan:
         if wait:
             self.wait(stream)
         return rgbs
+
+    def vectors(self, k: int, stream=None) -> torch.Tensor:
+        """Integer block-matching vectors (level 0, half-res px) of burst k from the last
+        run: int32 [n, TY, TX, 2] (hmfsr_batch_vectors)."""
+        if self.ws is None:
+            raise RuntimeError("run the plan first")
+        n, h, w = self.shapes[k]
+        out = torch.empty((n,) + n_tiles(h, w, 16) + (2,), dtype=torch.int32, device=self.ws.device)
+        _lib.check(self._L.hmfsr_batch_vectors(self._h, _ptr(self.ws), k, _ptr(out), _stream(self.ws.device, stream)),
+                   "hmfsr_batch_vectors")
+        return out
 
     def wait(self, stream=None) -> int:
         st = self._L.hmfsr_batch_wait(self._h, _ptr(self.ws), _stream(self.ws.device, stream))

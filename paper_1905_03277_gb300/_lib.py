@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libhmfsr.so")
-SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu", "tuning.cu")
+SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu", "tuning.cu", "probe.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic FMA contraction, so a device function gives the same bits in
 # every kernel it is inlined into (fused multiply-adds are written out with fmaf)
@@ -85,13 +85,14 @@ class MergeParamsC(ctypes.Structure):
 
 
 OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD = 0, 1, 2, 3
+PIPE_FP32_FMA, PIPE_MUFU_EX2 = 0, 1
 NOISE_LEVELS = 129
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
-           "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_configure",
+           "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_vectors", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
            "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit", "hmfsr_merge_ex",
-           "hmfsr_status_string", "hmfsr_version")
+           "hmfsr_pipe_probe", "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
 
@@ -132,6 +133,8 @@ def load(path: str | None = None):
     L.hmfsr_batch_run.restype = ci
     L.hmfsr_batch_wait.argtypes = [vp, vp, vp]
     L.hmfsr_batch_wait.restype = ci
+    L.hmfsr_batch_vectors.argtypes = [vp, vp, ci, vp, vp]
+    L.hmfsr_batch_vectors.restype = ci
     L.hmfsr_batch_configure.argtypes = [vp, ci, ci, ci, ci, ci, ci]
     L.hmfsr_batch_configure.restype = ci
     L.hmfsr_batch_tune.argtypes = [vp, pp, pp, pp, vp, sz, vp, P(ctypes.c_float), P(ctypes.c_float)]
@@ -142,7 +145,8 @@ def load(path: str | None = None):
     L.hmfsr_batch_free.restype = None
     L.hmfsr_frame_sum.argtypes = [vp, P(BurstDesc), ci, vp, vp]
     L.hmfsr_frame_sum.restype = ci
-    L.hmfsr_snr_tuning.argtypes = [ctypes.c_double, ctypes.c_float, ctypes.c_float, P(MergeParamsC), P(AlignParamsC),
+    L.hmfsr_snr_tuning.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_float, ctypes.c_float, P(MergeParamsC),
+                                   P(AlignParamsC),
                                    P(ctypes.c_double)]
     L.hmfsr_snr_tuning.restype = ci
     L.hmfsr_align_quadfit.argtypes = [vp, P(BurstDesc), P(AlignParamsC), vp, vp, vp, sz, vp]
@@ -153,6 +157,8 @@ def load(path: str | None = None):
     L.hmfsr_noise_table.restype = ci
     L.hmfsr_merge_noise.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, ci, ci, vp, vp, vp, sz, vp]
     L.hmfsr_merge_noise.restype = ci
+    L.hmfsr_pipe_probe.argtypes = [ci, ci, ci, vp, P(ctypes.c_double), vp]
+    L.hmfsr_pipe_probe.restype = ci
     L.hmfsr_status_string.argtypes = [ci]
     L.hmfsr_status_string.restype = ctypes.c_char_p
     L.hmfsr_version.argtypes = []

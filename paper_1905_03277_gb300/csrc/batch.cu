@@ -652,6 +652,19 @@ hmfsr_status hmfsr_batch_wait(hmfsr_batch_plan plan, void *ws, void *stream) {
     return status == 0 ? HMFSR_OK : (hmfsr_status)status;
 }
 
+hmfsr_status hmfsr_batch_vectors(hmfsr_batch_plan plan, const void *ws, int burst, int32_t *motion_int_dev,
+                                 void *stream) {
+    if (!plan || !ws || !motion_int_dev || burst < 0 || burst >= plan->nb ||
+        (reinterpret_cast<uintptr_t>(motion_int_dev) & 3))
+        return HMFSR_ERR_INVALID_ARG;
+    // level 0's vectors follow level 0's image in the burst's part of the workspace
+    const BatchBurst &bb = plan->host[burst];
+    const size_t off = plan->burst_off[burst] + align256(sizeof(uint16_t) * (size_t)bb.g.n * bb.L.lh[0] * bb.L.lw[0]);
+    const size_t bytes = sizeof(int2) * (size_t)bb.g.n * bb.L.lty[0] * bb.L.ltx[0];
+    return cudaMemcpyAsync(motion_int_dev, static_cast<const char *>(ws) + off, bytes, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream) == cudaSuccess ? HMFSR_OK : HMFSR_ERR_CUDA;
+}
+
 hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *bursts_dev, float *const *motion_dev,
                               float *const *rgb_dev, void *ws, size_t ws_bytes, void *stream, float *best_ms,
                               float *tune_log) {

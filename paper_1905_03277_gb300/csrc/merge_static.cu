@@ -25,7 +25,9 @@ std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device; resolved once per device
-// (the array's name is only a host-side stand-in in host code).
+// (the array's name is only a host-side stand-in in host code) and kept until the
+// process exits: it belongs to the device's primary context, which cudaDeviceReset ends,
+// so the entry point is not for use on a device after a reset (the header says so).
 hmfsr_status scratch_address(void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HMFSR_ERR_CUDA;

@@ -198,11 +198,13 @@ hmfsr_status hmfsr_noise_table(float noise_a, float noise_b, int white_level, fl
     return cudaGetLastError() == cudaSuccess ? HMFSR_OK : HMFSR_ERR_CUDA;
 }
 
-hmfsr_status hmfsr_snr_tuning(double mean, float noise_a, float noise_b, hmfsr_merge_params *mparams,
-                              hmfsr_align_params *aparams, double *snr_out) {
-    if (!mparams || !aparams || !isfinite(mean) || mean < 0.0 || !isfinite(noise_a) || !isfinite(noise_b) ||
-        noise_a < 0.f || noise_b < 0.f)
+hmfsr_status hmfsr_snr_tuning(uint64_t sample_sum, uint64_t sample_count, float noise_a, float noise_b,
+                              hmfsr_merge_params *mparams, hmfsr_align_params *aparams, double *snr_out) {
+    // both below 2^53: exact as doubles, so the mean is the correctly rounded quotient
+    if (!mparams || !aparams || sample_count == 0 || sample_count >= (1ull << 53) || sample_sum >= (1ull << 53) ||
+        !isfinite(noise_a) || !isfinite(noise_b) || noise_a < 0.f || noise_b < 0.f)
         return HMFSR_ERR_INVALID_ARG;
+    const double mean = (double)sample_sum / (double)sample_count;
     // SNR of one raw sample of a single frame at the mean brightness
     const double var = (double)noise_a * mean + (double)noise_b;
     const double snr = var > 0.0 ? mean / sqrt(var) : INFINITY;

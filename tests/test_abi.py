@@ -160,12 +160,29 @@ def test_batch_plan_validation_on_host(L):
         p.configure(merge_tile_w=48)                       # must divide 128
 
 
+def test_batch_vectors_rejects_bad_arguments(L):
+    # fake, never dereferenced pointers: every case returns before any copy
+    p = hm.BatchPlan([(4, 64, 96)])
+    ws, dst = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    assert L.hmfsr_batch_vectors(None, ws, 0, dst, None) == -1
+    assert L.hmfsr_batch_vectors(p._h, None, 0, dst, None) == -1
+    assert L.hmfsr_batch_vectors(p._h, ws, 0, None, None) == -1
+    assert L.hmfsr_batch_vectors(p._h, ws, 1, dst, None) == -1        # burst index outside the plan
+    assert L.hmfsr_batch_vectors(p._h, ws, -1, dst, None) == -1
+    assert L.hmfsr_batch_vectors(p._h, ws, 0, ctypes.c_void_p(514), None) == -1   # misaligned
+    with pytest.raises(RuntimeError):
+        p.vectors(0)                                                 # not run yet
+
+
 def test_snr_tuning_through_the_abi_matches_the_oracle(L):
     # host-only entry point: no GPU needed
     import oracle
-    for mean, a, b in [(50.0, 4.0, 36.0), (700.0, 2.0, 9.0), (1500.0, 4.0, 36.0), (3240.0, 10.0, 0.0),
-                       (4000.0, 0.5, 4.0), (800.0, 0.0, 0.0), (0.0, 1.0, 1.0)]:
-        mp, ap, snr = hm.snr_tuning(mean, a, b)
+    # (sum, count): whole means and a 12-MP frame's ragged quotient
+    for (ssum, cnt), a, b in [((200, 4), 4.0, 36.0), ((700, 1), 2.0, 9.0), ((6000, 4), 4.0, 36.0),
+                              ((3240, 1), 10.0, 0.0), ((4000, 1), 0.5, 4.0), ((800, 1), 0.0, 0.0),
+                              ((0, 7), 1.0, 1.0), ((17_654_321_987, 12_192_768), 4.0, 36.0)]:
+        mean = ssum / cnt
+        mp, ap, snr = hm.snr_tuning(ssum, cnt, a, b)
         want = oracle.snr_tuning(mean, a, b)
         assert snr == want["snr"]
         assert mp.tile == ap.tile == want["tile"]
@@ -177,10 +194,11 @@ def test_snr_tuning_through_the_abi_matches_the_oracle(L):
 
 def test_tuning_entry_points_reject_bad_arguments(L):
     mp, ap = _lib.MergeParamsC(), _lib.AlignParamsC()
-    assert L.hmfsr_snr_tuning(-1.0, 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
-    assert L.hmfsr_snr_tuning(float("nan"), 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
-    assert L.hmfsr_snr_tuning(10.0, -1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
-    assert L.hmfsr_snr_tuning(10.0, 1.0, 1.0, None, ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(10, 0, 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1       # no samples
+    assert L.hmfsr_snr_tuning(1 << 53, 1, 1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1  # sum not exact
+    assert L.hmfsr_snr_tuning(10, 1, float("nan"), 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(10, 1, -1.0, 1.0, ctypes.byref(mp), ctypes.byref(ap), None) == -1
+    assert L.hmfsr_snr_tuning(10, 1, 1.0, 1.0, None, ctypes.byref(ap), None) == -1
     d = desc(n=2)
     # fake, never dereferenced pointers: every case returns before any launch
     assert L.hmfsr_frame_sum(ctypes.c_void_p(16), ctypes.byref(d), 2, ctypes.c_void_p(256), None) == -1

@@ -1,11 +1,16 @@
-"""Ragged batches through one persistent, graph-captured launch (hmfsr_batch_*): outputs
-bit-identical to aligning and merging each burst on its own; the bounded dependency
-waits report HMFSR_ERR_TIMEOUT (without faulting) when a dependency never completes."""
+"""Ragged batches through one persistent, graph-captured launch (hmfsr_batch_*): every
+burst's integer vectors bit-exact and its merge within the merge bar against the FP64
+oracle; outputs bit-identical to aligning and merging each burst on its own; the bounded
+dependency waits report HMFSR_ERR_TIMEOUT (without faulting) when a dependency never
+completes."""
+import numpy as np
 import pytest
 import torch
 
 import burstgen
+import oracle
 import paper_1905_03277_gb300 as hm
+from _parity import assert_merge_close, assert_motion_matches_oracle, oparams
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +65,25 @@ def test_batch_bit_identical_to_plain(dev, batch):
         for k in range(len(CASES)):
             assert torch.equal(mvs[k], plain_mv[k]), f"motion of burst {k}"
             assert torch.equal(rgbs[k], plain_rgb[k]), f"rgb of burst {k}"
+
+
+def test_batch_matches_the_oracle(dev, batch):
+    # each burst of the ragged batch (6 shapes, 3 scales, refs 0-4) against the oracle
+    # directly: its alignment from the same frames, and its merge given the batch's own
+    # float32 motion
+    bursts, params, _, _ = batch
+    plan = make_plan(bursts, params)
+    rgbs = plan.outputs(dev)
+    mvs = [torch.empty((n,) + hm.n_tiles(h, w, 16) + (2,), dtype=torch.float32, device=dev)
+           for (n, h, w, _, _) in CASES]
+    plan.run(bursts, rgbs, mvs, wait=True)
+    for k, (n, h, w, sc, ref) in enumerate(CASES):
+        raw_np = bursts[k].cpu().numpy()
+        g_int = plan.vectors(k).cpu().numpy()
+        g_mv = mvs[k].cpu().numpy()
+        assert_motion_matches_oracle(g_int, g_mv, raw_np, ref)
+        want = oracle.merge(raw_np, g_mv, oparams(params[k]), scale=sc, ref=ref)
+        assert_merge_close(rgbs[k].cpu().numpy(), want, f"burst {k}: {n}x{h}x{w}, scale {sc}, ref {ref}")
 
 
 def test_batch_timeout_is_reported_and_recovers(dev, batch):

@@ -13,12 +13,9 @@ import torch
 import burstgen
 import oracle
 import paper_1905_03277_gb300 as hm
+from _parity import assert_merge_close, assert_motion_matches_oracle, oparams
 
 pytestmark = pytest.mark.gpu
-
-WL = 4095
-MAX_ABS = 1e-4 * WL
-MEAN_ABS = 1e-6 * WL
 
 
 @pytest.fixture(scope="module")
@@ -33,62 +30,12 @@ def params_of(b, **kw):
     return hm.MergeParams(noise_a=b["gain"], noise_b=b["read"] ** 2, **kw)
 
 
-def oparams(p: hm.MergeParams) -> oracle.MergeParams:
-    return oracle.MergeParams(**{k: getattr(p, k) for k in oracle.MergeParams.__dataclass_fields__})
-
-
-def merge_errors(gpu, ref):
-    err = np.abs(gpu.astype(np.float64) - ref)
-    return err.reshape(3, -1).max(axis=1), err.reshape(3, -1).mean(axis=1)
-
-
-def assert_merge_close(gpu, ref, what=""):
-    assert np.isfinite(gpu).all(), what
-    mx, mn = merge_errors(gpu, ref)
-    assert (mx <= MAX_ABS).all() and (mn <= MEAN_ABS).all(), f"{what}: max {mx}, mean {mn}"
-
-
-def lk_conditioned(raw_np, ref, tile, floor=1e-6):
-    """Tiles whose level-0 normal matrix is well conditioned (lambda_min / lambda_max)."""
-    lq = oracle.luma(raw_np[ref]).astype(np.float64)
-    gx = np.zeros_like(lq)
-    gy = np.zeros_like(lq)
-    gx[:, 1:-1] = lq[:, 2:] - lq[:, :-2]
-    gx[:, 0] = lq[:, 1] - lq[:, 0]
-    gx[:, -1] = lq[:, -1] - lq[:, -2]
-    gy[1:-1] = lq[2:] - lq[:-2]
-    gy[0] = lq[1] - lq[0]
-    gy[-1] = lq[-1] - lq[-2]
-    t = tile // 2
-    H, W = lq.shape
-    ty, tx = -(-H // t), -(-W // t)
-    pad = lambda a: np.pad(a, ((0, ty * t - H), (0, tx * t - W)), mode="edge")
-    sxx = (pad(gx * gx)).reshape(ty, t, tx, t).sum(axis=(1, 3))
-    syy = (pad(gy * gy)).reshape(ty, t, tx, t).sum(axis=(1, 3))
-    sxy = (pad(gx * gy)).reshape(ty, t, tx, t).sum(axis=(1, 3))
-    tr = sxx + syy
-    det = sxx * syy - sxy * sxy
-    disc = np.sqrt(np.maximum(tr * tr / 4 - det, 0))
-    lmin, lmax = tr / 2 - disc, tr / 2 + disc
-    return lmin > floor * np.maximum(lmax, 1e-30) * 1e3
-
-
 def check_align(raw, dev, ref=0, tile=16, white_level=4095, **kw):
     raw_np = raw.numpy()
     ap = hm.AlignParams(tile=tile, **kw)
     g_motion, g_int = hm.align(raw.to(dev), ref, ap, with_int=True, white_level=white_level)
-    mi, mf, fl, _ = oracle.align(raw_np, ref=ref, tile=tile, n_levels=ap.n_levels, radius=ap.radius,
-                                 lk_iters=ap.lk_iters)
-    g_int = g_int.cpu().numpy()
-    g_motion = g_motion.cpu().numpy()
-    assert np.array_equal(g_int, mi), "integer block matching differs"
-    # skipped (ill-conditioned) tiles are exactly 2u on both sides
-    sk = fl.astype(bool)
-    assert np.array_equal(g_motion[sk], (2 * mi[sk]).astype(np.float32))
-    good = lk_conditioned(raw_np, ref, tile)[None].repeat(raw_np.shape[0], 0) & ~sk
-    err = np.abs(g_motion - mf).max(axis=-1)
-    assert err[good].max() <= 1e-3, f"LK max err {err[good].max()} on conditioned tiles"
-    return mf.astype(np.float32)
+    return assert_motion_matches_oracle(g_int.cpu().numpy(), g_motion.cpu().numpy(), raw_np, ref, tile,
+                                        n_levels=ap.n_levels, radius=ap.radius, lk_iters=ap.lk_iters)
 
 
 # --------------------------------------------------------------------------------------
@@ -215,18 +162,12 @@ def test_merge_rejects_bad_arguments(dev, tiny_burst):
 
 
 # --------------------------------------------------------------------------------------
-# full-size workloads, sampled outputs
+# full-size workloads, whole images
 # --------------------------------------------------------------------------------------
-def sample_pixels(ho, wo, k, seed):
-    rng = np.random.default_rng(seed)
-    xy = np.stack([rng.integers(0, wo, k), rng.integers(0, ho, k)], axis=1)
-    edge = [(0, 0), (wo - 1, 0), (0, ho - 1), (wo - 1, ho - 1), (wo // 2, 0), (0, ho // 2), (wo - 1, ho // 2),
-            (wo // 2, ho - 1)]
-    return np.concatenate([np.array(edge), xy]).astype(np.int32)
-
-
-@pytest.mark.parametrize("config,k", [("12mp", 3000), ("sr15", 1500)])
-def test_full_size_sampled(dev, config, k):
+@pytest.mark.parametrize("config", ["12mp", "sr15"])
+def test_full_size_whole_image(dev, config):
+    # 12 MP x 8 at 1x and 12 MP x 15 at 2x (48.8 M output pixels): every output pixel of
+    # the GPU merge against the oracle's, given the same float32 motion
     b = burstgen.make_burst(config, device=dev)
     raw = b["raw"]
     raw_np = raw.cpu().numpy()
@@ -234,14 +175,8 @@ def test_full_size_sampled(dev, config, k):
     p = params_of(b)
     scale = b["scale"]
     rgb = hm.merge(raw, torch.from_numpy(mv).to(dev), p, scale).cpu().numpy()
-    ho, wo = rgb.shape[1:]
-    xy = sample_pixels(ho, wo, k, seed=5)
-    ref = oracle.merge_pixels(raw_np, mv, oparams(p), xy, scale=scale)
-    got = rgb[:, xy[:, 1], xy[:, 0]].T
-    err = np.abs(got.astype(np.float64) - ref)
-    assert np.isfinite(got).all()
-    assert err.max(axis=0).max() <= MAX_ABS, f"max {err.max(axis=0)}"
-    assert (err.mean(axis=0) <= MEAN_ABS).all(), f"mean {err.mean(axis=0)}"
+    ref = oracle.merge(raw_np, mv, oparams(p), scale=scale)
+    assert_merge_close(rgb, ref, config)
 
 
 # --------------------------------------------------------------------------------------

@@ -77,7 +77,8 @@ def test_motion_gradients_match_central_differences():
             continue
         step = float(mp[f, y, x, c]) - float(mm[f, y, x, c])
         fd = (loss(raw, mp, p, g, scale) - loss(raw, mm, p, g, scale)) / step
-        assert gm[f, y, x, c] == pytest.approx(fd, rel=2e-3, abs=2e-3 * (abs(gm).max())), (f, y, x, c, gm[f, y, x, c], fd)
+        # per element, 1e-3 relative (the gradient bar); the FP64 differences agree to ~3e-6
+        assert gm[f, y, x, c] == pytest.approx(fd, rel=1e-3, abs=1e-12), (f, y, x, c, gm[f, y, x, c], fd)
         checked += 1
     assert checked >= 15
     assert np.all(gm[0] == 0)
