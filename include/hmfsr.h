@@ -201,6 +201,19 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
  * stops early and the outputs are incomplete; the device stays usable). */
 hmfsr_status hmfsr_batch_wait(hmfsr_batch_plan plan, void *ws, void *stream);
 
+/* Per-stage profile of the persistent kernel (a diagnostic; off by default).  With
+ * `enable` != 0 the next runs' persistent kernel has each block's lead thread add, per
+ * stage, the SM clock cycles it spent waiting for the stages an item depends on and the
+ * cycles the item ran, and count the items (the graph is captured again when the
+ * setting changes; the graph mode records nothing).  hmfsr_batch_stage_profile copies
+ * the last run's counters from workspace `ws` to the host array out[n_out], n_out >= 3 x
+ * 14: for stage s = 0..13 (luminance, preparation, pyramid levels 1-3, block matching on
+ * levels 3-0, Lucas-Kanade, motion prior, robustness, accumulation, unused) out[3 s] wait
+ * cycles, out[3 s + 1] run cycles, out[3 s + 2] items; it synchronises `stream`. */
+hmfsr_status hmfsr_batch_set_profile(hmfsr_batch_plan plan, int enable);
+hmfsr_status hmfsr_batch_stage_profile(hmfsr_batch_plan plan, const void *ws, unsigned long long *out, int n_out,
+                                       void *stream);
+
 /* The integer block-matching vectors (Sec. 3.2, level 0, in half-res px) that the last
  * run of the plan on workspace `ws` computed for burst `burst`: int32
  * [n_frames][TY][TX][2] into motion_int_dev (4-byte aligned, caller-owned), as
@@ -224,10 +237,11 @@ hmfsr_status hmfsr_batch_configure(hmfsr_batch_plan plan, int merge_tile_w, int 
 hmfsr_status hmfsr_batch_set_mode(hmfsr_batch_plan plan, int streams);
 
 /* Autotuner: times the batch on the given buffers for 8 candidates -- the persistent
- * kernel with accumulation tiles 32x4 / 16x8 and register budgets 64 / 80 / 128 (the
- * stage-major queue), and the per-burst graph on 1, 2, 4 and 8 branches -- keeps the
- * fastest in the plan and returns its time (ms) in *best_ms and every candidate's time
- * in tune_log[8] (both nullable).  Overwrites the outputs. */
+ * kernel at 128 registers per thread with accumulation tiles 32x4 and 16x8 (for scales
+ * other than 1; scale 1 always takes 2 x 2 pixel blocks), at 80 and at 64 registers
+ * (32x4), and at 128 registers with the wavefront queue; and the per-burst graph on 2, 4
+ * and 8 branches -- keeps the fastest in the plan and returns its time (ms) in *best_ms
+ * and every candidate's time in tune_log[8] (both nullable).  Overwrites the outputs. */
 hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *bursts_dev, float *const *motion_dev,
                               float *const *rgb_dev, void *ws, size_t ws_bytes, void *stream, float *best_ms,
                               float *tune_log);

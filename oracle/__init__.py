@@ -32,6 +32,17 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_sanitized(path: str) -> str:
+    """Compile the oracle with AddressSanitizer and UndefinedBehaviorSanitizer (every
+    report fatal) into `path`; a test runs the oracle's pins against it in a process
+    that preloads the ASan runtime and points HMFSR_ORACLE_LIB at it."""
+    cmd = ["gcc", "-O1", "-g", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer",
+           "-shared", "-o", str(path), _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    return str(path)
+
+
 class _Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
@@ -74,8 +85,9 @@ class MergeParams:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        # HMFSR_ORACLE_LIB: an oracle built elsewhere (the sanitizer build of the tests)
+        path = os.environ.get("HMFSR_ORACLE_LIB") or build()
+        L = ctypes.CDLL(path)
         P = ctypes.POINTER
         u16p, i32p, f32p, f64p = P(ctypes.c_uint16), P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_double)
         ci = ctypes.c_int

@@ -592,6 +592,23 @@ class BatchPlan:
             self.wait(stream)
         return rgbs
 
+    STAGES = ("luminance", "preparation", "pyramid 1", "pyramid 2", "pyramid 3", "matching 3", "matching 2",
+              "matching 1", "matching 0", "lucas-kanade", "motion prior", "robustness", "accumulation")
+
+    def set_profile(self, enable: bool = True):
+        """Per-stage cycle counters in the persistent kernel (hmfsr_batch_set_profile)."""
+        _lib.check(self._L.hmfsr_batch_set_profile(self._h, int(enable)), "hmfsr_batch_set_profile")
+
+    def stage_profile(self, stream=None) -> dict:
+        """{stage: (wait cycles, run cycles, items)} of the last profiled persistent run."""
+        if self.ws is None:
+            raise RuntimeError("run the plan first")
+        n = 3 * 14
+        out = (ctypes.c_ulonglong * n)()
+        _lib.check(self._L.hmfsr_batch_stage_profile(self._h, _ptr(self.ws), out, n, _stream(self.ws.device, stream)),
+                   "hmfsr_batch_stage_profile")
+        return {name: (int(out[3 * s]), int(out[3 * s + 1]), int(out[3 * s + 2])) for s, name in enumerate(self.STAGES)}
+
     def vectors(self, k: int, stream=None) -> torch.Tensor:
         """Integer block-matching vectors (level 0, half-res px) of burst k from the last
         run: int32 [n, TY, TX, 2] (hmfsr_batch_vectors)."""
@@ -613,9 +630,9 @@ class BatchPlan:
         _lib.check(self._L.hmfsr_batch_configure(self._h, merge_tile_w, ctas_per_sm, regs_variant, queue_order,
                                                  spin_limit, int(inject_stall)), "hmfsr_batch_configure")
 
-    TUNE_CANDIDATES = ("persistent 32x4 64reg", "persistent 16x8 64reg", "persistent 32x4 80reg",
-                       "persistent 32x4 128reg", "graph 1 branch", "graph 2 branches", "graph 4 branches",
-                       "graph 8 branches")
+    TUNE_CANDIDATES = ("persistent 32x4 128reg", "persistent 16x8 128reg", "persistent 32x4 80reg",
+                       "persistent 32x4 64reg", "persistent 32x4 128reg wavefront", "graph 2 branches",
+                       "graph 4 branches", "graph 8 branches")
 
     def set_mode(self, streams: int):
         """0: the one persistent kernel; k > 0: graph of per-burst kernels on k branches."""

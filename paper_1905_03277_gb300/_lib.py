@@ -89,7 +89,8 @@ PIPE_FP32_FMA, PIPE_MUFU_EX2 = 0, 1
 NOISE_LEVELS = 129
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
-           "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_vectors", "hmfsr_batch_configure",
+           "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_vectors",
+           "hmfsr_batch_set_profile", "hmfsr_batch_stage_profile", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
            "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit", "hmfsr_merge_ex",
            "hmfsr_pipe_probe", "hmfsr_status_string", "hmfsr_version")
@@ -98,11 +99,12 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libhmfsr.so; raises if it is missing (there is no fallback path)."""
+    """Load libhmfsr.so (or `path`, or the file HMFSR_LIB names); raises if it is missing
+    (there is no fallback path)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or os.environ.get("HMFSR_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libhmfsr.so not found at {path}: run paper_1905_03277_gb300.build() first")
     L = ctypes.CDLL(path)
@@ -133,6 +135,10 @@ def load(path: str | None = None):
     L.hmfsr_batch_run.restype = ci
     L.hmfsr_batch_wait.argtypes = [vp, vp, vp]
     L.hmfsr_batch_wait.restype = ci
+    L.hmfsr_batch_set_profile.argtypes = [vp, ci]
+    L.hmfsr_batch_set_profile.restype = ci
+    L.hmfsr_batch_stage_profile.argtypes = [vp, vp, P(ctypes.c_ulonglong), ci, vp]
+    L.hmfsr_batch_stage_profile.restype = ci
     L.hmfsr_batch_vectors.argtypes = [vp, vp, ci, vp, vp]
     L.hmfsr_batch_vectors.restype = ci
     L.hmfsr_batch_configure.argtypes = [vp, ci, ci, ci, ci, ci, ci]

@@ -118,6 +118,7 @@ static void launch_quadfit(const Geom &g, const AlignLevels &L, float *motion, i
 
 cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p,
                                  const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s) {
+    StageRange range("hmfsr align with the quadratic-fit subpixel step");
     hmfsr_align_params q = p;
     q.lk_iters = 0;  // the search's vectors; the fit below replaces the Lucas-Kanade step
     cudaError_t e = launch_align(burst, g, q, L, motion, motion_int, s);
@@ -134,6 +135,7 @@ cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmf
 
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s) {
+    StageRange range("hmfsr align: pyramid, block matching, Lucas-Kanade");
     const int n = g.n;
     // levels 0 and 1 in one pass over the raw burst; the coarser levels from level 1
     const bool two = L.n_levels > 1;

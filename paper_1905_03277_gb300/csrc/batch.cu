@@ -119,7 +119,9 @@ __device__ __host__ inline int stage_subitems(const BatchBurst &b, int s, int mw
         case S_LK: return div_up(b.L.lty[0] * b.L.ltx[0], kLkTiles) * g.n;
         case S_STRENGTH: return div_up(g.n * g.ty * g.tx, kBatchThreads);
         case S_ROB: return div_up(g.wh, 4 * stage::kRobOut) * div_up(g.hh, stage::kRobStrip) * (g.n - 1);
-        case S_MERGE: return div_up(b.wo, mw) * div_up(b.ho, mh);
+        case S_MERGE:  // scale 1: blocks of 32 x 16 pixels in 2 x 2 quads (merge_quad1)
+            return b.snum == b.sden ? div_up(b.wo, stage::kQuadW) * div_up(b.ho, 8 * stage::kQuadNY)
+                                    : div_up(b.wo, mw) * div_up(b.ho, mh);
         default: return 0;
     }
 }
@@ -206,6 +208,16 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
             break;
         }
         case S_MERGE: {
+            if (b.snum == b.sden) {
+                // the per-burst kernel's layout: 4 warps of 8 x 4 threads of 2 x kQuadNY pixels
+                constexpr int NY = stage::kQuadNY;
+                const int nx = div_up(b.wo, stage::kQuadW), by = k / nx, bx = k - by * nx;
+                const int w = tid >> 5, lane = tid & 31;
+                const int qx = (w & 1) * 8 + (lane & 7), qy = (w >> 1) * 4 + (lane >> 3);
+                stage::merge_quad1<false, NY>(b.burst, b.P.geo, b.g, b.P.kern, b.P.rhat, b.rgb, nullptr,
+                                              bx * stage::kQuadW + 2 * qx, by * 8 * NY + NY * qy);
+                break;
+            }
             const int nx = div_up(b.wo, mw);
             const int by = k / nx, bx = k - by * nx;
             const int X = bx * mw + tid % mw, Y = by * mh + tid / mw;
@@ -240,12 +252,16 @@ __device__ __forceinline__ void add_release(int *p, int v) {
 
 constexpr int kMaxCachedBursts = 256;
 
-// ctrl[0]: next queue position; ctrl[1]: status (0 or HMFSR_ERR_TIMEOUT)
+// ctrl[0]: next queue position; ctrl[1]: status (0 or HMFSR_ERR_TIMEOUT).
+// prof (nullable): per stage {cycles waiting for dependencies, cycles running items,
+// items}, summed over the blocks by their lead thread (SM clock cycles).
 template <int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch(const BatchBurst *__restrict__ bursts, const Segment *__restrict__ segs, int nseg, int total,
-            int *ctrl, int *done, const int *__restrict__ totals, int mw, int mh, int spin_limit) {
+            int *ctrl, int *done, const int *__restrict__ totals, int mw, int mh, int spin_limit,
+            unsigned long long *prof) {
     __shared__ int s_item, s_next, s_ok, s_seg;
+    __shared__ long long s_t1;
     __shared__ unsigned int s_ready[kMaxCachedBursts];  // per burst: bit s set once stage s is complete
     const int tid = threadIdx.x;
     for (int i = tid; i < kMaxCachedBursts; i += kBatchThreads) s_ready[i] = 0u;
@@ -255,6 +271,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     }
     for (;;) {
         if (tid == 0) {
+            const long long t0 = prof ? clock64() : 0;
             // take the prefetched position and fetch the following one while this item runs
             const int st = *(volatile int *)&ctrl[1];
             const int item = (st != 0) ? total : s_next;
@@ -286,6 +303,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
                     if (ok) ready |= 1u << d;
                 }
                 if (b < kMaxCachedBursts) s_ready[b] = ready;
+                if (prof) {
+                    s_t1 = clock64();
+                    atomicAdd(prof + 3 * sidx, (unsigned long long)(s_t1 - t0));
+                }
             }
             s_ok = ok;
         }
@@ -296,7 +317,13 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         const int b = sg.burst, s = sg.stage, k = item - sg.first;
         run_item(bursts[b], s, k, tid, mw, mh);
         __syncthreads();
-        if (tid == 0) add_release(&done[b * S_COUNT + s], 1);
+        if (tid == 0) {
+            add_release(&done[b * S_COUNT + s], 1);
+            if (prof) {
+                atomicAdd(prof + 3 * s + 1, (unsigned long long)(clock64() - s_t1));
+                atomicAdd(prof + 3 * s + 2, 1ull);
+            }
+        }
     }
 }
 
@@ -316,13 +343,21 @@ struct hmfsr_batch_plan_t {
     std::vector<Segment> segs;
     std::vector<int> totals;
     int total = 0;
-    size_t table_off = 0, seg_off = 0, tot_off = 0, done_off = 0, ctrl_off = 0, ws_bytes = 0;
+    size_t table_off = 0, seg_off = 0, tot_off = 0, done_off = 0, ctrl_off = 0, prof_off = 0, ws_bytes = 0;
+    int profile = 0;  // the persistent kernel sums per-stage cycles (hmfsr_batch_set_profile)
     int mw = 32, mh = 4, ctas_per_sm = 0;  // accumulation item shape, blocks per SM (0: all that fit)
     int regs_variant = 1;                  // kernel build: 0 = 128, 1 = 80, 2 = 64 registers per thread
     int mode = 0;                          // 0: one persistent kernel; k > 0: graph of per-burst kernels on k streams
     int order = 0;                         // queue: 0 = stage-major, 1 = burst-major
     int spin_limit = 1 << 22;
     int inject_stall = 0;
+    // device tables of the persistent mode: uploaded from pinned staging when the burst
+    // pointers, the workspace or the queue change, never on a replay with the same ones
+    void *staging = nullptr;       // pinned host copy of table + queue + totals
+    size_t staging_bytes = 0;
+    cudaEvent_t staged = nullptr;  // the last upload from staging has been copied
+    bool tables_valid = false;     // the device tables match the current pointers and queue
+    const void *tables_ws = nullptr;
     // captured run
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -380,6 +415,7 @@ void build_queue(hmfsr_batch_plan_t *p) {
 }
 
 void drop_graph(hmfsr_batch_plan_t *p) {
+    p->tables_valid = false;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     p->exec = nullptr;
@@ -434,6 +470,7 @@ hmfsr_status hmfsr_batch_plan_create(const hmfsr_burst_desc *descs, int n_bursts
     p->tot_off = off; off = align256(off + tot_bytes);
     p->done_off = off; off = align256(off + tot_bytes);
     p->ctrl_off = off; off = align256(off + 2 * sizeof(int));
+    p->prof_off = off; off = align256(off + 3 * S_COUNT * sizeof(unsigned long long));
     for (int b = 0; b < n_bursts; ++b) {
         BatchBurst &bb = p->host[b];
         memset(&bb, 0, sizeof(bb));
@@ -511,9 +548,12 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
     if (!plan || !bursts_dev || !rgb_dev) return HMFSR_ERR_INVALID_ARG;
     if (!ws || ws_bytes < plan->ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 255)) return HMFSR_ERR_WORKSPACE;
     char *base = static_cast<char *>(ws);
+    bool changed = !plan->tables_valid || plan->tables_ws != ws;
     for (int b = 0; b < plan->nb; ++b) {
         if (!bursts_dev[b] || !rgb_dev[b] || (reinterpret_cast<uintptr_t>(bursts_dev[b]) & 3)) return HMFSR_ERR_INVALID_ARG;
         BatchBurst &bb = plan->host[b];
+        const float *old_motion = bb.motion;
+        changed = changed || bb.burst != bursts_dev[b] || bb.rgb != rgb_dev[b];
         bb.burst = bursts_dev[b];
         bb.rgb = rgb_dev[b];
         size_t off = plan->burst_off[b];
@@ -534,6 +574,7 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
         float *own_motion = reinterpret_cast<float *>(base + off);
         bb.motion = (motion_dev && motion_dev[b]) ? motion_dev[b] : own_motion;
         if (reinterpret_cast<uintptr_t>(bb.motion) & 7) return HMFSR_ERR_INVALID_ARG;
+        changed = changed || bb.motion != old_motion;
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (plan->mode > 0) {
@@ -588,17 +629,37 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
         }
         return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? HMFSR_OK : HMFSR_ERR_CUDA;
     }
-    // tables (pointers may change between runs); the copies complete before returning
-    if (cudaMemcpyAsync(base + plan->table_off, plan->host.data(), sizeof(BatchBurst) * plan->nb,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(base + plan->seg_off, plan->segs.data(), sizeof(Segment) * plan->segs.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(base + plan->tot_off, plan->totals.data(), sizeof(int) * plan->totals.size(),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return HMFSR_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return HMFSR_ERR_CUDA;
+    // tables: uploaded when the pointers, the workspace or the queue changed since the
+    // last upload, as one copy from pinned staging on the stream (ordered before the
+    // kernel); the host waits only if the previous upload from staging is still pending
+    if (changed) {
+        const size_t tb = sizeof(BatchBurst) * plan->nb, sb = sizeof(Segment) * plan->segs.size();
+        const size_t cb = sizeof(int) * plan->totals.size();
+        const size_t need = plan->tot_off + cb;  // table, queue and totals, as laid out in ws
+        if (plan->staging_bytes < need) {
+            if (plan->staged && cudaEventSynchronize(plan->staged) != cudaSuccess) return HMFSR_ERR_CUDA;
+            if (plan->staging) cudaFreeHost(plan->staging);
+            plan->staging = nullptr;
+            plan->staging_bytes = 0;
+            if (cudaHostAlloc(&plan->staging, need, cudaHostAllocDefault) != cudaSuccess) return HMFSR_ERR_CUDA;
+            plan->staging_bytes = need;
+        }
+        if (!plan->staged && cudaEventCreateWithFlags(&plan->staged, cudaEventDisableTiming) != cudaSuccess)
+            return HMFSR_ERR_CUDA;
+        if (cudaEventSynchronize(plan->staged) != cudaSuccess) return HMFSR_ERR_CUDA;
+        char *st = static_cast<char *>(plan->staging);
+        memcpy(st + plan->table_off, plan->host.data(), tb);
+        memcpy(st + plan->seg_off, plan->segs.data(), sb);
+        memcpy(st + plan->tot_off, plan->totals.data(), cb);
+        if (cudaMemcpyAsync(base, st, need, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaEventRecord(plan->staged, s) != cudaSuccess)
+            return HMFSR_ERR_CUDA;
+        plan->tables_valid = true;
+        plan->tables_ws = ws;
+    }
     // persistent grid: the blocks that fit on the device (or the tuned count per SM)
-    using KernelFn = void (*)(const BatchBurst *, const Segment *, int, int, int *, int *, const int *, int, int, int);
+    using KernelFn = void (*)(const BatchBurst *, const Segment *, int, int, int *, int *, const int *, int, int, int,
+                              unsigned long long *);
     const KernelFn kernel = plan->regs_variant == 0 ? k_batch<4> : (plan->regs_variant == 1 ? k_batch<6> : k_batch<8>);
     int dev = 0, nsm = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -612,13 +673,15 @@ hmfsr_status hmfsr_batch_run(hmfsr_batch_plan plan, const uint16_t *const *burst
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return HMFSR_ERR_CUDA;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const size_t ctr_bytes = (size_t)(plan->ctrl_off - plan->done_off) + 2 * sizeof(int);
+            // completion counters, control words and the stage profile start at zero
+            const size_t ctr_bytes = (size_t)(plan->prof_off - plan->done_off) + 3 * S_COUNT * sizeof(unsigned long long);
             cudaMemsetAsync(base + plan->done_off, 0, ctr_bytes, cap);
             kernel<<<grid, kBatchThreads, 0, cap>>>(
                 reinterpret_cast<const BatchBurst *>(base + plan->table_off),
                 reinterpret_cast<const Segment *>(base + plan->seg_off), (int)plan->segs.size(), plan->total,
                 reinterpret_cast<int *>(base + plan->ctrl_off), reinterpret_cast<int *>(base + plan->done_off),
-                reinterpret_cast<const int *>(base + plan->tot_off), plan->mw, plan->mh, plan->spin_limit);
+                reinterpret_cast<const int *>(base + plan->tot_off), plan->mw, plan->mh, plan->spin_limit,
+                plan->profile ? reinterpret_cast<unsigned long long *>(base + plan->prof_off) : nullptr);
             e = cudaStreamEndCapture(cap, &plan->graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
@@ -652,6 +715,24 @@ hmfsr_status hmfsr_batch_wait(hmfsr_batch_plan plan, void *ws, void *stream) {
     return status == 0 ? HMFSR_OK : (hmfsr_status)status;
 }
 
+hmfsr_status hmfsr_batch_set_profile(hmfsr_batch_plan plan, int enable) {
+    if (!plan) return HMFSR_ERR_INVALID_ARG;
+    plan->profile = enable ? 1 : 0;
+    drop_graph(plan);
+    return HMFSR_OK;
+}
+
+hmfsr_status hmfsr_batch_stage_profile(hmfsr_batch_plan plan, const void *ws, unsigned long long *out, int n_out,
+                                       void *stream) {
+    if (!plan || !ws || !out || n_out < 3 * (int)S_COUNT) return HMFSR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(out, static_cast<const char *>(ws) + plan->prof_off, 3 * S_COUNT * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return HMFSR_ERR_CUDA;
+    return HMFSR_OK;
+}
+
 hmfsr_status hmfsr_batch_vectors(hmfsr_batch_plan plan, const void *ws, int burst, int32_t *motion_int_dev,
                                  void *stream) {
     if (!plan || !ws || !motion_int_dev || burst < 0 || burst >= plan->nb ||
@@ -673,8 +754,8 @@ hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *burs
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HMFSR_ERR_CUDA;
     // candidates: {mode, merge tile width, register variant, queue order}
-    static const int kCand[][4] = {{0, 32, 2, 0}, {0, 16, 2, 0}, {0, 32, 1, 0}, {0, 32, 0, 0},
-                                   {1, 32, 2, 0}, {2, 32, 2, 0}, {4, 32, 2, 0}, {8, 32, 2, 0}};
+    static const int kCand[][4] = {{0, 32, 0, 0}, {0, 16, 0, 0}, {0, 32, 1, 0}, {0, 32, 2, 0},
+                                   {0, 32, 0, 2}, {2, 32, 0, 0}, {4, 32, 0, 0}, {8, 32, 0, 0}};
     float best = 1e30f;
     int best_i = 0;
     hmfsr_status st = HMFSR_OK;
@@ -708,6 +789,11 @@ hmfsr_status hmfsr_batch_tune(hmfsr_batch_plan plan, const uint16_t *const *burs
 void hmfsr_batch_free(hmfsr_batch_plan plan) {
     if (!plan) return;
     drop_graph(plan);
+    if (plan->staged) {
+        cudaEventSynchronize(plan->staged);
+        cudaEventDestroy(plan->staged);
+    }
+    if (plan->staging) cudaFreeHost(plan->staging);
     delete plan;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hmfsr.h"
@@ -47,6 +48,16 @@ __device__ __forceinline__ float fast_sqrt(float x) {
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// A named NVTX range over the host code that enqueues one stage's launches, so that a
+// profiler's timeline groups the kernels by stage (header-only NVTX; without a tool
+// attached a push or pop is one indirect call).
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange &) = delete;
+    StageRange &operator=(const StageRange &) = delete;
+};
 
 // ---------------------------------------------------------------------------------------
 // geometry of one burst
@@ -107,7 +118,7 @@ cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *ome
 
 // adjoint of the merge: buffers beyond the forward planes
 struct BwdPlanes {
-    float4 *shape;          // [n][hh*wh] {A, sqrt(l1_norm), cos 2t, sin 2t}
+    float4 *shape;          // [n][hh*wh][4] per texel: d k_across / d p, d k_along / d p, e1 e1^T
     float4 *rb;             // [n][hh*wh] {R, dR/dvx, dR/dvy, dR/ds2}
     unsigned char *flags;   // [n][hh*wh] bit 7: R unclamped; bits 0-4: argmin of the 5x5 window
     float *rhbar_tex;       // [n][hh*wh] dL/dRhat on base texels

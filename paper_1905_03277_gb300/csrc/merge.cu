@@ -59,12 +59,28 @@ __global__ void __launch_bounds__(kMergeW *kMergeH, 8) k_merge(const uint16_t *_
                                   blockIdx.x * kMergeW + threadIdx.x, blockIdx.y * kMergeH + threadIdx.y);
 }
 
+// scale 1: one thread per 2 x kQuadNY output pixels; 4 warps of 8 x 4 threads (16 x
+// 4 kQuadNY pixels, so that a warp lies inside one 16-pixel motion tile), the block
+// 32 x 8 kQuadNY pixels
+template <bool kDen, int NY>
+__global__ void __launch_bounds__(128, (NY == 2 ? 4 : 5)) k_merge_q1(const uint16_t *__restrict__ burst,
+                                                                    const int4 *__restrict__ geo, Geom g,
+                                                                    const float4 *__restrict__ kern,
+                                                                    const float *__restrict__ rhat_planes,
+                                                                    float *__restrict__ rgb, float *__restrict__ den_out) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qx = (w & 1) * 8 + (lane & 7), qy = (w >> 1) * 4 + (lane >> 3);
+    stage::merge_quad1<kDen, NY>(burst, geo, g, kern, rhat_planes, rgb, den_out, blockIdx.x * stage::kQuadW + 2 * qx,
+                                 blockIdx.y * 8 * NY + NY * qy);
+}
+
 template <bool kDen>
 static void launch_k_merge(dim3 grid, cudaStream_t s, const uint16_t *burst, const int4 *mv, const Geom &g,
                            const MergePlanes &P, int snum, int sden, int ho, int wo, float *rgb, float *den) {
     const dim3 block(kMergeW, kMergeH);
-    if (snum == 1 && sden == 1)
-        k_merge<kDen, 1, 1><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
+    if (snum == sden)
+        k_merge_q1<kDen, stage::kQuadNY><<<dim3(div_up(wo, stage::kQuadW), div_up(ho, 8 * stage::kQuadNY)), 128, 0, s>>>(
+            burst, mv, g, P.kern, P.rhat, rgb, den);
     else if (snum == 3 && sden == 2)
         k_merge<kDen, 3, 2><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den);
     else if (snum == 2 && sden == 1)
@@ -151,6 +167,7 @@ int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, i
 
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
+    StageRange range("hmfsr merge: kernel covariance and robustness");
     const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
                                     g.hh, 8, stage::kPrepStrip);
     k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
@@ -179,6 +196,7 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
 
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
                                int snum, int sden, float *rgb, float *den, cudaStream_t s) {
+    StageRange range("hmfsr merge: accumulation and normalisation");
     int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     dim3 grid(div_up(wo, kMergeW), div_up(ho, kMergeH));
     const int ntl = g.ty * g.tx;

@@ -172,6 +172,11 @@ def test_batch_vectors_rejects_bad_arguments(L):
     assert L.hmfsr_batch_vectors(p._h, ws, 0, ctypes.c_void_p(514), None) == -1   # misaligned
     with pytest.raises(RuntimeError):
         p.vectors(0)                                                 # not run yet
+    out = (ctypes.c_ulonglong * 42)()
+    assert L.hmfsr_batch_stage_profile(None, ws, out, 42, None) == -1
+    assert L.hmfsr_batch_stage_profile(p._h, None, out, 42, None) == -1
+    assert L.hmfsr_batch_stage_profile(p._h, ws, out, 41, None) == -1     # too short
+    assert L.hmfsr_batch_set_profile(None, 1) == -1
 
 
 def test_snr_tuning_through_the_abi_matches_the_oracle(L):

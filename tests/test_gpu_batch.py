@@ -86,6 +86,23 @@ def test_batch_matches_the_oracle(dev, batch):
         assert_merge_close(rgbs[k].cpu().numpy(), want, f"burst {k}: {n}x{h}x{w}, scale {sc}, ref {ref}")
 
 
+def test_batch_stage_profile(dev, batch):
+    # the persistent kernel's per-stage counters: every stage that has work records items
+    # and cycles, and profiling leaves the results unchanged
+    bursts, params, plain_rgb, _ = batch
+    plan = make_plan(bursts, params)
+    plan.set_mode(0)
+    plan.set_profile(True)
+    rgbs = plan.outputs(dev)
+    plan.run(bursts, rgbs, wait=True)
+    prof = plan.stage_profile()
+    for name in ("luminance", "preparation", "matching 0", "lucas-kanade", "robustness", "accumulation"):
+        wait, run, items = prof[name]
+        assert items > 0 and run > 0, (name, prof[name])
+    for k in range(len(CASES)):
+        assert torch.equal(rgbs[k], plain_rgb[k])
+
+
 def test_batch_timeout_is_reported_and_recovers(dev, batch):
     bursts, params, plain_rgb, _ = batch
     plan = make_plan(bursts, params)
