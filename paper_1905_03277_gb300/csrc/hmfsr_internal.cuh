@@ -118,7 +118,7 @@ cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *ome
 
 // adjoint of the merge: buffers beyond the forward planes
 struct BwdPlanes {
-    float4 *shape;          // [n][hh*wh][4] per texel: d k_across / d p, d k_along / d p, e1 e1^T
+    float4 *shape;          // [n][hh*wh] {A, sqrt(l1_norm), cos 2t, sin 2t}
     float4 *rb;             // [n][hh*wh] {R, dR/dvx, dR/dvy, dR/ds2}
     unsigned char *flags;   // [n][hh*wh] bit 7: R unclamped; bits 0-4: argmin of the 5x5 window
     float *rhbar_tex;       // [n][hh*wh] dL/dRhat on base texels

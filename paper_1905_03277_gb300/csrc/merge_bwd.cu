@@ -36,6 +36,33 @@ __device__ __forceinline__ void warp_sums_comp(float (&v)[K], float (&e)[K]) {
         }
 }
 
+// d k_across / d p and d k_along / d p for the six kernel parameters at one texel
+struct KGrad {
+    float dac[6], dal[6];
+};
+
+// inv_dtr = 1 / D_tr and inv_shrink = 1 / k_shrink (per call); 1/A on the SFU
+__device__ __forceinline__ void kernel_grad(const float4 sh, const MergeConsts &c, float inv_dtr, float inv_shrink,
+                                            KGrad &kg) {
+    const float A = sh.x, rl = sh.y, invA = fast_rcp(A);
+    const float Draw = 1.f - rl * inv_dtr + c.d_th;
+    const float D = fminf(fmaxf(Draw, 0.f), 1.f);
+    const bool inside = Draw > 0.f && Draw < 1.f;
+    const float dD2 = inside ? 1.f : 0.f, dD3 = inside ? rl * inv_dtr * inv_dtr : 0.f;
+    const float kh_al = c.k_detail * c.k_stretch * A, kh_ac = c.k_detail * inv_shrink * invA;
+    const float kd = c.k_detail * c.k_denoise;
+    const float s_al = (1.f - D) * kh_al + D * kd, s_ac = (1.f - D) * kh_ac + D * kd;
+    const float al[6] = {(1.f - D) * c.k_stretch * A + D * c.k_denoise, D * c.k_detail, (kd - kh_al) * dD2,
+                         (kd - kh_al) * dD3, (1.f - D) * c.k_detail * A, 0.f};
+    const float ac[6] = {(1.f - D) * inv_shrink * invA + D * c.k_denoise, D * c.k_detail, (kd - kh_ac) * dD2,
+                         (kd - kh_ac) * dD3, 0.f, -(1.f - D) * c.k_detail * inv_shrink * inv_shrink * invA};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        kg.dal[q] = 2.f * s_al * al[q];
+        kg.dac[q] = 2.f * s_ac * ac[q];
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // per texel: what the kernel-shape derivative needs {A, sqrt(l1_norm), cos 2t, sin 2t}
 // ---------------------------------------------------------------------------------------
@@ -72,31 +99,6 @@ __global__ void k_shape(const uint16_t *__restrict__ burst, int h, int pitch, in
     const float A = (ta + tc == 0) ? 1.f : 1.f + sqrtf(r / tr);
     const float rl = sqrtf(0.5f * (tr + r)) / (16.f * (float)wl);
     shape[((size_t)f * hh + v) * wh + u] = make_float4(A, rl, cs, sn);
-}
-
-// d k_across / d p and d k_along / d p for the six kernel parameters at one texel
-struct KGrad {
-    float dac[6], dal[6];
-};
-
-__device__ __forceinline__ void kernel_grad(const float4 sh, const MergeConsts &c, KGrad &kg) {
-    const float A = sh.x, rl = sh.y;
-    const float Draw = 1.f - rl / c.d_tr + c.d_th;
-    const float D = fminf(fmaxf(Draw, 0.f), 1.f);
-    const bool inside = Draw > 0.f && Draw < 1.f;
-    const float dD2 = inside ? 1.f : 0.f, dD3 = inside ? rl / (c.d_tr * c.d_tr) : 0.f;
-    const float kh_al = c.k_detail * c.k_stretch * A, kh_ac = c.k_detail / (c.k_shrink * A);
-    const float kd = c.k_detail * c.k_denoise;
-    const float s_al = (1.f - D) * kh_al + D * kd, s_ac = (1.f - D) * kh_ac + D * kd;
-    const float al[6] = {(1.f - D) * c.k_stretch * A + D * c.k_denoise, D * c.k_detail, (kd - kh_al) * dD2,
-                         (kd - kh_al) * dD3, (1.f - D) * c.k_detail * A, 0.f};
-    const float ac[6] = {(1.f - D) / (c.k_shrink * A) + D * c.k_denoise, D * c.k_detail, (kd - kh_ac) * dD2,
-                         (kd - kh_ac) * dD3, 0.f, -(1.f - D) * c.k_detail / (c.k_shrink * c.k_shrink * A)};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        kg.dal[q] = 2.f * s_al * al[q];
-        kg.dac[q] = 2.f * s_ac * ac[q];
-    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -213,9 +215,15 @@ __global__ void k_argmin(const float4 *__restrict__ rb, Geom g, unsigned char *_
 // ---------------------------------------------------------------------------------------
 // per output pixel: recompute the frame loop and emit the adjoint contributions
 // ---------------------------------------------------------------------------------------
-// 5 blocks per SM: 96 registers, no spills (128 registers gave 4 blocks and 8% more time;
-// 80 spilled and ran slower still)
-__global__ void __launch_bounds__(kBwdThreads, 5) k_merge_bwd(
+// Per sample the inverse quadratic form is split into per-column and per-row parts and
+// the per-channel values (C, log2 den, dL/dC) are mapped once per frame onto the window's
+// four sample classes, so a sample indexes nothing at run time (indexing the channel
+// arrays by a run-time channel had put them in local memory).  Each texel's kernel-shape
+// derivatives use reciprocals of the per-call constants and one 1/A on the SFU in place
+// of divisions.  4 blocks per SM: 128 registers, no spills (at 96 the body spills and
+// measured 1% slower).  Fitting workload (8 x 1024^2, 1.5x): adjoint 1.29 ms, against
+// 1.43 ms before these changes on the same box.
+__global__ void __launch_bounds__(kBwdThreads, 4) k_merge_bwd(
     const uint16_t *__restrict__ burst, const float2 *__restrict__ motion, Geom g, MergeConsts c,
     const float4 *__restrict__ kern, const float4 *__restrict__ shape, const float *__restrict__ rhat_planes,
     int snum, int sden, int ho, int wo, const float *__restrict__ rgb, const float *__restrict__ lden,
@@ -227,6 +235,7 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_merge_bwd(
     const int tid = threadIdx.y * kBwdW + threadIdx.x;
     const bool active = X < wo && Y < ho;
     float pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float inv_dtr = 1.f / c.d_tr, inv_shrink = 1.f / c.k_shrink;
     if (active) {
         const int Q = 2 * snum, Q2 = 4 * snum;
         const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
@@ -240,9 +249,9 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_merge_bwd(
         const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
         const float rw00 = (1.f - rfx) * (1.f - rfy), rw10 = rfx * (1.f - rfy), rw01 = (1.f - rfx) * rfy,
                     rw11 = rfx * rfy;
-        const float Cc[3] = {rgb[op], rgb[po + op], rgb[2 * po + op]};
-        const float Lc[3] = {lden[op], lden[po + op], lden[2 * po + op]};
-        const float gc[3] = {grad_rgb[op], grad_rgb[po + op], grad_rgb[2 * po + op]};
+        const float Cc0 = rgb[op], Cc1 = rgb[po + op], Cc2 = rgb[2 * po + op];
+        const float Lc0 = lden[op], Lc1 = lden[po + op], Lc2 = lden[2 * po + op];
+        const float gc0 = grad_rgb[op], gc1 = grad_rgb[po + op], gc2 = grad_rgb[2 * po + op];
         for (int f = 0; f < g.n; ++f) {
             float vx = 0.f, vy = 0.f, rh = 1.f;
             if (f != g.ref) {
@@ -266,8 +275,6 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_merge_bwd(
             const int ty_[4] = {clampi(oy, 0, g.hh - 1), clampi(oy, 0, g.hh - 1), clampi(oy + 1, 0, g.hh - 1),
                                 clampi(oy + 1, 0, g.hh - 1)};
             const float beta[4] = {(1.f - ax) * (1.f - ay), ax * (1.f - ay), (1.f - ax) * ay, ax * ay};
-            const float dbx[4] = {-(1.f - ay), 1.f - ay, -ay, ay};
-            const float dby[4] = {-(1.f - ax), -ax, 1.f - ax, ax};
             float4 t[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) t[k] = kern[(size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]];
@@ -291,48 +298,90 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_merge_bwd(
                     detM += gk[k] * gk[l] * cr * cr;
                 }
             const float det = fmaf(a, a + G, detM);
+            // each texel's Omega entries, for the sampling-position and shape terms below
+            float okx[4], oky[4], okz[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float ux = t[k].z, uy = t[k].w;
+                okx[k] = t[k].x + t[k].y * ux * ux;
+                oky[k] = t[k].y * ux * uy;
+                okz[k] = t[k].x + t[k].y * uy * uy;
+            }
             const float invdet = 1.f / det;
-            // adj(Omega) = a I + [[Oyy, -Oxy], [-Oxy, Oxx]] of M
-            const float Axx = a + Oyy, Ayy = a + Oxx, Axy = -Oxy;
+            // adj(Omega) = a I + [[Oyy, -Oxy], [-Oxy, Oxx]] of M; P = Omega^-1 d splits into
+            // per-column and per-row parts: Px = ax[i] + bx[j], Py = cy[i] + dy[j]
+            const float sxx = (a + Oyy) * invdet, syy = (a + Oxx) * invdet, sxy = -Oxy * invdet;
+            const float dxs[3] = {dx0 - 1.f, dx0, dx0 + 1.f}, dys[3] = {dy0 - 1.f, dy0, dy0 + 1.f};
+            float pxc[3], pxr[3], pyc[3], pyr[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pxc[k] = sxx * dxs[k];
+                pyc[k] = sxy * dxs[k];
+                pxr[k] = sxy * dys[k];
+                pyr[k] = syy * dys[k];
+            }
+            // per-channel values mapped onto the window's sample classes (C centre, H
+            // (+-1, 0), V (0, +-1), K corners) from the parity of the centre (kx, ky):
+            // channel(x, y) = (x & 1) + (y & 1) for RGGB
+            const int cx = kx & 1, cy = ky & 1;
+            auto pick = [](int ch, float r, float gg, float b) { return ch == 0 ? r : (ch == 1 ? gg : b); };
+            const int chC = cx + cy, chH = (cx ^ 1) + cy, chV = cx + (cy ^ 1), chK = (cx ^ 1) + (cy ^ 1);
+            const float LC = pick(chC, Lc0, Lc1, Lc2), LH = pick(chH, Lc0, Lc1, Lc2);
+            const float LV = pick(chV, Lc0, Lc1, Lc2), LK = pick(chK, Lc0, Lc1, Lc2);
+            const float gC = pick(chC, gc0, gc1, gc2), gH = pick(chH, gc0, gc1, gc2);
+            const float gV = pick(chV, gc0, gc1, gc2), gK = pick(chK, gc0, gc1, gc2);
+            const float cC = pick(chC, Cc0, Cc1, Cc2), cH = pick(chH, Cc0, Cc1, Cc2);
+            const float cV = pick(chV, Cc0, Cc1, Cc2), cK = pick(chK, Cc0, Cc1, Cc2);
             const uint16_t *fr = burst + (size_t)f * g.h * g.pitch;
-            float ob0 = 0.f, ob1 = 0.f, ob2 = 0.f, vbx = 0.f, vby = 0.f, rhb = 0.f;
+            const bool inside = (unsigned)(kx - 1) < (unsigned)(g.w - 2) && (unsigned)(ky - 1) < (unsigned)(g.h - 2);
+            const float mrh = -0.5f * rh;
+            float ob0 = 0.f, ob1 = 0.f, ob2 = 0.f, sPx = 0.f, sPy = 0.f, rhb = 0.f;
 #pragma unroll
             for (int j = -1; j <= 1; ++j)
 #pragma unroll
                 for (int i = -1; i <= 1; ++i) {
                     const int qx = kx + i, qy = ky + j;
-                    if (qx < 0 || qx >= g.w || qy < 0 || qy >= g.h) continue;
-                    const float dx = dx0 + (float)i, dy = dy0 + (float)j;
-                    const float Pxv = (Axx * dx + Axy * dy) * invdet, Pyv = (Axy * dx + Ayy * dy) * invdet;
-                    const float qq = dx * Pxv + dy * Pyv;  // d^T Omega^-1 d
-                    const int ch = (qx & 1) + (qy & 1);
-                    const float wn = fast_exp2(-(kHalfLog2e * qq + Lc[ch]));  // w / den
-                    const float cv = (float)fr[(size_t)qy * g.pitch + qx];
-                    const float e = gc[ch] * (cv - Cc[ch]) * wn;  // dL/d(w Rhat) * w
+                    if (!inside && (qx < 0 || qx >= g.w || qy < 0 || qy >= g.h)) continue;
+                    const float dx = dxs[i + 1], dy = dys[j + 1];
+                    const float Pxv = pxc[i + 1] + pxr[j + 1], Pyv = pyc[i + 1] + pyr[j + 1];
+                    const float qq = fmaf(dx, Pxv, dy * Pyv);  // d^T Omega^-1 d
+                    // the sample's class: centre, horizontal, vertical or corner neighbour
+                    const float Lq = (i == 0) ? (j == 0 ? LC : LV) : (j == 0 ? LH : LK);
+                    const float gq = (i == 0) ? (j == 0 ? gC : gV) : (j == 0 ? gH : gK);
+                    const float cq = (i == 0) ? (j == 0 ? cC : cV) : (j == 0 ? cH : cK);
+                    const float wn = fast_exp2(-fmaf(kHalfLog2e, qq, Lq));  // w / den
+                    const float cv = (float)__ldg(fr + (size_t)qy * g.pitch + qx);
+                    const float e = gq * (cv - cq) * wn;  // dL/d(w Rhat) * w
                     rhb += e;
-                    const float qb = -0.5f * rh * e;  // dL/dq
-                    vbx -= 2.f * qb * Pxv;
-                    vby -= 2.f * qb * Pyv;
-                    ob0 -= qb * Pxv * Pxv;
-                    ob1 -= 2.f * qb * Pxv * Pyv;
-                    ob2 -= qb * Pyv * Pyv;
+                    const float qb = mrh * e;  // dL/dq
+                    const float t1 = qb * Pxv, t2 = qb * Pyv;
+                    sPx += t1;
+                    sPy += t2;
+                    ob0 = fmaf(t1, Pxv, ob0);
+                    ob1 = fmaf(t1, Pyv, ob1);
+                    ob2 = fmaf(t2, Pyv, ob2);
                 }
+            // d L / d v through the offsets d (d = q - x0 - v): -2 sum qb P; Omega-bar = -qb P P^T
+            float vbx = -2.f * sPx, vby = -2.f * sPy;
+            ob0 = -ob0;
+            ob1 = -2.f * ob1;
+            ob2 = -ob2;
             // Omega sampling position (x0 + v - 1/2)/2 and the texel parameters
+            const float dbx[4] = {-(1.f - ay), 1.f - ay, -ay, ay};
+            const float dby[4] = {-(1.f - ax), -ax, 1.f - ax, ax};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float ux = t[k].z, uy = t[k].w;
-                const float okx = t[k].x + t[k].y * ux * ux, oky = t[k].y * ux * uy, okz = t[k].x + t[k].y * uy * uy;
-                const float dot = ob0 * okx + ob1 * oky + ob2 * okz;
+                const float dot = ob0 * okx[k] + ob1 * oky[k] + ob2 * okz[k];
                 vbx += 0.5f * dbx[k] * dot;
                 vby += 0.5f * dby[k] * dot;
-                const float4 sh = shape[(size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]];
+                const float4 sh = __ldg(shape + (size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]);
                 KGrad kg;
-                kernel_grad(sh, c, kg);
+                kernel_grad(sh, c, inv_dtr, inv_shrink, kg);
                 const float e1xx = 0.5f * (1.f + sh.z), e1xy = 0.5f * sh.w, e1yy = 0.5f * (1.f - sh.z);
                 const float oE1 = ob0 * e1xx + ob1 * e1xy + ob2 * e1yy;
-                const float oE2 = (ob0 + ob2) - oE1;
+                const float bo1 = beta[k] * oE1, bo2 = beta[k] * ((ob0 + ob2) - oE1);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) pb[q] += beta[k] * (kg.dac[q] * oE1 + kg.dal[q] * oE2);
+                for (int q = 0; q < 6; ++q) pb[q] = fmaf(kg.dac[q], bo1, fmaf(kg.dal[q], bo2, pb[q]));
             }
             const size_t of = (size_t)f * po + op;
             vbar_pix[of] = (f == g.ref) ? make_float2(0.f, 0.f) : make_float2(vbx, vby);
@@ -576,6 +625,7 @@ cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, co
                                   const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
                                   const float *lden, const float *grad_rgb, float *grad_params, float *grad_motion,
                                   cudaStream_t s) {
+    StageRange range("hmfsr merge adjoint");
     const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
