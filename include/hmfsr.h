@@ -340,6 +340,27 @@ enum { HMFSR_PIPE_FP32_FMA = 0, HMFSR_PIPE_MUFU_EX2 = 1 };
  * misaligned sink. */
 hmfsr_status hmfsr_pipe_probe(int pipe, int blocks, int iters, float *sink_dev, double *lane_ops, void *stream);
 
+/* ---- Checked build (the library compiled with -DHMFSR_CHECKED: a test build, not the
+ * default).  The paper has no counterpart; this is a memory-safety aid.  In that build
+ * every global load and store of the alignment and merge kernels (the entry points
+ * hmfsr_align, hmfsr_align_quadfit, hmfsr_merge and its variants _ex, _noise, _prepare,
+ * _accumulate, _stages and _static) is checked against the buffers of its call: the
+ * burst, motion, outputs, tables and the workspace the call needs.  An access outside
+ * all of them is not made (a load gives 0, a store is dropped) and the source line of
+ * the first such access goes to a device error word; nothing traps.  Calls that overlap
+ * on the GPU share the checker's state.  In the default build both functions return
+ * HMFSR_ERR_UNSUPPORTED.  ---- */
+
+/* *line = the error word (0: every checked access stayed inside its call's buffers);
+ * with reset != 0 the word is cleared.  Synchronises with the device (legacy default
+ * stream). */
+hmfsr_status hmfsr_check_status(int reset, int *line);
+
+/* Test hook: every workspace registered from now on is taken as `bytes` shorter than
+ * the call needs, so that the kernels' last workspace accesses count as outside (they
+ * are then not made).  0 restores the exact extent. */
+hmfsr_status hmfsr_check_shrink(size_t bytes);
+
 /* Human-readable name of a status code (static string). */
 const char *hmfsr_status_string(hmfsr_status s);
 

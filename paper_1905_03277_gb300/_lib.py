@@ -32,31 +32,57 @@ def _inputs():
     return files
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit for sm_103a (in parallel) and link libhmfsr.so."""
-    newest = max(os.path.getmtime(f) for f in _inputs())
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
-    os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
+CHECKED_LIB_PATH = os.path.join(PKG, "libhmfsr_checked.so")
+# the units whose kernels the checked build checks (alignment and merge entry points);
+# the others link unchanged from the default build
+CHECKED_SOURCES = ("api.cu", "align.cu", "merge.cu")
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
-        if verbose:
-            print(r.stdout, r.stderr)
-        return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+def _compile(nvcc, src, obj, extra, verbose):
+    cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    if verbose:
+        print(r.stdout, r.stderr)
+    return obj
+
+
+def _link(nvcc, objs, lib_path):
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
+    os.replace(tmp, lib_path)
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every translation unit for sm_103a (in parallel) and link libhmfsr.so.
+    With `checked`, also the checked test build (the alignment and merge units compiled
+    with -DHMFSR_CHECKED, the rest shared) into libhmfsr_checked.so, in the same pass.
+    Returns the default library's path."""
+    newest = max(os.path.getmtime(f) for f in _inputs())
+    need_default = force or not os.path.exists(LIB_PATH) or os.path.getmtime(LIB_PATH) < newest
+    need_checked = checked and (force or not os.path.exists(CHECKED_LIB_PATH) or
+                                os.path.getmtime(CHECKED_LIB_PATH) < newest)
+    if not need_default and not need_checked:
+        return LIB_PATH
+    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(BUILD + "_checked", exist_ok=True)
+    nvcc = _nvcc()
+    jobs = []
+    default_objs = {src: os.path.join(BUILD, os.path.splitext(src)[0] + ".o") for src in SOURCES}
+    checked_objs = {src: os.path.join(BUILD + "_checked", os.path.splitext(src)[0] + ".o") for src in CHECKED_SOURCES}
+    if need_default or not all(os.path.exists(o) for o in default_objs.values()):
+        jobs += [(src, default_objs[src], []) for src in SOURCES]
+    if need_checked:
+        jobs += [(src, checked_objs[src], ["-DHMFSR_CHECKED"]) for src in CHECKED_SOURCES]
+    with ThreadPoolExecutor(max(1, len(jobs))) as ex:
+        list(ex.map(lambda j: _compile(nvcc, j[0], j[1], j[2], verbose), jobs))
+    if need_default:
+        _link(nvcc, [default_objs[s] for s in SOURCES], LIB_PATH)
+    if need_checked:
+        _link(nvcc, [checked_objs[s] if s in checked_objs else default_objs[s] for s in SOURCES], CHECKED_LIB_PATH)
     return LIB_PATH
 
 
@@ -93,18 +119,23 @@ EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_merge_pr
            "hmfsr_batch_set_profile", "hmfsr_batch_stage_profile", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
            "hmfsr_noise_table", "hmfsr_merge_noise", "hmfsr_align_quadfit", "hmfsr_merge_ex",
-           "hmfsr_pipe_probe", "hmfsr_status_string", "hmfsr_version")
+           "hmfsr_pipe_probe", "hmfsr_check_status", "hmfsr_check_shrink", "hmfsr_status_string", "hmfsr_version")
 
 _lib = None
 
 
 def load(path: str | None = None):
-    """Load libhmfsr.so (or `path`, or the file HMFSR_LIB names); raises if it is missing
-    (there is no fallback path)."""
+    """Load libhmfsr.so (or `path`, or the file HMFSR_LIB names) once; raises if it is
+    missing (there is no fallback path)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or os.environ.get("HMFSR_LIB") or LIB_PATH
+    _lib = open_library(path or os.environ.get("HMFSR_LIB") or LIB_PATH)
+    return _lib
+
+
+def open_library(path: str):
+    """A library file opened with every entry point's signature set (not cached)."""
     if not os.path.exists(path):
         raise RuntimeError(f"libhmfsr.so not found at {path}: run paper_1905_03277_gb300.build() first")
     L = ctypes.CDLL(path)
@@ -169,7 +200,10 @@ def load(path: str | None = None):
     L.hmfsr_status_string.restype = ctypes.c_char_p
     L.hmfsr_version.argtypes = []
     L.hmfsr_version.restype = ctypes.c_char_p
-    _lib = L
+    L.hmfsr_check_status.argtypes = [ci, P(ci)]
+    L.hmfsr_check_status.restype = ci
+    L.hmfsr_check_shrink.argtypes = [sz]
+    L.hmfsr_check_shrink.restype = ci
     return L
 
 

@@ -32,7 +32,7 @@ __device__ __forceinline__ void gather3x3(const uint16_t *__restrict__ fr, int p
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int xx = kx - 1 + i;
-            rv[j][i] = (float)__ldg(fr + row + (kBorder ? clampi(xx, 0, w - 1) : xx));
+            rv[j][i] = (float)HMFSR_LDG(fr + row + (kBorder ? clampi(xx, 0, w - 1) : xx));
             const float qq = fmaf(Ex[i], dys[j], Ax[i] + Cy[j]);
             if (kBorder) q[j][i] = (yok && (unsigned)xx < (unsigned)w) ? qq : INFINITY;
             else q[j][i] = qq;
@@ -196,12 +196,12 @@ __device__ __forceinline__ void geo_entry(const float2 *__restrict__ motion, int
     if (i >= n * ntl) return;
     int4 e = make_int4(0, 0, 0, 0);
     if (i / ntl != ref) {
-        const float2 mv = motion[i];
+        const float2 mv = HMFSR_LD(motion + i);
         const int FX = floor_mul(Q, mv.x), FY = floor_mul(Q, mv.y);
         const float fQ = (float)Q;
         e = make_int4(FX, FY, __float_as_int(fmaf(fQ, mv.x, -(float)FX)), __float_as_int(fmaf(fQ, mv.y, -(float)FY)));
     }
-    geo[i] = e;
+    HMFSR_ST(geo + i, e);
 }
 
 // The quadratic form of Eq. 2 for Omega interpolated bilinearly (weights b0..b3) from
@@ -266,7 +266,7 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
     auto rhat_at = [&](int f) -> float {
         if (f == g.ref) return 1.f;
         const float *Rp = rhat_planes + (size_t)f * hw;
-        return fmaf(rw00, __ldg(Rp + r00), fmaf(rw10, __ldg(Rp + r10), fmaf(rw01, __ldg(Rp + r01), rw11 * __ldg(Rp + r11))));
+        return fmaf(rw00, HMFSR_LDG(Rp + r00), fmaf(rw10, HMFSR_LDG(Rp + r10), fmaf(rw01, HMFSR_LDG(Rp + r01), rw11 * HMFSR_LDG(Rp + r11))));
     };
 
     PixelAcc acc;
@@ -275,7 +275,7 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
     // frames in the order base frame, then the others; the next frame's geometry and
     // robustness are fetched while this one is merged
     int f_nx = g.ref;
-    int4 geo_nx = __ldg(geo_px + (size_t)f_nx * ntl);
+    int4 geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
     float rh_nx = 1.f;
     for (int it = 0; it < g.n; ++it) {
         const int f = f_nx;
@@ -283,7 +283,7 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         const float rh = rh_nx;
         if (it + 1 < g.n) {
             f_nx = (it + 1 <= g.ref) ? it : it + 1;
-            geo_nx = __ldg(geo_px + (size_t)f_nx * ntl);
+            geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
             rh_nx = rhat_at(f_nx);
         }
         if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
@@ -301,8 +301,8 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         const int ox0 = clampi(ox, 0, g.wh - 1), ox1 = clampi(ox + 1, 0, g.wh - 1);
         const int oy0 = clampi(oy, 0, g.hh - 1) * g.wh, oy1 = clampi(oy + 1, 0, g.hh - 1) * g.wh;
         const float4 *K = kern + (size_t)f * hw;
-        const float4 t0 = __ldg(K + (oy0 + ox0)), t1 = __ldg(K + (oy0 + ox1));
-        const float4 t2 = __ldg(K + (oy1 + ox0)), t3 = __ldg(K + (oy1 + ox1));
+        const float4 t0 = HMFSR_LDG(K + (oy0 + ox0)), t1 = HMFSR_LDG(K + (oy0 + ox1));
+        const float4 t2 = HMFSR_LDG(K + (oy1 + ox0)), t3 = HMFSR_LDG(K + (oy1 + ox1));
         const float b0 = (1.f - ofx) * (1.f - ofy), b1 = ofx * (1.f - ofy), b2 = (1.f - ofx) * ofy, b3 = ofx * ofy;
         float Bxx, Byy, Bxy2;
         omega_form(t0, t1, t2, t3, b0, b1, b2, b3, Bxx, Byy, Bxy2);
@@ -326,13 +326,13 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         accumulate_frame(q, rv, rh, ((kx ^ ky) & 1) != 0, (ky & 1) != 0, acc);
     }
     const size_t po = (size_t)ho * wo, o = (size_t)Y * wo + X;
-    rgb[o] = acc.numR / acc.denR;
-    rgb[po + o] = acc.numG / acc.denG;
-    rgb[2 * po + o] = acc.numB / acc.denB;
+    HMFSR_ST(rgb + o, acc.numR / acc.denR);
+    HMFSR_ST(rgb + po + o, acc.numG / acc.denG);
+    HMFSR_ST(rgb + 2 * po + o, acc.numB / acc.denB);
     if (kDen) {
-        den_out[o] = log2f(acc.denR) - acc.mR;
-        den_out[po + o] = log2f(acc.denG) - acc.mG;
-        den_out[2 * po + o] = log2f(acc.denB) - acc.mB;
+        HMFSR_ST(den_out + o, log2f(acc.denR) - acc.mR);
+        HMFSR_ST(den_out + po + o, log2f(acc.denG) - acc.mG);
+        HMFSR_ST(den_out + 2 * po + o, log2f(acc.denB) - acc.mB);
     }
 }
 
@@ -379,7 +379,7 @@ __device__ __forceinline__ void quad_omega(const QuadOmega<NY> &om, int pa, int 
         r1 = clampi(r1, 0, om.hh - 1);
     }
     const float4 *R0 = om.K + (size_t)r0 * om.wh, *R1 = om.K + (size_t)r1 * om.wh;
-    const float4 t0 = __ldg(R0 + c0), t1 = __ldg(R0 + c1), t2 = __ldg(R1 + c0), t3 = __ldg(R1 + c1);
+    const float4 t0 = HMFSR_LDG(R0 + c0), t1 = HMFSR_LDG(R0 + c1), t2 = HMFSR_LDG(R1 + c0), t3 = HMFSR_LDG(R1 + c1);
     const float ofx = om.fx[pa], ofy = om.fy[pb];
     const float b0 = (1.f - ofx) * (1.f - ofy), b1 = ofx * (1.f - ofy), b2 = (1.f - ofx) * ofy, b3 = ofx * ofy;
     omega_form(t0, t1, t2, t3, b0, b1, b2, b3, Bxx, Byy, Bxy2);
@@ -399,7 +399,7 @@ __device__ __forceinline__ void quad_block(const uint16_t *__restrict__ fr, int 
         const int yy = kBorder ? clampi(by + r, 0, h - 1) : by + r;
         const uint16_t *row = fr + (size_t)yy * pitch;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) rv[r][c] = (float)__ldg(row + (kBorder ? clampi(bx + c, 0, w - 1) : bx + c));
+        for (int c = 0; c < 4; ++c) rv[r][c] = (float)HMFSR_LDG(row + (kBorder ? clampi(bx + c, 0, w - 1) : bx + c));
     }
 }
 
@@ -476,7 +476,7 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
 #pragma unroll
         for (int j = 0; j <= NY; ++j)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) R[j][i] = __ldg(Rp + rr[j] + rc[i]);
+            for (int i = 0; i < 3; ++i) R[j][i] = HMFSR_LDG(Rp + rr[j] + rc[i]);
 #pragma unroll
         for (int p = 0; p < 2 * NY; ++p) {
             const int pa = p & 1, pb = p >> 1;
@@ -494,7 +494,7 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
     // frames in the order base frame, then the others; the next frame's geometry and
     // Rhat are fetched while this one is merged
     int f_nx = g.ref;
-    int4 geo_nx = __ldg(geo_q + (size_t)f_nx * ntl);
+    int4 geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
     float rh_nx[2 * NY];
     rhat_at(f_nx, rh_nx);
     for (int it = 0; it < g.n; ++it) {
@@ -505,7 +505,7 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
         for (int p = 0; p < 2 * NY; ++p) rh[p] = rh_nx[p];
         if (it + 1 < g.n) {
             f_nx = (it + 1 <= g.ref) ? it : it + 1;
-            geo_nx = __ldg(geo_q + (size_t)f_nx * ntl);
+            geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
             rhat_at(f_nx, rh_nx);
         }
         bool any = false;
@@ -568,15 +568,15 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
     for (int pb = 0; pb < NY; ++pb) {
         const size_t o = (size_t)(Y + pb) * wo + X;
         const PixelAcc &a0 = acc[2 * pb], &a1 = acc[2 * pb + 1];
-        *reinterpret_cast<float2 *>(rgb + o) = make_float2(a0.numR / a0.denR, a1.numR / a1.denR);
-        *reinterpret_cast<float2 *>(rgb + po + o) = make_float2(a0.numG / a0.denG, a1.numG / a1.denG);
-        *reinterpret_cast<float2 *>(rgb + 2 * po + o) = make_float2(a0.numB / a0.denB, a1.numB / a1.denB);
+        HMFSR_ST(reinterpret_cast<float2 *>(rgb + o), make_float2(a0.numR / a0.denR, a1.numR / a1.denR));
+        HMFSR_ST(reinterpret_cast<float2 *>(rgb + po + o), make_float2(a0.numG / a0.denG, a1.numG / a1.denG));
+        HMFSR_ST(reinterpret_cast<float2 *>(rgb + 2 * po + o), make_float2(a0.numB / a0.denB, a1.numB / a1.denB));
         if (kDen) {
-            *reinterpret_cast<float2 *>(den_out + o) = make_float2(log2f(a0.denR) - a0.mR, log2f(a1.denR) - a1.mR);
-            *reinterpret_cast<float2 *>(den_out + po + o) =
-                make_float2(log2f(a0.denG) - a0.mG, log2f(a1.denG) - a1.mG);
-            *reinterpret_cast<float2 *>(den_out + 2 * po + o) =
-                make_float2(log2f(a0.denB) - a0.mB, log2f(a1.denB) - a1.mB);
+            HMFSR_ST(reinterpret_cast<float2 *>(den_out + o), make_float2(log2f(a0.denR) - a0.mR, log2f(a1.denR) - a1.mR));
+            HMFSR_ST(reinterpret_cast<float2 *>(den_out + po + o),
+                     make_float2(log2f(a0.denG) - a0.mG, log2f(a1.denG) - a1.mG));
+            HMFSR_ST(reinterpret_cast<float2 *>(den_out + 2 * po + o),
+                     make_float2(log2f(a0.denB) - a0.mB, log2f(a1.denB) - a1.mB));
         }
     }
 }

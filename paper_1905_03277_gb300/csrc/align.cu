@@ -123,6 +123,7 @@ cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmf
     q.lk_iters = 0;  // the search's vectors; the fit below replaces the Lucas-Kanade step
     cudaError_t e = launch_align(burst, g, q, L, motion, motion_int, s);
     if (e != cudaSuccess) return e;
+    CheckedLaunches checked(s);
     switch (p.tile) {
         case 8: launch_quadfit<4>(g, L, motion, motion_int, s); break;
         case 16: launch_quadfit<8>(g, L, motion, motion_int, s); break;
@@ -136,6 +137,7 @@ cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmf
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s) {
     StageRange range("hmfsr align: pyramid, block matching, Lucas-Kanade");
+    CheckedLaunches checked(s);
     const int n = g.n;
     // levels 0 and 1 in one pass over the raw burst; the coarser levels from level 1
     const bool two = L.n_levels > 1;

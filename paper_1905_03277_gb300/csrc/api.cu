@@ -6,7 +6,51 @@
 
 using namespace hmfsr;
 
+#ifdef HMFSR_CHECKED
+// the checked build's error word: 0, or the source line of the first access that lay
+// outside every buffer of its call
+__device__ int g_check_err;
+#endif
+
 namespace {
+
+// the buffers of the entry-point call running on this host thread (checked build)
+thread_local CheckRanges t_check = {};
+size_t g_check_shrink = 0;  // test hook of the checked build: bytes taken off each registered workspace
+
+// For the duration of one entry-point call: the caller's buffers, as its kernels may read
+// and write them (checked build; nothing in the default build).
+struct CheckScope {
+#ifdef HMFSR_CHECKED
+    CheckScope() {
+        t_check = CheckRanges{};
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_check_err) == cudaSuccess) t_check.err = static_cast<int *>(p);
+        else cudaGetLastError();
+    }
+    ~CheckScope() { t_check = CheckRanges{}; }
+    void add(const void *p, size_t bytes) {
+        if (!p || t_check.n >= kCheckMaxRanges) return;
+        t_check.lo[t_check.n] = static_cast<const char *>(p);
+        t_check.hi[t_check.n] = static_cast<const char *>(p) + bytes;
+        ++t_check.n;
+    }
+    void add_ws(const void *p, size_t bytes) { add(p, bytes > g_check_shrink ? bytes - g_check_shrink : 0); }
+#else
+    void add(const void *, size_t) {}
+    void add_ws(const void *, size_t) {}
+#endif
+};
+
+// bytes of a burst as the kernels may read it: frames h x pitch apart, the last row of
+// the last frame `width` samples long
+size_t burst_bytes(const hmfsr_burst_desc *d) {
+    return (((size_t)d->n_frames - 1) * d->height + d->height - 1) * d->pitch_elems * 2 + (size_t)d->width * 2;
+}
+size_t motion_bytes(const Geom &g) { return (size_t)g.n * g.ty * g.tx * 2 * sizeof(float); }
+size_t rgb_bytes(const hmfsr_burst_desc *d, int num, int den) {
+    return 3 * (size_t)(((long long)d->height * num) / den) * (size_t)(((long long)d->width * num) / den) * sizeof(float);
+}
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -134,6 +178,8 @@ hmfsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HMFSR_OK : H
 
 }  // namespace
 
+const CheckRanges &hmfsr::current_check_ranges() { return t_check; }
+
 extern "C" {
 
 size_t hmfsr_workspace_size(int op, const hmfsr_burst_desc *desc, int tile, int scale_num, int scale_den) {
@@ -171,6 +217,11 @@ hmfsr_status hmfsr_align(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
     hmfsr_status st = check_ws(ws, ws_bytes, need);
     if (st != HMFSR_OK) return st;
     carve_align(ws, g, params->tile, params->n_levels, &L);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(motion_int_dev, motion_bytes(g));
+    chk.add_ws(ws, need);
     return cuda_status(launch_align(burst_dev, g, *params, L, motion_dev, motion_int_dev, (cudaStream_t)stream));
 }
 
@@ -186,6 +237,11 @@ hmfsr_status hmfsr_align_quadfit(const uint16_t *burst_dev, const hmfsr_burst_de
     hmfsr_status st = check_ws(ws, ws_bytes, need);
     if (st != HMFSR_OK) return st;
     carve_align(ws, g, params->tile, params->n_levels, &L);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(motion_int_dev, motion_bytes(g));
+    chk.add_ws(ws, need);
     return cuda_status(launch_align_quadfit(burst_dev, g, *params, L, motion_dev, motion_int_dev,
                                             (cudaStream_t)stream));
 }
@@ -206,6 +262,12 @@ hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
     carve_merge(ws, g, &P);
     cudaStream_t s = (cudaStream_t)stream;
     MergeConsts c = consts_of(params);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add_ws(ws, need);
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
@@ -230,6 +292,13 @@ hmfsr_status hmfsr_merge_noise(const uint16_t *burst_dev, const hmfsr_burst_desc
     cudaStream_t s = (cudaStream_t)stream;
     MergeConsts c = consts_of(params);
     c.noise_table = reinterpret_cast<const float4 *>(noise_table_dev);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(noise_table_dev, sizeof(float4) * kNoiseLevels);
+    chk.add_ws(ws, need);
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
@@ -255,6 +324,13 @@ hmfsr_status hmfsr_merge_ex(const uint16_t *burst_dev, const hmfsr_burst_desc *d
     MergeConsts c = consts_of(params);
     c.noise_table = reinterpret_cast<const float4 *>(opts->noise_table);
     c.hf_loss = opts->hf_loss;
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(opts->noise_table, sizeof(float4) * kNoiseLevels);
+    chk.add_ws(ws, need);
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
@@ -267,9 +343,14 @@ hmfsr_status hmfsr_merge_prepare(const uint16_t *burst_dev, const hmfsr_burst_de
     if (!burst_dev || !motion_dev || !aligned4(burst_dev) || !aligned8(motion_dev) || !valid_merge_params(params)) return HMFSR_ERR_INVALID_ARG;
     Geom g = make_geom(desc, params->tile);
     MergePlanes P;
-    hmfsr_status st = check_ws(ws, ws_bytes, carve_merge(nullptr, g, &P));
+    const size_t need = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
     if (st != HMFSR_OK) return st;
     carve_merge(ws, g, &P);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add_ws(ws, need);
     return cuda_status(launch_merge_prep(burst_dev, motion_dev, g, consts_of(params), P, (cudaStream_t)stream));
 }
 
@@ -283,9 +364,16 @@ hmfsr_status hmfsr_merge_accumulate(const uint16_t *burst_dev, const hmfsr_burst
         return HMFSR_ERR_INVALID_ARG;
     Geom g = make_geom(desc, params->tile);
     MergePlanes P;
-    hmfsr_status st = check_ws(ws, ws_bytes, carve_merge(nullptr, g, &P));
+    const size_t need = carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
     if (st != HMFSR_OK) return st;
     carve_merge(ws, g, &P);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add_ws(ws, need);
     return cuda_status(
         launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, (cudaStream_t)stream));
 }
@@ -303,6 +391,13 @@ hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_des
     if (st != HMFSR_OK) return st;
     carve_merge(ws, g, &P);
     cudaStream_t s = (cudaStream_t)stream;
+    const size_t hw = (size_t)g.hh * g.wh;
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(omega_dev, (size_t)g.n * 3 * hw * sizeof(float));
+    chk.add(rhat_dev, (size_t)g.n * hw * sizeof(float));
+    chk.add_ws(ws, need);
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, consts_of(params), P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_export_stages(g, P, omega_dev, rhat_dev, s));
@@ -345,6 +440,34 @@ const char *hmfsr_status_string(hmfsr_status s) {
         case HMFSR_ERR_TIMEOUT: return "device wait timed out";
     }
     return "unknown status";
+}
+
+hmfsr_status hmfsr_check_status(int reset, int *line) {
+#ifdef HMFSR_CHECKED
+    if (!line) return HMFSR_ERR_INVALID_ARG;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_err, sizeof(int)) != cudaSuccess) return HMFSR_ERR_CUDA;
+    *line = v;
+    if (reset) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(g_check_err, &z, sizeof(int)) != cudaSuccess) return HMFSR_ERR_CUDA;
+    }
+    return HMFSR_OK;
+#else
+    (void)reset;
+    (void)line;
+    return HMFSR_ERR_UNSUPPORTED;
+#endif
+}
+
+hmfsr_status hmfsr_check_shrink(size_t bytes) {
+#ifdef HMFSR_CHECKED
+    g_check_shrink = bytes;
+    return HMFSR_OK;
+#else
+    (void)bytes;
+    return HMFSR_ERR_UNSUPPORTED;
+#endif
 }
 
 const char *hmfsr_version(void) { return "0.1.0"; }

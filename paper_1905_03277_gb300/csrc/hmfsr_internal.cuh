@@ -60,6 +60,91 @@ struct StageRange {
 };
 
 // ---------------------------------------------------------------------------------------
+// Checked build (-DHMFSR_CHECKED, a test build of the library, never the default): every
+// global load and store of the alignment and merge kernels goes through HMFSR_LDG /
+// HMFSR_LD / HMFSR_ST, which check the address against the buffers of the current call
+// (the caller's burst, motion, outputs, tables and workspace, as the entry point
+// registers them).  An access outside all of them is not made -- a load gives 0, a store
+// is dropped -- and the source line of the first such access is recorded in a device
+// error word that the host reads back (hmfsr_check_status).  Nothing traps.  Each
+// translation unit holds its own copy of the ranges, which its launchers set before
+// their launches; calls that register no ranges (n = 0) are not checked.  In the
+// default build the macros are plain loads and stores.
+// ---------------------------------------------------------------------------------------
+constexpr int kCheckMaxRanges = 8;
+struct CheckRanges {
+    const char *lo[kCheckMaxRanges];
+    const char *hi[kCheckMaxRanges];  // one past the last byte
+    int n;                            // 0: not checked
+    int *err;                         // device word: 0, or the line of the first bad access
+};
+// the ranges of the current entry-point call on this host thread (api.cu)
+const CheckRanges &current_check_ranges();
+
+#ifdef HMFSR_CHECKED
+static __constant__ CheckRanges g_check;  // one copy per translation unit
+
+template <typename T>
+__device__ __forceinline__ bool check_access(const T *p) {
+    if (g_check.n == 0) return true;
+    const char *a = reinterpret_cast<const char *>(p);
+    for (int i = 0; i < g_check.n; ++i)
+        if (a >= g_check.lo[i] && a + sizeof(T) <= g_check.hi[i]) return true;
+    return false;
+}
+__device__ __forceinline__ void check_fail(int site) {
+    if (g_check.err) atomicCAS(g_check.err, 0, site);
+}
+template <typename T>
+__device__ __forceinline__ T checked_ldg(const T *p, int site) {
+    if (check_access(p)) return __ldg(p);
+    check_fail(site);
+    return T();
+}
+template <typename T>
+__device__ __forceinline__ T checked_ld(const T *p, int site) {
+    if (check_access(p)) return *p;
+    check_fail(site);
+    return T();
+}
+template <typename T>
+__device__ __forceinline__ void checked_st(T *p, const T &v, int site) {
+    if (check_access(p)) *p = v;
+    else check_fail(site);
+}
+#define HMFSR_LDG(p) ::hmfsr::checked_ldg((p), __LINE__)
+#define HMFSR_LD(p) ::hmfsr::checked_ld((p), __LINE__)
+#define HMFSR_ST(p, v) ::hmfsr::checked_st((p), (v), __LINE__)
+// host: for the launches between construction and destruction on stream s, this
+// translation unit checks against the current call's ranges; afterwards its launches are
+// unchecked again.  Inside stream capture nothing is set (captured launches stay
+// unchecked).
+struct CheckedLaunches {
+    cudaStream_t s;
+    bool set = false;
+    explicit CheckedLaunches(cudaStream_t s_) : s(s_) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+        const CheckRanges &r = current_check_ranges();
+        if (r.n == 0) return;
+        set = cudaMemcpyToSymbolAsync(g_check, &r, sizeof(CheckRanges), 0, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    }
+    ~CheckedLaunches() {
+        if (!set) return;
+        CheckRanges none = {};
+        cudaMemcpyToSymbolAsync(g_check, &none, sizeof(CheckRanges), 0, cudaMemcpyHostToDevice, s);
+    }
+};
+#else
+#define HMFSR_LDG(p) __ldg(p)
+#define HMFSR_LD(p) (*(p))
+#define HMFSR_ST(p, v) ((void)(*(p) = (v)))
+struct CheckedLaunches {
+    explicit CheckedLaunches(cudaStream_t) {}
+};
+#endif
+
+// ---------------------------------------------------------------------------------------
 // geometry of one burst
 // ---------------------------------------------------------------------------------------
 struct Geom {

@@ -98,13 +98,13 @@ __global__ void k_export(const float4 *__restrict__ kern, const float *__restric
     int f = blockIdx.y;
     if (i >= hw) return;
     if (omega) {
-        float4 t = kern[(size_t)f * hw + i];
+        const float4 t = HMFSR_LD(kern + (size_t)f * hw + i);
         float *o = omega + (size_t)f * 3 * hw;
-        o[i] = t.x + t.y * t.z * t.z;
-        o[hw + i] = t.y * t.z * t.w;
-        o[2 * hw + i] = t.x + t.y * t.w * t.w;
+        HMFSR_ST(o + i, t.x + t.y * t.z * t.z);
+        HMFSR_ST(o + hw + i, t.y * t.z * t.w);
+        HMFSR_ST(o + 2 * hw + i, t.x + t.y * t.w * t.w);
     }
-    if (rhat_out) rhat_out[(size_t)f * hw + i] = (f == ref) ? 1.f : rhat[(size_t)f * hw + i];
+    if (rhat_out) HMFSR_ST(rhat_out + (size_t)f * hw + i, (f == ref) ? 1.f : HMFSR_LD(rhat + (size_t)f * hw + i));
 }
 
 // --------------------------------------------------------------------------------------
@@ -168,6 +168,7 @@ int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, i
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s) {
     StageRange range("hmfsr merge: kernel covariance and robustness");
+    CheckedLaunches checked(s);
     const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
                                     g.hh, 8, stage::kPrepStrip);
     k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
@@ -197,6 +198,7 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
                                int snum, int sden, float *rgb, float *den, cudaStream_t s) {
     StageRange range("hmfsr merge: accumulation and normalisation");
+    CheckedLaunches checked(s);
     int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     dim3 grid(div_up(wo, kMergeW), div_up(ho, kMergeH));
     const int ntl = g.ty * g.tx;
@@ -210,6 +212,7 @@ cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const
 }
 
 cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *omega, float *rhat, cudaStream_t s) {
+    CheckedLaunches checked(s);
     size_t hw = (size_t)g.hh * g.wh;
     k_export<<<dim3((unsigned)((hw + 255) / 256), g.n), 256, 0, s>>>(P.kern, P.rhat, g.n, g.ref, hw, omega, rhat);
     return cudaGetLastError();

@@ -26,19 +26,19 @@ __device__ __forceinline__ void luma0(const uint16_t *__restrict__ burst, int h,
     uint16_t *o = out + ((size_t)f * hh + v) * wh + u;
     if (u + 4 <= wh && ((reinterpret_cast<uintptr_t>(r0) | reinterpret_cast<uintptr_t>(r0 + pitch)) & 15) == 0 &&
         (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
-        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(r0));
-        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(r0 + pitch));
+        const uint4 a = HMFSR_LDG(reinterpret_cast<const uint4 *>(r0));
+        const uint4 b = HMFSR_LDG(reinterpret_cast<const uint4 *>(r0 + pitch));
         const uint32_t s0 = (a.x & 0xffffu) + (a.x >> 16) + (b.x & 0xffffu) + (b.x >> 16);
         const uint32_t s1 = (a.y & 0xffffu) + (a.y >> 16) + (b.y & 0xffffu) + (b.y >> 16);
         const uint32_t s2 = (a.z & 0xffffu) + (a.z >> 16) + (b.z & 0xffffu) + (b.z >> 16);
         const uint32_t s3 = (a.w & 0xffffu) + (a.w >> 16) + (b.w & 0xffffu) + (b.w >> 16);
-        *reinterpret_cast<uint2 *>(o) = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
+        HMFSR_ST(reinterpret_cast<uint2 *>(o), make_uint2(s0 | (s1 << 16), s2 | (s3 << 16)));
         return;
     }
     for (int i = 0; i < 4 && u + i < wh; ++i) {
-        const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
-        const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
-        o[i] = (uint16_t)((a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16));
+        const uint32_t a = HMFSR_LDG(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
+        const uint32_t b = HMFSR_LDG(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
+        HMFSR_ST(o + i, (uint16_t)((a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16)));
     }
 }
 
@@ -62,21 +62,21 @@ __device__ __forceinline__ void luma01(const uint16_t *__restrict__ burst, int h
         uint16_t *o = out0 + ((size_t)f * hh + v) * wh + u;
         if (u + 4 <= wh && ((reinterpret_cast<uintptr_t>(r0) | reinterpret_cast<uintptr_t>(r0 + pitch)) & 15) == 0 &&
             (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(r0));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(r0 + pitch));
+            const uint4 a = HMFSR_LDG(reinterpret_cast<const uint4 *>(r0));
+            const uint4 b = HMFSR_LDG(reinterpret_cast<const uint4 *>(r0 + pitch));
             sq[r][0] = (a.x & 0xffffu) + (a.x >> 16) + (b.x & 0xffffu) + (b.x >> 16);
             sq[r][1] = (a.y & 0xffffu) + (a.y >> 16) + (b.y & 0xffffu) + (b.y >> 16);
             sq[r][2] = (a.z & 0xffffu) + (a.z >> 16) + (b.z & 0xffffu) + (b.z >> 16);
             sq[r][3] = (a.w & 0xffffu) + (a.w >> 16) + (b.w & 0xffffu) + (b.w >> 16);
-            *reinterpret_cast<uint2 *>(o) = make_uint2(sq[r][0] | (sq[r][1] << 16), sq[r][2] | (sq[r][3] << 16));
+            HMFSR_ST(reinterpret_cast<uint2 *>(o), make_uint2(sq[r][0] | (sq[r][1] << 16), sq[r][2] | (sq[r][3] << 16)));
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (u + i >= wh) break;
-                const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
-                const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
+                const uint32_t a = HMFSR_LDG(reinterpret_cast<const uint32_t *>(r0 + 2 * i));
+                const uint32_t b = HMFSR_LDG(reinterpret_cast<const uint32_t *>(r0 + pitch + 2 * i));
                 sq[r][i] = (a & 0xffffu) + (a >> 16) + (b & 0xffffu) + (b >> 16);
-                o[i] = (uint16_t)sq[r][i];
+                HMFSR_ST(o + i, (uint16_t)sq[r][i]);
             }
         }
     }
@@ -85,7 +85,7 @@ __device__ __forceinline__ void luma01(const uint16_t *__restrict__ burst, int h
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int x = u / 2 + k;  // level-1 texel over level-0 columns 2 x, 2 x + 1
-        if (x < lw1) o1[x] = (uint16_t)((sq[0][2 * k] + sq[0][2 * k + 1] + sq[1][2 * k] + sq[1][2 * k + 1]) / 4u);
+        if (x < lw1) HMFSR_ST(o1 + x, (uint16_t)((sq[0][2 * k] + sq[0][2 * k + 1] + sq[1][2 * k] + sq[1][2 * k + 1]) / 4u));
     }
 }
 
@@ -96,8 +96,8 @@ __device__ __forceinline__ void down(const uint16_t *__restrict__ src, int sh, i
     const uint16_t *p = src + (size_t)f * sh * sw + (size_t)(y * fct) * sw + x * fct;
     uint32_t s = 0;
     for (int j = 0; j < fct; ++j)
-        for (int i = 0; i < fct; ++i) s += p[(size_t)j * sw + i];
-    dst[((size_t)f * dh + y) * dw + x] = (uint16_t)(s / (uint32_t)(fct * fct));
+        for (int i = 0; i < fct; ++i) s += HMFSR_LD(p + (size_t)j * sw + i);
+    HMFSR_ST(dst + ((size_t)f * dh + y) * dw + x, (uint16_t)(s / (uint32_t)(fct * fct)));
 }
 
 constexpr int kMaxRad = 7;
@@ -144,7 +144,7 @@ __device__ __forceinline__ int2 ssd_centre(const int2 *__restrict__ parent, int 
     if (!parent) return make_int2(0, 0);
     const int px = min(((tx * T + T / 2) >> fsh) / T, ptx - 1);
     const int py = min(((ty * T + T / 2) >> fsh) / T, pty - 1);
-    const int2 pv = __ldg(parent + (size_t)f * pty * ptx + (size_t)py * ptx + px);
+    const int2 pv = HMFSR_LDG(parent + (size_t)f * pty * ptx + (size_t)py * ptx + px);
     return make_int2(pv.x << fsh, pv.y << fsh);
 }
 
@@ -156,12 +156,12 @@ template <int N>
 __device__ __forceinline__ void load_row(const uint16_t *__restrict__ row, int x, int lw, bool inside, int (&v)[N]) {
     if (inside) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = __ldg(row + x + i);
+        for (int i = 0; i < N; ++i) v[i] = HMFSR_LDG(row + x + i);
     } else {
         int xb = x;
         asm volatile("" : "+r"(xb));
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[i] = __ldg(row + clampi(xb + i, 0, lw - 1));
+        for (int i = 0; i < N; ++i) v[i] = HMFSR_LDG(row + clampi(xb + i, 0, lw - 1));
     }
 }
 
@@ -186,7 +186,7 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
     const int ty = tile / ltx, tx = tile - ty * ltx;
     int2 *out = vec + (size_t)f * lty * ltx + tile;
     if (f == ref) {
-        *out = make_int2(0, 0);
+        HMFSR_ST(out, make_int2(0, 0));
         return;
     }
     const int2 cc = ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
@@ -216,7 +216,7 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
         }
     }
     const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
-    *out = make_int2(cx + bdx, cy + bdy);
+    HMFSR_ST(out, make_int2(cx + bdx, cy + bdy));
 }
 
 // The same search with the tile rows outermost (small radii): each candidate row is read
@@ -231,7 +231,7 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
     const int ty = tile / ltx, tx = tile - ty * ltx;
     int2 *out = vec + (size_t)f * lty * ltx + tile;
     if (f == ref) {
-        *out = make_int2(0, 0);
+        HMFSR_ST(out, make_int2(0, 0));
         return;
     }
     const int2 cc = ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
@@ -273,7 +273,7 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
             best = key < best ? key : best;
         }
     const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
-    *out = make_int2(cc.x + bdx, cc.y + bdy);
+    HMFSR_ST(out, make_int2(cc.x + bdx, cc.y + bdy));
 }
 
 // The same search with the offsets dy spread over a group of 2 RAD + 1 lanes (lane d of
@@ -291,7 +291,7 @@ __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int 
     const int tile = tile0 + grp;
     const bool active = grp < kG && tile < lty * ltx;
     if (f == ref) {
-        if (active && d == 0) vec[(size_t)f * lty * ltx + tile] = make_int2(0, 0);
+        if (active && d == 0) HMFSR_ST(vec + (size_t)f * lty * ltx + tile, make_int2(0, 0));
         return;
     }
     const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
@@ -331,7 +331,7 @@ __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int 
     }
     if (active && d == 0) {
         const int bdx = (int)(m & 15ull) - 7, bdy = (int)((m >> 4) & 15ull) - 7;
-        vec[(size_t)f * lty * ltx + tile] = make_int2(cc.x + bdx, cc.y + bdy);
+        HMFSR_ST(vec + (size_t)f * lty * ltx + tile, make_int2(cc.x + bdx, cc.y + bdy));
     }
 }
 
@@ -351,15 +351,15 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
     const size_t o = (size_t)f * lty * ltx + warp;
     if (f == ref) {
         if (lane == 0) {
-            motion[2 * o] = 0.f;
-            motion[2 * o + 1] = 0.f;
-            if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+            HMFSR_ST(motion + 2 * o, 0.f);
+            HMFSR_ST(motion + 2 * o + 1, 0.f);
+            if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
         }
         return;
     }
     const uint16_t *R = L0 + (size_t)ref * lh * lw;
     const uint16_t *A = L0 + (size_t)f * lh * lw;
-    const int2 u = vec0[o];
+    const int2 u = HMFSR_LD(vec0 + o);
     int gxs[nper], gys[nper], pxs[nper], pys[nper], rv[nper];
     long long hxx = 0, hxy = 0, hyy = 0;
 #pragma unroll
@@ -368,10 +368,10 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
         if (k >= npx) { gxs[m] = gys[m] = 0; pxs[m] = pys[m] = 0; rv[m] = 0; continue; }
         const int x = min(tx * t + k % t, lw - 1), y = min(ty * t + k / t, lh - 1);
         const uint16_t *row = R + (size_t)y * lw;
-        const int gx = (int)__ldg(row + min(x + 1, lw - 1)) - (int)__ldg(row + max(x - 1, 0));
-        const int gy = (int)__ldg(R + (size_t)min(y + 1, lh - 1) * lw + x) - (int)__ldg(R + (size_t)max(y - 1, 0) * lw + x);
+        const int gx = (int)HMFSR_LDG(row + min(x + 1, lw - 1)) - (int)HMFSR_LDG(row + max(x - 1, 0));
+        const int gy = (int)HMFSR_LDG(R + (size_t)min(y + 1, lh - 1) * lw + x) - (int)HMFSR_LDG(R + (size_t)max(y - 1, 0) * lw + x);
         gxs[m] = gx; gys[m] = gy; pxs[m] = x; pys[m] = y;
-        rv[m] = __ldg(row + x);
+        rv[m] = HMFSR_LDG(row + x);
         hxx += (long long)(gx * gx);
         hxy += (long long)(gx * gy);
         hyy += (long long)(gy * gy);
@@ -400,7 +400,7 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
                 const int x0 = clampi(ix, 0, lw - 1), x1 = clampi(ix + 1, 0, lw - 1);
                 const uint16_t *a0 = A + (size_t)clampi(iy, 0, lh - 1) * lw;
                 const uint16_t *a1 = A + (size_t)clampi(iy + 1, 0, lh - 1) * lw;
-                const float i00 = __ldg(a0 + x0), i10 = __ldg(a0 + x1), i01 = __ldg(a1 + x0), i11 = __ldg(a1 + x1);
+                const float i00 = HMFSR_LDG(a0 + x0), i10 = HMFSR_LDG(a0 + x1), i01 = HMFSR_LDG(a1 + x0), i11 = HMFSR_LDG(a1 + x1);
                 const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
                 const float ia = fmaf(ay, bot, (1.f - ay) * top);
                 const float r = (ia - (float)rv[m]) * 0.25f;
@@ -416,9 +416,9 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
         }
     }
     if (lane == 0) {
-        motion[2 * o] = 2.f * ((float)u.x + dx);
-        motion[2 * o + 1] = 2.f * ((float)u.y + dy);
-        if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+        HMFSR_ST(motion + 2 * o, 2.f * ((float)u.x + dx));
+        HMFSR_ST(motion + 2 * o + 1, 2.f * ((float)u.y + dy));
+        if (motion_int) { HMFSR_ST(motion_int + 2 * o, (int32_t)u.x); HMFSR_ST(motion_int + 2 * o + 1, (int32_t)u.y); }
     }
 }
 
@@ -439,16 +439,16 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
     const size_t o = (size_t)f * lty * ltx + tile;
     if (f == ref) {
         if (active && c == 0) {
-            motion[2 * o] = 0.f;
-            motion[2 * o + 1] = 0.f;
-            if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+            HMFSR_ST(motion + 2 * o, 0.f);
+            HMFSR_ST(motion + 2 * o + 1, 0.f);
+            if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
         }
         return;
     }
     const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
     const uint16_t *R = L0 + (size_t)ref * lh * lw;
     const uint16_t *A = L0 + (size_t)f * lh * lw;
-    const int2 u = active ? vec0[o] : make_int2(0, 0);
+    const int2 u = active ? HMFSR_LD(vec0 + o) : make_int2(0, 0);
     const int x = min(tx * T + c, lw - 1), y0 = ty * T;
     const int xm = max(x - 1, 0), xp = min(x + 1, lw - 1);
     float gxs[T], gys[T], rv[T];
@@ -457,11 +457,11 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
     for (int j = 0; j < T; ++j) {
         const int y = min(y0 + j, lh - 1);
         const uint16_t *row = R + y * lw;  // 32-bit offsets: a level holds < 2^31 texels
-        const int gx = (int)__ldg(row + xp) - (int)__ldg(row + xm);
-        const int gy = (int)__ldg(R + min(y + 1, lh - 1) * lw + x) - (int)__ldg(R + max(y - 1, 0) * lw + x);
+        const int gx = (int)HMFSR_LDG(row + xp) - (int)HMFSR_LDG(row + xm);
+        const int gy = (int)HMFSR_LDG(R + min(y + 1, lh - 1) * lw + x) - (int)HMFSR_LDG(R + max(y - 1, 0) * lw + x);
         gxs[j] = (float)gx * 0.125f;
         gys[j] = (float)gy * 0.125f;
-        rv[j] = (float)__ldg(row + x);
+        rv[j] = (float)HMFSR_LDG(row + x);
         hxx += (long long)(gx * gx);
         hxy += (long long)(gx * gy);
         hyy += (long long)(gy * gy);
@@ -489,11 +489,11 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
         if (y0 + T <= lh && y0 + oy >= 0 && y0 + oy + T < lh) {
             // the tile's rows and the sampled rows are inside the level: one row after another
             const uint16_t *a = A + (y0 + oy) * lw;
-            float i00 = (float)__ldg(a + x0), i10 = (float)__ldg(a + x1);
+            float i00 = (float)HMFSR_LDG(a + x0), i10 = (float)HMFSR_LDG(a + x1);
 #pragma unroll
             for (int j = 0; j < T; ++j) {
                 a += lw;
-                const float i01 = (float)__ldg(a + x0), i11 = (float)__ldg(a + x1);
+                const float i01 = (float)HMFSR_LDG(a + x0), i11 = (float)HMFSR_LDG(a + x1);
                 const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
                 const float ia = fmaf(ay, bot, (1.f - ay) * top);
                 const float r = (ia - rv[j]) * 0.25f;
@@ -508,8 +508,8 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
                 const int iy = min(y0 + j, lh - 1) + oy;
                 const uint16_t *a0 = A + clampi(iy, 0, lh - 1) * lw;
                 const uint16_t *a1 = A + clampi(iy + 1, 0, lh - 1) * lw;
-                const float i00 = (float)__ldg(a0 + x0), i10 = (float)__ldg(a0 + x1);
-                const float i01 = (float)__ldg(a1 + x0), i11 = (float)__ldg(a1 + x1);
+                const float i00 = (float)HMFSR_LDG(a0 + x0), i10 = (float)HMFSR_LDG(a0 + x1);
+                const float i01 = (float)HMFSR_LDG(a1 + x0), i11 = (float)HMFSR_LDG(a1 + x1);
                 const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
                 const float ia = fmaf(ay, bot, (1.f - ay) * top);
                 const float r = (ia - rv[j]) * 0.25f;
@@ -530,9 +530,9 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
         }
     }
     if (active && c == 0) {
-        motion[2 * o] = 2.f * ((float)u.x + dx);
-        motion[2 * o + 1] = 2.f * ((float)u.y + dy);
-        if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+        HMFSR_ST(motion + 2 * o, 2.f * ((float)u.x + dx));
+        HMFSR_ST(motion + 2 * o + 1, 2.f * ((float)u.y + dy));
+        if (motion_int) { HMFSR_ST(motion_int + 2 * o, (int32_t)u.x); HMFSR_ST(motion_int + 2 * o + 1, (int32_t)u.y); }
     }
 }
 
@@ -555,15 +555,15 @@ __device__ __forceinline__ void quadfit(const uint16_t *__restrict__ L0, int lh,
     if (tile >= lty * ltx) return;
     const size_t o = (size_t)f * lty * ltx + tile;
     if (f == ref) {
-        motion[2 * o] = 0.f;
-        motion[2 * o + 1] = 0.f;
-        if (motion_int) { motion_int[2 * o] = 0; motion_int[2 * o + 1] = 0; }
+        HMFSR_ST(motion + 2 * o, 0.f);
+        HMFSR_ST(motion + 2 * o + 1, 0.f);
+        if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
         return;
     }
     const int ty = tile / ltx, tx = tile - ty * ltx;
     const uint16_t *R = L0 + (size_t)ref * lh * lw;
     const uint16_t *A = L0 + (size_t)f * lh * lw;
-    const int2 u = vec0[o];
+    const int2 u = HMFSR_LD(vec0 + o);
     const int x0 = tx * T, y0 = ty * T;
     auto ssd_at = [&](int dx, int dy) -> long long {
         long long e = 0;
@@ -572,7 +572,7 @@ __device__ __forceinline__ void quadfit(const uint16_t *__restrict__ L0, int lh,
             const uint16_t *ar = A + clampi(y0 + j + u.y + dy, 0, lh - 1) * lw;
 #pragma unroll
             for (int i = 0; i < T; ++i) {
-                const int d = (int)__ldg(rr + min(x0 + i, lw - 1)) - (int)__ldg(ar + clampi(x0 + i + u.x + dx, 0, lw - 1));
+                const int d = (int)HMFSR_LDG(rr + min(x0 + i, lw - 1)) - (int)HMFSR_LDG(ar + clampi(x0 + i + u.x + dx, 0, lw - 1));
                 e += (long long)(d * d);
             }
         }
@@ -581,9 +581,9 @@ __device__ __forceinline__ void quadfit(const uint16_t *__restrict__ L0, int lh,
     const long long e0 = ssd_at(0, 0);
     const double dx = parabola_vertex(ssd_at(-1, 0), e0, ssd_at(1, 0));
     const double dy = parabola_vertex(ssd_at(0, -1), e0, ssd_at(0, 1));
-    motion[2 * o] = (float)__dmul_rn(2.0, __dadd_rn((double)u.x, dx));
-    motion[2 * o + 1] = (float)__dmul_rn(2.0, __dadd_rn((double)u.y, dy));
-    if (motion_int) { motion_int[2 * o] = u.x; motion_int[2 * o + 1] = u.y; }
+    HMFSR_ST(motion + 2 * o, (float)__dmul_rn(2.0, __dadd_rn((double)u.x, dx)));
+    HMFSR_ST(motion + 2 * o + 1, (float)__dmul_rn(2.0, __dadd_rn((double)u.y, dy)));
+    if (motion_int) { HMFSR_ST(motion_int + 2 * o, (int32_t)u.x); HMFSR_ST(motion_int + 2 * o + 1, (int32_t)u.y); }
 }
 
 // ======================================================================================
@@ -609,7 +609,7 @@ __device__ __forceinline__ float4 base_stats_of(const uint32_t (&S1)[3], const u
             const float tp = fminf(fmaxf(mu, 0.f), (float)wl) * ((float)(kNoiseLevels - 1) / (float)wl);
             const int i = min((int)tp, kNoiseLevels - 2);
             const float f = tp - (float)i;
-            const float4 t0 = __ldg(c.noise_table + i), t1 = __ldg(c.noise_table + i + 1);
+            const float4 t0 = HMFSR_LDG(c.noise_table + i), t1 = HMFSR_LDG(c.noise_table + i + 1);
             const float v0 = ch == 1 ? t0.y : t0.x, v1 = ch == 1 ? t1.y : t1.x;
             const float d0 = ch == 1 ? t0.w : t0.z, d1 = ch == 1 ? t1.w : t1.z;
             var_md = fmaf(f, v1 - v0, v0);
@@ -689,12 +689,12 @@ __device__ __forceinline__ PrepRow prep_fetch(const uint16_t *__restrict__ fr, i
                                               bool halo, int v) {
     const uint16_t *row = fr + (size_t)(2 * clampi(v, 0, hh - 1)) * pitch;
     PrepRow p;
-    p.a = __ldg(reinterpret_cast<const uint32_t *>(row + 2 * uc));
-    p.b = __ldg(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uc));
+    p.a = HMFSR_LDG(reinterpret_cast<const uint32_t *>(row + 2 * uc));
+    p.b = HMFSR_LDG(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uc));
     p.ha = p.hb = 0u;
     if (halo) {
-        p.ha = __ldg(reinterpret_cast<const uint32_t *>(row + 2 * uh));
-        p.hb = __ldg(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uh));
+        p.ha = HMFSR_LDG(reinterpret_cast<const uint32_t *>(row + 2 * uh));
+        p.hb = HMFSR_LDG(reinterpret_cast<const uint32_t *>(row + pitch + 2 * uh));
     }
     return p;
 }
@@ -740,14 +740,14 @@ __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r,
         if (v < g.hh) {
             const int idx = v * g.wh + u;
             const uint32_t srb = st.rb[0] + st.rb[1] + rb, sg = st.gs[0] + st.gs[1] + gs;
-            s1f[idx] = make_uint2(srb, sg);
+            HMFSR_ST(s1f + idx, make_uint2(srb, sg));
             if (is_ref) {
                 const uint32_t S1[3] = {srb & 0xffffu, sg, srb >> 16};
                 const uint32_t S2[3] = {st.q[0][0] + st.q[1][0] + q[0], st.q[0][1] + st.q[1][1] + q[1],
                                         st.q[0][2] + st.q[1][2] + q[2]};
-                base_stats[idx] = base_stats_of(S1, S2, c, g.wl);
+                HMFSR_ST(base_stats + idx, base_stats_of(S1, S2, c, g.wl));
             }
-            kernf[idx] = kern_of_tensor(st.pa + pa, st.pb + pb, st.pc + pc, c, inv_dtr);
+            HMFSR_ST(kernf + idx, kern_of_tensor(st.pa + pa, st.pb + pb, st.pc + pc, c, inv_dtr));
         }
     }
     st.rb[0] = st.rb[1]; st.rb[1] = rb;
@@ -804,7 +804,7 @@ __device__ __forceinline__ bool motion_span_exceeds(const float2 *__restrict__ m
         for (int k = -1; k <= 1; ++k) {
             int yy = y + j, xx = x + k;
             if (yy < 0 || yy >= ty || xx < 0 || xx >= tx) continue;
-            float2 v = mv[(size_t)yy * tx + xx];
+            float2 v = HMFSR_LD(mv + (size_t)yy * tx + xx);
             mnx = fminf(mnx, v.x); mxx = fmaxf(mxx, v.x);
             mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
         }
@@ -817,7 +817,7 @@ __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int 
                                          float s2, float *__restrict__ s_tile, int i) {
     if (i >= n * ty * tx) return;
     int f = i / (ty * tx), r = i % (ty * tx), y = r / tx, x = r % tx;
-    s_tile[i] = motion_span_exceeds(motion + (size_t)f * ty * tx, ty, tx, y, x, m_th) ? s1 : s2;
+    HMFSR_ST(s_tile + i, motion_span_exceeds(motion + (size_t)f * ty * tx, ty, tx, y, x, m_th) ? s1 : s2);
 }
 
 // --------------------------------------------------------------------------------------
@@ -837,15 +837,15 @@ __device__ __forceinline__ void hf_flag_px(const uint16_t *__restrict__ burst, c
     for (int j = -1; j <= 1; ++j)
         for (int i = -1; i <= 1; ++i) {
             const uint16_t *q = fr + (size_t)(2 * clampi(v + j, 0, g.hh - 1)) * g.pitch + 2 * clampi(u + i, 0, g.wh - 1);
-            const uint32_t a = __ldg(reinterpret_cast<const uint32_t *>(q));
-            const uint32_t b = __ldg(reinterpret_cast<const uint32_t *>(q + g.pitch));
+            const uint32_t a = HMFSR_LDG(reinterpret_cast<const uint32_t *>(q));
+            const uint32_t b = HMFSR_LDG(reinterpret_cast<const uint32_t *>(q + g.pitch));
             const long long R = a & 0xffffu, G = (a >> 16) + (b & 0xffffu), B = b >> 16;
             sq[0] += R * R; sq[1] += G * G; sq[2] += B * B;
         }
     long long t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
     for (int j = -1; j <= 1; ++j)
         for (int i = -1; i <= 1; ++i) {
-            const uint2 m = __ldg(S + (size_t)clampi(v + j, 0, g.hh - 1) * g.wh + clampi(u + i, 0, g.wh - 1));
+            const uint2 m = HMFSR_LDG(S + (size_t)clampi(v + j, 0, g.hh - 1) * g.wh + clampi(u + i, 0, g.wh - 1));
             const long long k[3] = {(long long)(m.x & 0xffffu), (long long)m.y, (long long)(m.x >> 16)};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -861,7 +861,8 @@ __device__ __forceinline__ void hf_flag_px(const uint16_t *__restrict__ burst, c
         B += wgt[c] * (9 * sq[c] - c1[c] * c1[c]);
         A += wgt[c] * (9 * t2[c] - t1[c] * t1[c]);
     }
-    flag[(size_t)v * g.wh + u] = (B > 0 && (double)A < __dmul_rn((double)kappa, __dmul_rn(81.0, (double)B))) ? 1 : 0;
+    HMFSR_ST(flag + (size_t)v * g.wh + u,
+             (unsigned char)((B > 0 && (double)A < __dmul_rn((double)kappa, __dmul_rn(81.0, (double)B))) ? 1 : 0));
 }
 
 // --------------------------------------------------------------------------------------
@@ -920,8 +921,8 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
             const int tyi = min(tq, g.ty - 1);
             if (tyi != cur_tile) {
                 cur_tile = tyi;
-                const float2 mv = mvf[tyi * g.tx];
-                sc = stf[tyi * g.tx];
+                const float2 mv = HMFSR_LD(mvf + tyi * g.tx);
+                sc = HMFSR_LD(stf + tyi * g.tx);
                 // aligned position (u, v) + v/2 split into an exact integer part and fraction
                 const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
                 const float flx = floorf(hx), flyf = floorf(hy);
@@ -940,18 +941,18 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
                 nt1 = nb1;
             } else {
                 const int o0 = clampi(iy, 0, g.hh - 1) * wh;
-                nt0 = S1n[o0 + x0];
-                nt1 = S1n[o0 + x1];
+                nt0 = HMFSR_LD(S1n + o0 + x0);
+                nt1 = HMFSR_LD(S1n + o0 + x1);
             }
             const int o1 = clampi(iy + 1, 0, g.hh - 1) * wh;
-            nb0 = S1n[o1 + x0];
-            nb1 = S1n[o1 + x1];
+            nb0 = HMFSR_LD(S1n + o1 + x0);
+            nb1 = HMFSR_LD(S1n + o1 + x1);
             have_prev = true;
-            if (kHF && col_ok && span && hf_flag[off]) {
+            if (kHF && col_ok && span && HMFSR_LD(hf_flag + off)) {
                 R = 0.f;  // high-frequency content with a large local motion span: rejected
             } else if (col_ok) {
-                const uint2 sb = S1b[off];
-                const float4 st = base_stats[off];
+                const uint2 sb = HMFSR_LD(S1b + off);
+                const float4 st = HMFSR_LD(base_stats + off);
                 // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9, from exact
                 // integer differences
                 const int ri = (int)(sb.x & 0xffffu), bi = (int)(sb.x >> 16), gi = (int)sb.y;
@@ -979,7 +980,8 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
         m = fminf(m, __shfl_down_sync(0xffffffffu, R, 4));
         if (e >= 4) {
             const int vo = v - 2, uo = u0 + lane;
-            if (lane < kRobOut && uo < wh && vo < g.hh) out[vo * wh + uo] = fminf(fminf(fminf(h0, h1), fminf(h2, h3)), m);
+            if (lane < kRobOut && uo < wh && vo < g.hh)
+                HMFSR_ST(out + vo * wh + uo, fminf(fminf(fminf(h0, h1), fminf(h2, h3)), m));
         }
         h0 = h1; h1 = h2; h2 = h3; h3 = m;
     }

@@ -36,6 +36,13 @@ def test_exports_every_declared_symbol(L):
     assert set(_lib.EXPORTS) <= names
 
 
+def test_default_build_has_no_checker(L):
+    # the checker's entry points answer "unsupported" outside the checked build
+    line = ctypes.c_int(0)
+    assert L.hmfsr_check_status(0, ctypes.byref(line)) == -2
+    assert L.hmfsr_check_shrink(0) == -2
+
+
 def test_status_strings(L):
     assert L.hmfsr_status_string(0) == b"ok"
     assert b"workspace" in L.hmfsr_status_string(-3)
