@@ -210,6 +210,7 @@ struct BwdPlanes {
     float2 *vbar_tex;       // [n][hh*wh] motion contributions through R
     float2 *vbar_pix;       // [n][ho*wo] motion contributions through the weights
     float *rhbar_pix;       // [n][ho*wo] dL/dRhat at output pixels
+    float *rhbar_rows;      // [n][ho][wh] dL/dRhat gathered along x (output rows x texel columns)
     double *part6;          // [n_bwd_blocks][6] kernel-parameter partial sums
     double *part2;          // [n_rp_blocks][2] (s2, t) partial sums
     unsigned char *sel;     // [n][ty*tx] 1 where the motion prior chose s2

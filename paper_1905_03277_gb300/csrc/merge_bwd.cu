@@ -36,31 +36,48 @@ __device__ __forceinline__ void warp_sums_comp(float (&v)[K], float (&e)[K]) {
         }
 }
 
-// d k_across / d p and d k_along / d p for the six kernel parameters at one texel
-struct KGrad {
-    float dac[6], dal[6];
+// The six kernel parameters' contribution of one texel.  With k_x = s_x^2 the kernel
+// variances of Eq. 4 / S.1 (s_along, s_across their square roots), d k_x / d p_q = 2 s_x
+// a_x[q], and the texel adds sum_q (d k_across / d p_q bo1 + d k_along / d p_q bo2) to
+// pb[q], bo1 and bo2 being dL/dk_across and dL/dk_along times the bilinear weight:
+//   a_along  = {(1-D) k_stretch A + D k_denoise, D k_detail, (kd - kh_al) dD/dD_th,
+//               (kd - kh_al) dD/dD_tr, (1-D) k_detail A, 0},
+//   a_across = {(1-D) / (k_shrink A) + D k_denoise, D k_detail, (kd - kh_ac) dD/dD_th,
+//               (kd - kh_ac) dD/dD_tr, 0, -(1-D) k_detail / (k_shrink^2 A)}
+// with kd = k_detail k_denoise, kh_al = k_detail k_stretch A, kh_ac = k_detail /
+// (k_shrink A), D = clamp(1 - sqrt(l1_norm) / D_tr + D_th, 0, 1) and its derivatives 0
+// where clamped.  Per-call constants in KConsts; 1/A on the SFU.
+struct KConsts {
+    float inv_dtr, inv_shrink, kd, kds, kdi, kdi2;
 };
-
-// inv_dtr = 1 / D_tr and inv_shrink = 1 / k_shrink (per call); 1/A on the SFU
-__device__ __forceinline__ void kernel_grad(const float4 sh, const MergeConsts &c, float inv_dtr, float inv_shrink,
-                                            KGrad &kg) {
+__device__ __forceinline__ KConsts kconsts_of(const MergeConsts &c) {
+    KConsts k;
+    k.inv_dtr = 1.f / c.d_tr;
+    k.inv_shrink = 1.f / c.k_shrink;
+    k.kd = c.k_detail * c.k_denoise;
+    k.kds = c.k_detail * c.k_stretch;
+    k.kdi = c.k_detail * k.inv_shrink;
+    k.kdi2 = k.kdi * k.inv_shrink;
+    return k;
+}
+__device__ __forceinline__ void kernel_grad_acc(const float4 sh, const MergeConsts &c, const KConsts &k, float bo1,
+                                                float bo2, float (&pb)[6]) {
     const float A = sh.x, rl = sh.y, invA = fast_rcp(A);
-    const float Draw = 1.f - rl * inv_dtr + c.d_th;
-    const float D = fminf(fmaxf(Draw, 0.f), 1.f);
+    const float Draw = 1.f - rl * k.inv_dtr + c.d_th;
+    const float D = fminf(fmaxf(Draw, 0.f), 1.f), omD = 1.f - D;
     const bool inside = Draw > 0.f && Draw < 1.f;
-    const float dD2 = inside ? 1.f : 0.f, dD3 = inside ? rl * inv_dtr * inv_dtr : 0.f;
-    const float kh_al = c.k_detail * c.k_stretch * A, kh_ac = c.k_detail * inv_shrink * invA;
-    const float kd = c.k_detail * c.k_denoise;
-    const float s_al = (1.f - D) * kh_al + D * kd, s_ac = (1.f - D) * kh_ac + D * kd;
-    const float al[6] = {(1.f - D) * c.k_stretch * A + D * c.k_denoise, D * c.k_detail, (kd - kh_al) * dD2,
-                         (kd - kh_al) * dD3, (1.f - D) * c.k_detail * A, 0.f};
-    const float ac[6] = {(1.f - D) * inv_shrink * invA + D * c.k_denoise, D * c.k_detail, (kd - kh_ac) * dD2,
-                         (kd - kh_ac) * dD3, 0.f, -(1.f - D) * c.k_detail * inv_shrink * inv_shrink * invA};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        kg.dal[q] = 2.f * s_al * al[q];
-        kg.dac[q] = 2.f * s_ac * ac[q];
+    const float kh_al = k.kds * A, kh_ac = k.kdi * invA;
+    const float s_al = omD * kh_al + D * k.kd, s_ac = omD * kh_ac + D * k.kd;
+    const float P = 2.f * s_ac * bo1, Qv = 2.f * s_al * bo2;  // dL/d(a_across), dL/d(a_along) weights
+    pb[0] = fmaf(P, omD * k.inv_shrink * invA + D * c.k_denoise, fmaf(Qv, omD * c.k_stretch * A + D * c.k_denoise, pb[0]));
+    pb[1] = fmaf(P + Qv, D * c.k_detail, pb[1]);
+    if (inside) {
+        const float sD = P * (k.kd - kh_ac) + Qv * (k.kd - kh_al);
+        pb[2] += sD;
+        pb[3] = fmaf(sD, rl * k.inv_dtr * k.inv_dtr, pb[3]);
     }
+    pb[4] = fmaf(Qv, omD * c.k_detail * A, pb[4]);
+    pb[5] = fmaf(-P, omD * k.kdi2 * invA, pb[5]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -235,7 +252,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_merge_bwd(
     const int tid = threadIdx.y * kBwdW + threadIdx.x;
     const bool active = X < wo && Y < ho;
     float pb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float inv_dtr = 1.f / c.d_tr, inv_shrink = 1.f / c.k_shrink;
+    const KConsts kc = kconsts_of(c);
     if (active) {
         const int Q = 2 * snum, Q2 = 4 * snum;
         const float fQ = (float)Q, invQ = 1.f / fQ, inv2Q = 0.5f / fQ;
@@ -375,13 +392,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_merge_bwd(
                 vbx += 0.5f * dbx[k] * dot;
                 vby += 0.5f * dby[k] * dot;
                 const float4 sh = __ldg(shape + (size_t)f * hw + (size_t)ty_[k] * g.wh + tx_[k]);
-                KGrad kg;
-                kernel_grad(sh, c, inv_dtr, inv_shrink, kg);
                 const float e1xx = 0.5f * (1.f + sh.z), e1xy = 0.5f * sh.w, e1yy = 0.5f * (1.f - sh.z);
                 const float oE1 = ob0 * e1xx + ob1 * e1xy + ob2 * e1yy;
                 const float bo1 = beta[k] * oE1, bo2 = beta[k] * ((ob0 + ob2) - oE1);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) pb[q] = fmaf(kg.dac[q], bo1, fmaf(kg.dal[q], bo2, pb[q]));
+                kernel_grad_acc(sh, c, kc, bo1, bo2, pb);
             }
             const size_t of = (size_t)f * po + op;
             vbar_pix[of] = (f == g.ref) ? make_float2(0.f, 0.f) : make_float2(vbx, vby);
@@ -409,54 +423,56 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_merge_bwd(
 // ---------------------------------------------------------------------------------------
 // Rhat-bar gathered onto base texels, then through the 5x5 argmin into R's parameters
 // ---------------------------------------------------------------------------------------
-__global__ void k_rhat_gather(const float *__restrict__ rhbar_pix, Geom g, int snum, int sden, int ho, int wo,
-                              float *__restrict__ rhbar_tex) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
-    if (u >= g.wh || f == g.ref) return;
+// The forward samples Rhat bilinearly on the base grid at (x0 - 1/2)/2 with clamped taps,
+// separably in x and y; its transpose gathers dL/dRhat-at-pixels onto texels the same
+// way: first along x, per output row (k_rhat_rows), then along y (k_rhat_cols).
+// rhat_range: the output pixels (along one axis) whose taps (clamped) reach texel t:
+// x0 within (2t - 1.5, 2t + 2.5), plus, at the border, every pixel clamped onto it.
+__device__ __forceinline__ void rhat_range(int t, int nt, int nout, int snum, int sden, int &lo, int &hi) {
+    lo = (int)floorf(((2.f * t - 1.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) - 1;
+    hi = (int)ceilf(((2.f * t + 2.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) + 1;
+    if (t == 0) lo = 0;
+    if (t == nt - 1) hi = nout - 1;
+    lo = max(lo, 0);
+    hi = min(hi, nout - 1);
+}
+// the forward's tap weight of output pixel X (along one axis) on texel t
+__device__ __forceinline__ float rhat_weight(int X, int t, int nt, int snum, int sden) {
     const int Q2 = 4 * snum;
     const float inv2Q = 0.25f / (float)snum;
-    // output pixels whose bilinear taps (clamped) reach texel u: x0 within (2u - 1.5, 2u + 2.5)
-    // plus, at the border, every pixel clamped onto it
-    auto xrange = [&](int t, int nt, int nout, int &lo, int &hi) {
-        lo = (int)floorf(((2.f * t - 1.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) - 1;
-        hi = (int)ceilf(((2.f * t + 2.5f) + 0.5f) * (float)snum / (float)sden - 0.5f) + 1;
-        if (t == 0) lo = 0;
-        if (t == nt - 1) hi = nout - 1;
-        lo = max(lo, 0);
-        hi = min(hi, nout - 1);
-    };
-    int xlo, xhi, ylo, yhi;
-    xrange(u, g.wh, wo, xlo, xhi);
-    xrange(v, g.hh, ho, ylo, yhi);
-    const size_t po = (size_t)ho * wo;
-    // the columns' weights once (the same for every row); a clamped border texel can
-    // collect more columns than fit, which then take the per-row path
-    constexpr int kMaxCols = 16;
-    float wxs[kMaxCols];
-    const bool cached = xhi - xlo < kMaxCols;
-    auto col_weight = [&](int X) -> float {
-        const int Px = 2 * sden * X + sden - snum;
-        const int rx = floor_div(Px - snum, Q2);
-        const float fx = (float)(Px - snum - rx * Q2) * inv2Q;
-        const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
-        return (rx0 == u ? 1.f - fx : 0.f) + (rx1 == u ? fx : 0.f);
-    };
-    if (cached)
-        for (int X = xlo; X <= xhi; ++X) wxs[X - xlo] = col_weight(X);
+    const int Px = 2 * sden * X + sden - snum;
+    const int rx = floor_div(Px - snum, Q2);
+    const float fx = (float)(Px - snum - rx * Q2) * inv2Q;
+    const int rx0 = clampi(rx, 0, nt - 1), rx1 = clampi(rx + 1, 0, nt - 1);
+    return (rx0 == t ? 1.f - fx : 0.f) + (rx1 == t ? fx : 0.f);
+}
+
+__global__ void k_rhat_rows(const float *__restrict__ rhbar_pix, Geom g, int snum, int sden, int ho, int wo,
+                            float *__restrict__ rows) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, f = blockIdx.z;
+    if (u >= g.wh || f == g.ref) return;
+    int lo, hi;
+    rhat_range(u, g.wh, wo, snum, sden, lo, hi);
+    const float *row = rhbar_pix + (size_t)f * ho * wo + (size_t)Y * wo;
     float acc = 0.f;
-    for (int Y = ylo; Y <= yhi; ++Y) {
-        const int Py = 2 * sden * Y + sden - snum;
-        const int ry = floor_div(Py - snum, Q2);
-        const float fy = (float)(Py - snum - ry * Q2) * inv2Q;
-        const int ry0 = clampi(ry, 0, g.hh - 1), ry1 = clampi(ry + 1, 0, g.hh - 1);
-        const float wy = (ry0 == v ? 1.f - fy : 0.f) + (ry1 == v ? fy : 0.f);
-        if (wy == 0.f) continue;
-        const float *row = rhbar_pix + (size_t)f * po + (size_t)Y * wo;
-        for (int X = xlo; X <= xhi; ++X) {
-            const float wx = cached ? wxs[X - xlo] : col_weight(X);
-            if (wx == 0.f) continue;
-            acc += wx * wy * row[X];
-        }
+    for (int X = lo; X <= hi; ++X) {
+        const float w = rhat_weight(X, u, g.wh, snum, sden);
+        if (w != 0.f) acc = fmaf(w, __ldg(row + X), acc);
+    }
+    rows[((size_t)f * ho + Y) * g.wh + u] = acc;
+}
+
+__global__ void k_rhat_cols(const float *__restrict__ rows, Geom g, int snum, int sden, int ho,
+                            float *__restrict__ rhbar_tex) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
+    if (u >= g.wh || f == g.ref) return;
+    int lo, hi;
+    rhat_range(v, g.hh, ho, snum, sden, lo, hi);
+    const float *col = rows + (size_t)f * ho * g.wh + u;
+    float acc = 0.f;
+    for (int Y = lo; Y <= hi; ++Y) {
+        const float w = rhat_weight(Y, v, g.hh, snum, sden);
+        if (w != 0.f) acc = fmaf(w, __ldg(col + (size_t)Y * g.wh), acc);
     }
     rhbar_tex[(size_t)f * g.hh * g.wh + (size_t)v * g.wh + u] = acc;
 }
@@ -545,12 +561,25 @@ __global__ void __launch_bounds__(kRedThreads) k_motion_reduce(const float2 *__r
         const int Y0 = tile_first(tyi, g.ty, ho, snum, sden, g.tile), Y1 = tile_first(tyi + 1, g.ty, ho, snum, sden, g.tile);
         const size_t po = (size_t)ho * wo;
         const float2 *vp = vbar_pix + (size_t)f * po;
-        for (int Y = Y0; Y < Y1; ++Y)
-            for (int X = X0 + lane; X < X1; X += 32) {
-                const float2 vb = vp[(size_t)Y * wo + X];
+        if (X1 - X0 <= 32) {
+            // one column per lane: the rows' loads are independent of the sums, so four
+            // are in flight at a time
+            const bool on = X0 + lane < X1;
+            const float2 *cp = vp + (size_t)Y0 * wo + X0 + (on ? lane : 0);
+#pragma unroll 4
+            for (int Y = Y0; Y < Y1; ++Y, cp += wo) {
+                const float2 vb = on ? __ldg(cp) : make_float2(0.f, 0.f);
                 comp_add(sx, cx, vb.x);
                 comp_add(sy, cy, vb.y);
             }
+        } else {
+            for (int Y = Y0; Y < Y1; ++Y)
+                for (int X = X0 + lane; X < X1; X += 32) {
+                    const float2 vb = vp[(size_t)Y * wo + X];
+                    comp_add(sx, cx, vb.x);
+                    comp_add(sy, cy, vb.y);
+                }
+        }
         const int ht = g.tile / 2;
         const int u0 = txi * ht, v0 = tyi * ht;
         const int u1 = (txi == g.tx - 1) ? g.wh : min(u0 + ht, g.wh), v1 = (tyi == g.ty - 1) ? g.hh : min(v0 + ht, g.hh);
@@ -613,6 +642,7 @@ size_t carve_backward(void *ws, const Geom &g, int ho, int wo, size_t fwd_bytes,
     B->vbar_tex = (float2 *)take(sizeof(float2) * g.n * hw);
     B->vbar_pix = (float2 *)take(sizeof(float2) * g.n * npx);
     B->rhbar_pix = (float *)take(sizeof(float) * g.n * npx);
+    B->rhbar_rows = (float *)take(sizeof(float) * g.n * (size_t)ho * g.wh);
     B->n_bwd_blocks = div_up(wo, kBwdW) * div_up(ho, kBwdH);
     B->n_rp_blocks = div_up(g.wh, kRpThreads) * g.hh * g.n;
     B->part6 = (double *)take(sizeof(double) * 6 * (size_t)B->n_bwd_blocks);
@@ -636,7 +666,8 @@ cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, co
     k_merge_bwd<<<dim3(div_up(wo, kBwdW), div_up(ho, kBwdH)), dim3(kBwdW, kBwdH), 0, s>>>(
         burst, mv, g, c, P.kern, B.shape, P.rhat, snum, sden, ho, wo, rgb, lden, grad_rgb, B.vbar_pix, B.rhbar_pix,
         B.part6);
-    k_rhat_gather<<<tex_grid, 128, 0, s>>>(B.rhbar_pix, g, snum, sden, ho, wo, B.rhbar_tex);
+    k_rhat_rows<<<dim3(div_up(g.wh, 128), ho, g.n), 128, 0, s>>>(B.rhbar_pix, g, snum, sden, ho, wo, B.rhbar_rows);
+    k_rhat_cols<<<tex_grid, 128, 0, s>>>(B.rhbar_rows, g, snum, sden, ho, B.rhbar_tex);
     k_rpath<<<dim3(div_up(g.wh, kRpThreads), g.hh, g.n), kRpThreads, 0, s>>>(B.rhbar_tex, B.flags, B.rb, g,
                                                                            B.vbar_tex, B.part2);
     k_motion_reduce<<<div_up(g.n * g.ty * g.tx, kRedThreads / 32), kRedThreads, 0, s>>>(B.vbar_pix, B.vbar_tex, g, snum,
