@@ -74,7 +74,13 @@ typedef struct {
     int tile;                       /* raw px of the motion field's tiles: 8, 16, 32, 64 */
 } hmfsr_merge_params;
 
-enum { HMFSR_OP_ALIGN = 0, HMFSR_OP_MERGE = 1, HMFSR_OP_MERGE_STAGES = 2, HMFSR_OP_MERGE_BACKWARD = 3 };
+enum {
+    HMFSR_OP_ALIGN = 0,
+    HMFSR_OP_MERGE = 1,
+    HMFSR_OP_MERGE_STAGES = 2,
+    HMFSR_OP_MERGE_BACKWARD = 3,
+    HMFSR_OP_ALIGN_MERGE = 4
+};
 
 /* Bytes of scratch the op needs for this burst (0 on invalid arguments).  For
  * HMFSR_OP_ALIGN, `tile` is the alignment tile; scale_num/scale_den are ignored.  For the
@@ -112,6 +118,26 @@ hmfsr_status hmfsr_align_quadfit(const uint16_t *burst_dev, const hmfsr_burst_de
 hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
                          const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
                          float *den_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* align + merge of one burst in one call (Sec. 3.2, then Sec. 5): the same outputs, bit
+ * for bit, as hmfsr_align followed by hmfsr_merge with these arguments.  The part of the
+ * merge that needs no motion (the 3x3 guide sums, the base frame's local statistics and
+ * the kernel covariances of Eq. 3-4) runs on `stream` while the alignment runs beside it
+ * on a library-owned stream of the highest priority (one per device and calling host
+ * thread, created on first use and kept until the thread exits); events join the two
+ * before the robustness (Eq. 5-9) and the accumulation (Eq. 1-2).  The call is ordered
+ * on `stream` like every other entry point and may be captured into a CUDA graph.  Two
+ * calls from one host thread share that stream, so their alignments run in call order.
+ *   aparams->tile must equal mparams->tile (HMFSR_ERR_INVALID_ARG otherwise).
+ *   motion_dev      float32 [n_frames][TY][TX][2], written, as hmfsr_align's.
+ *   motion_int_dev  optional, as hmfsr_align's.
+ *   rgb_dev, den_dev as hmfsr_merge's.
+ *   Workspace: hmfsr_workspace_size(HMFSR_OP_ALIGN_MERGE, desc, tile, num, den) bytes,
+ *   256-byte aligned: the alignment's and the merge's scratch side by side. */
+hmfsr_status hmfsr_align_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                               const hmfsr_align_params *aparams, const hmfsr_merge_params *mparams, int scale_num,
+                               int scale_den, float *motion_dev, int32_t *motion_int_dev, float *rgb_dev,
+                               float *den_dev, void *ws, size_t ws_bytes, void *stream);
 
 /* hmfsr_merge in two halves that share the workspace (same ws, desc and params):
  * prepare writes the per-frame planes (kernel covariances, robustness) into ws;

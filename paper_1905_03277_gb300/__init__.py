@@ -195,21 +195,46 @@ def merge_stages(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams 
 
 def align_merge(burst: torch.Tensor, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
                 align_params: AlignParams | None = None, device=None, out=None, white_level: int = 4095,
-                stream=None):
-    """The whole path, align then merge.  A host `burst` (ideally pinned) is copied to the
-    device first and the RGB result is copied back into `out` (or a new host tensor)."""
+                stream=None, with_motion: bool = False):
+    """The whole path in one call (hmfsr_align_merge): align, then merge, with the merge's
+    motion-free preparation overlapping the alignment.  A device `burst` gives a device RGB
+    (written into `out` when given); a host `burst` (ideally pinned) is copied to the
+    device first and the RGB copied back into `out` (or a new pinned host tensor).  With
+    `with_motion`, also the motion field (on the device)."""
+    L = _lib.load()
     params = params or MergeParams()
     align_params = align_params or AlignParams(tile=params.tile)
+    if align_params.tile != params.tile:
+        raise ValueError("the alignment tile and the merge tile must match")
     host = not burst.is_cuda
     dev_burst = burst.to(device or "cuda", non_blocking=True) if host else burst
-    motion = align(dev_burst, ref, align_params, white_level=white_level, stream=stream)
-    rgb = merge(dev_burst, motion, params, scale, ref, white_level=white_level, stream=stream)
-    if not host:
-        return rgb
-    if out is None:
-        out = torch.empty(rgb.shape, dtype=rgb.dtype, pin_memory=True)
-    out.copy_(rgb, non_blocking=True)
-    return out
+    d = _desc(dev_burst, ref, white_level)
+    n, h, w = dev_burst.shape
+    ty, tx = n_tiles(h, w, params.tile)
+    ho, wo = out_size(h, w, scale)
+    dv = dev_burst.device
+    motion = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=dv)
+    if not host and out is not None:
+        if not out.is_cuda or out.device != dv or out.dtype != torch.float32 or tuple(out.shape) != (3, ho, wo) \
+                or not out.is_contiguous():
+            raise ValueError(f"out must be contiguous float32 [3,{ho},{wo}] on the burst's device")
+        rgb = out
+    else:
+        rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=dv)
+    nbytes = L.hmfsr_workspace_size(_lib.OP_ALIGN_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
+    if nbytes == 0:
+        raise ValueError("unsupported burst shape, tile or scale")
+    ws = _workspace(dv, nbytes, stream)
+    ap, mp = align_params.c(), params.c()
+    _lib.check(L.hmfsr_align_merge(_ptr(dev_burst), ctypes.byref(d), ctypes.byref(ap), ctypes.byref(mp), scale[0],
+                                   scale[1], _ptr(motion), None, _ptr(rgb), None, _ptr(ws), ws.numel(),
+                                   _stream(dv, stream)), "hmfsr_align_merge")
+    if host:
+        if out is None:
+            out = torch.empty(rgb.shape, dtype=rgb.dtype, pin_memory=True)
+        out.copy_(rgb, non_blocking=True)
+        rgb = out
+    return (rgb, motion) if with_motion else rgb
 
 
 class AlignMergePipeline:
@@ -218,7 +243,7 @@ class AlignMergePipeline:
 
     `depth` device slots each hold a burst, its motion field and its RGB result.  Per
     `submit`, the host burst is copied in on a copy stream, aligned and merged (through
-    hmfsr_align and hmfsr_merge) on a compute stream, and the RGB copied back into the
+    hmfsr_align_merge) on a compute stream, and the RGB copied back into the
     caller's host tensor on a second copy stream; CUDA events order the three, so burst
     k + 1 travels in and burst k - 1 travels out while burst k is merged.  Host buffers
     should be pinned; the caller keeps a submitted burst and its output untouched until
@@ -241,15 +266,15 @@ class AlignMergePipeline:
         self.motions = [mk((n, ty, tx, 2), dtype=torch.float32) for _ in range(depth)]
         self.rgbs = [mk((3, ho, wo), dtype=torch.float32) for _ in range(depth)]
         self.desc = _desc(self.bursts[0], ref, white_level)
-        wa = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(self.desc), self.align_params.tile, 1, 1)
-        wm = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(self.desc), self.params.tile, scale[0], scale[1])
-        if wa == 0 or wm == 0:
+        if self.align_params.tile != self.params.tile:
+            raise ValueError("the alignment tile and the merge tile must match")
+        nb = L.hmfsr_workspace_size(_lib.OP_ALIGN_MERGE, ctypes.byref(self.desc), self.params.tile, scale[0],
+                                    scale[1])
+        if nb == 0:
             raise ValueError("unsupported burst shape, tile or scale")
-        self._ws_raw = mk(wa + wm + 512, dtype=torch.uint8)  # one compute stream: the slots share it
+        self._ws_raw = mk(nb + 256, dtype=torch.uint8)  # one compute stream: the slots share it
         base = (-self._ws_raw.data_ptr()) % 256
-        self.ws_align = self._ws_raw[base:base + wa]
-        off = base + ((wa + 255) // 256) * 256
-        self.ws_merge = self._ws_raw[off:off + wm]
+        self.ws = self._ws_raw[base:base + nb]
         self.h2d, self.compute, self.d2h = (torch.cuda.Stream(self.device) for _ in range(3))
         self.ev_in = [torch.cuda.Event() for _ in range(depth)]
         self.ev_done = [torch.cuda.Event() for _ in range(depth)]
@@ -274,11 +299,9 @@ class AlignMergePipeline:
         if self.used[i]:
             self.compute.wait_event(self.ev_out[i])  # the slot's previous RGB has been read out
         cs = ctypes.c_void_p(self.compute.cuda_stream)
-        _lib.check(L.hmfsr_align(_ptr(b), ctypes.byref(self.desc), ctypes.byref(self._ap), _ptr(mv), None,
-                                 _ptr(self.ws_align), self.ws_align.numel(), cs), "hmfsr_align")
-        _lib.check(L.hmfsr_merge(_ptr(b), ctypes.byref(self.desc), _ptr(mv), ctypes.byref(self._mp), self.scale[0],
-                                 self.scale[1], _ptr(rgb), None, _ptr(self.ws_merge), self.ws_merge.numel(), cs),
-                   "hmfsr_merge")
+        _lib.check(L.hmfsr_align_merge(_ptr(b), ctypes.byref(self.desc), ctypes.byref(self._ap),
+                                       ctypes.byref(self._mp), self.scale[0], self.scale[1], _ptr(mv), None, _ptr(rgb),
+                                       None, _ptr(self.ws), self.ws.numel(), cs), "hmfsr_align_merge")
         self.ev_done[i].record(self.compute)
         with torch.cuda.stream(self.d2h):
             self.d2h.wait_event(self.ev_done[i])

@@ -176,6 +176,43 @@ bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0;
 
 hmfsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HMFSR_OK : HMFSR_ERR_CUDA; }
 
+// The calling host thread's side stream on one device (highest priority) and the two
+// events that fork it from, and join it back to, the caller's stream.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~SideStream() {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+constexpr int kMaxSideDevices = 64;
+thread_local SideStream t_side[kMaxSideDevices];
+
+// nullptr when the device has none and one cannot be made
+SideStream *side_stream() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxSideDevices) return nullptr;
+    SideStream &ss = t_side[dev];
+    if (ss.s) return &ss;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        if (s) cudaStreamDestroy(s);
+        return nullptr;
+    }
+    ss.s = s;
+    ss.fork = a;
+    ss.join = b;
+    return &ss;
+}
+
 }  // namespace
 
 const CheckRanges &hmfsr::current_check_ranges() { return t_check; }
@@ -194,6 +231,12 @@ size_t hmfsr_workspace_size(int op, const hmfsr_burst_desc *desc, int tile, int 
         if (op == HMFSR_OP_MERGE && !valid_scale(scale_num, scale_den)) return 0;
         MergePlanes P;
         return carve_merge(nullptr, g, &P);
+    }
+    if (op == HMFSR_OP_ALIGN_MERGE) {
+        if (!valid_scale(scale_num, scale_den)) return 0;
+        AlignLevels L;
+        MergePlanes P;
+        return carve_align(nullptr, g, tile, 4, &L) + carve_merge(nullptr, g, &P);
     }
     if (op == HMFSR_OP_MERGE_BACKWARD) {
         if (!valid_scale(scale_num, scale_den)) return 0;
@@ -270,6 +313,50 @@ hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
     chk.add_ws(ws, need);
     cudaError_t e = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     if (e != cudaSuccess) return HMFSR_ERR_CUDA;
+    return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
+}
+
+hmfsr_status hmfsr_align_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                               const hmfsr_align_params *aparams, const hmfsr_merge_params *mparams, int scale_num,
+                               int scale_den, float *motion_dev, int32_t *motion_int_dev, float *rgb_dev,
+                               float *den_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !rgb_dev || !aligned4(burst_dev) || !aligned8(motion_dev) ||
+        !valid_align_params(aparams) || !valid_merge_params(mparams) || aparams->tile != mparams->tile ||
+        !valid_scale(scale_num, scale_den))
+        return HMFSR_ERR_INVALID_ARG;
+    Geom g = make_geom(desc, mparams->tile);
+    AlignLevels L;
+    MergePlanes P;
+    const size_t align_bytes = carve_align(nullptr, g, aparams->tile, 4, &L);
+    const size_t need = align_bytes + carve_merge(nullptr, g, &P);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_align(ws, g, aparams->tile, aparams->n_levels, &L);
+    carve_merge(static_cast<char *>(ws) + align_bytes, g, &P);
+    SideStream *side = side_stream();
+    if (!side) return HMFSR_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const MergeConsts c = consts_of(mparams);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(motion_int_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add_ws(ws, need);
+    // fork: the alignment on the side stream, the motion-free preparation here
+    if (cudaEventRecord(side->fork, s) != cudaSuccess || cudaStreamWaitEvent(side->s, side->fork, 0) != cudaSuccess)
+        return HMFSR_ERR_CUDA;
+    const cudaError_t ea = launch_align(burst_dev, g, *aparams, L, motion_dev, motion_int_dev, side->s);
+    // the join is recorded even after a failed launch, so the side stream never runs ahead
+    // of a later fork unordered
+    const cudaError_t ej = cudaEventRecord(side->join, side->s);
+    const cudaError_t ef = launch_merge_prep_frames(burst_dev, g, c, P, s);
+    const cudaError_t ew = cudaStreamWaitEvent(s, side->join, 0);
+    if (ea != cudaSuccess || ej != cudaSuccess || ef != cudaSuccess || ew != cudaSuccess) return HMFSR_ERR_CUDA;
+    if (launch_merge_prep_motion(motion_dev, g, c, P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
 }
 

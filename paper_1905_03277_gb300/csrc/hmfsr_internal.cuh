@@ -194,9 +194,15 @@ cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align
 cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p,
                                  const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s);
 
-// merge
+// merge; launch_merge_prep == launch_merge_prep_frames (the motion-free part: 3x3 sums,
+// base statistics, kernel covariances, high-frequency flags) + launch_merge_prep_motion
+// (motion strength and robustness)
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s);
+cudaError_t launch_merge_prep_frames(const uint16_t *burst, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                                     cudaStream_t s);
+cudaError_t launch_merge_prep_motion(const float *motion, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                                     cudaStream_t s);
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
                                int snum, int sden, float *rgb, float *den, cudaStream_t s);
 cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *omega, float *rhat, cudaStream_t s);

@@ -165,22 +165,27 @@ int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, i
 
 }  // namespace
 
-cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
-                              const MergePlanes &P, cudaStream_t s) {
-    StageRange range("hmfsr merge: kernel covariance and robustness");
+cudaError_t launch_merge_prep_frames(const uint16_t *burst, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                                     cudaStream_t s) {
+    StageRange range("hmfsr merge: 3x3 sums, base statistics and kernel covariance");
     CheckedLaunches checked(s);
     const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
                                     g.hh, 8, stage::kPrepStrip);
     k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
                                                                                    P.kern, prep_rows);
+    if (c.hf_loss > 0.f && g.n > 1)
+        k_hf_flag<<<dim3(div_up(g.wh, 128), g.hh), 128, 0, s>>>(burst, P.s1, g, c.hf_loss, P.hf_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_prep_motion(const float *motion, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                                     cudaStream_t s) {
+    StageRange range("hmfsr merge: robustness");
+    CheckedLaunches checked(s);
     int nt = g.n * g.ty * g.tx;
     const float2 *mv = reinterpret_cast<const float2 *>(motion);
     k_strength<<<div_up(nt, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, c.s1, c.s2, P.s_tile);
-    const unsigned char *hf = nullptr;
-    if (c.hf_loss > 0.f && g.n > 1) {
-        k_hf_flag<<<dim3(div_up(g.wh, 128), g.hh), 128, 0, s>>>(burst, P.s1, g, c.hf_loss, P.hf_flag);
-        hf = P.hf_flag;
-    }
+    const unsigned char *hf = (c.hf_loss > 0.f && g.n > 1) ? P.hf_flag : nullptr;
     if (g.n > 1) {
         const int slots = hf ? strip_slots(SK_ROB_HF, (const void *)k_rob<true>)
                              : strip_slots(SK_ROB, (const void *)k_rob<false>);
@@ -193,6 +198,13 @@ cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const 
             k_rob<false><<<grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, g, c.t, P.rhat, nullptr, c.m_th, rows);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                              const MergePlanes &P, cudaStream_t s) {
+    const cudaError_t e = launch_merge_prep_frames(burst, g, c, P, s);
+    if (e != cudaSuccess) return e;
+    return launch_merge_prep_motion(motion, g, c, P, s);
 }
 
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,

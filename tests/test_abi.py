@@ -135,6 +135,32 @@ def test_align_rejects_bad_arguments_on_host(L):
     assert call(hm.AlignParams(), ws_bytes=10) == -3
 
 
+def test_align_merge_rejects_bad_arguments_on_host(L):
+    d = desc()
+    ws_a = L.hmfsr_workspace_size(_lib.OP_ALIGN, ctypes.byref(d), 16, 1, 1)
+    ws_m = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), 16, 2, 1)
+    assert L.hmfsr_workspace_size(_lib.OP_ALIGN_MERGE, ctypes.byref(d), 16, 2, 1) == ws_a + ws_m
+    assert L.hmfsr_workspace_size(_lib.OP_ALIGN_MERGE, ctypes.byref(d), 16, 1, 2) == 0
+
+    def call(ap=None, mp=None, snum=1, sden=1, motion=16, rgb=16, ws_bytes=1 << 40, dd=d):
+        a, m = (ap or hm.AlignParams()).c(), (mp or hm.MergeParams()).c()
+        v = lambda x: ctypes.c_void_p(x) if x else None
+        return L.hmfsr_align_merge(v(16), ctypes.byref(dd), ctypes.byref(a), ctypes.byref(m), snum, sden, v(motion),
+                                   None, v(rgb), None, v(256), ws_bytes, None)
+
+    # every case returns before any CUDA call (fake pointers, never dereferenced)
+    assert call(ap=hm.AlignParams(tile=32)) == -1            # alignment and merge tiles differ
+    assert call(ap=hm.AlignParams(tile=32), mp=hm.MergeParams(tile=16)) == -1
+    assert call(ap=hm.AlignParams(n_levels=0)) == -1
+    assert call(mp=hm.MergeParams(k_shrink=-1.0)) == -1
+    assert call(snum=1, sden=2) == -1
+    assert call(motion=0) == -1
+    assert call(motion=20) == -1                              # motion not 8-byte aligned
+    assert call(rgb=0) == -1
+    assert call(dd=desc(cfa=1)) == -2
+    assert call(ws_bytes=ws_a + ws_m - 1) == -3
+
+
 def test_product_path_does_not_use_the_oracle():
     src_dir = os.path.join(ROOT, "paper_1905_03277_gb300")
     for fn in os.listdir(src_dir):
