@@ -16,23 +16,141 @@ __global__ void k_down(const uint16_t *__restrict__ src, int sh, int sw, uint16_
     stage::down(src, sh, sw, dst, dh, dw, fct, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
 }
 
-template <int T, int RAD>
+template <int T, int RAD, int PART>
 __global__ void __launch_bounds__(64) k_ssd_rows(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                                  const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                                  int2 *__restrict__ vec) {
-    stage::ssd_rows<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec,
-                            blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+    stage::ssd_rows<T, RAD, PART>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec,
+                                  blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
 }
 
 // 4 warps of 32 / (2 RAD + 1) tiles each
-template <int T, int RAD>
+template <int T, int RAD, int PART>
 __global__ void __launch_bounds__(128) k_ssd_group(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                                    const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                                    int2 *__restrict__ vec) {
     constexpr int kG = 32 / (2 * RAD + 1);
     const int warp = blockIdx.x * 4 + (threadIdx.x >> 5);
-    stage::ssd_group<T, RAD>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, warp * kG, threadIdx.x & 31,
-                             blockIdx.y);
+    stage::ssd_group<T, RAD, PART>(img, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, vec, warp * kG,
+                                   threadIdx.x & 31, blockIdx.y);
+}
+
+// Block matching of one level with each warp's candidate windows staged in shared memory.
+// A warp takes kG = 32 / (2 RAD + 1) tiles, as k_ssd_group does (lane d of a group takes
+// the offsets dy = d - RAD).  The warp first copies, for each of its tiles, the T + 2 RAD
+// candidate rows of T + 2 RAD texels and the tile's T reference rows into shared memory
+// (as ints, each row once, through 16-byte loads where the rows allow); every lane then
+// reads its rows from there with 16-byte shared loads.  Same sums and keys as ssd_group,
+// so the same vectors.
+template <int T, int RAD>
+struct StagedSsd {
+    static constexpr int kW = 2 * RAD + 1, kG = 32 / kW, kA = T + 2 * RAD;
+    static constexpr int kS = ((kA + 3) & ~3) + 4;  // window row stride (ints): 16-byte rows, banks spread
+    static constexpr int kWin = kA * kS;
+    static constexpr int kTile = kWin + T * T;      // ints per tile: window, then the T x T reference
+    static constexpr int kWarps = 4;
+    static constexpr size_t kBytes = sizeof(int) * kWarps * kG * kTile;
+};
+
+template <int T, int RAD, int PART>
+__global__ void __launch_bounds__(128) k_ssd_staged(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                                    const int2 *__restrict__ parent, int pty, int ptx, int fsh,
+                                                    int ref, int2 *__restrict__ vec) {
+    using S = StagedSsd<T, RAD>;
+    constexpr int kW = S::kW, kG = S::kG, kA = S::kA, kS = S::kS;
+    static_assert(T % 4 == 0 && kS % 4 == 0, "16-byte shared rows");
+    __shared__ __align__(16) int sm[S::kWarps][kG][S::kTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, f = blockIdx.y;
+    const int tile0 = (blockIdx.x * S::kWarps + warp) * kG, ntiles = lty * ltx;
+    const int grp = lane / kW, d = lane - grp * kW;
+    const int tile = tile0 + grp;
+    const bool active = grp < kG && tile < ntiles;
+    if (f == ref) {
+        if (active && d == 0) HMFSR_ST(vec + (size_t)f * ntiles + tile, make_int2(0, 0));
+        return;
+    }
+    const uint16_t *R = img + (size_t)ref * lh * lw;
+    const uint16_t *A = img + (size_t)f * lh * lw;
+    const bool al16 = stage::rows_aligned16(img, lw);
+    // candidate rows: kG x kA rows over the warp's lanes
+    for (int r = lane; r < kG * kA; r += 32) {
+        const int g = r / kA, rr = r - g * kA, t = tile0 + g;
+        if (t >= ntiles) continue;
+        const int ty = t / ltx, tx = t - ty * ltx;
+        const int2 cc = stage::ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
+        const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD;
+        const bool inside = stage::ssd_inside(x0, xa, T, RAD, lw);
+        int v[kA];
+        stage::load_row2(A + (size_t)clampi(y0 + cc.y - RAD + rr, 0, lh - 1) * lw, xa, lw, inside, inside && al16, v);
+        int4 *dst = reinterpret_cast<int4 *>(&sm[warp][g][rr * kS]);
+#pragma unroll
+        for (int i = 0; i < kA / 4; ++i) dst[i] = make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        if constexpr (kA % 4 != 0) {
+#pragma unroll
+            for (int i = kA & ~3; i < kA; ++i) sm[warp][g][rr * kS + i] = v[i];
+        }
+    }
+    // reference rows: kG x T rows
+    for (int r = lane; r < kG * T; r += 32) {
+        const int g = r / T, j = r - g * T, t = tile0 + g;
+        if (t >= ntiles) continue;
+        const int ty = t / ltx, tx = t - ty * ltx;
+        const int x0 = tx * T, y0 = ty * T;
+        const bool inside = x0 + T <= lw;
+        int v[T];
+        stage::load_row2<T, T % 8 == 0>(R + (size_t)min(y0 + j, lh - 1) * lw, x0, lw, inside, inside && al16, v);
+        int4 *dst = reinterpret_cast<int4 *>(&sm[warp][g][S::kWin + j * T]);
+#pragma unroll
+        for (int i = 0; i < T / 4; ++i) dst[i] = make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+    __syncwarp();
+    unsigned long long best = ~0ull;
+    if (active) {
+        const int *win = &sm[warp][grp][d * kS];  // candidate row j + d of the window at row j
+        const int *rf = &sm[warp][grp][S::kWin];
+        stage::SsdAcc<T, PART> acc[kW];
+#pragma unroll 2
+        for (int j = 0; j < T; ++j) {
+            int rv[T], av[kA];
+            const int4 *pr = reinterpret_cast<const int4 *>(rf + j * T);
+            const int4 *pa = reinterpret_cast<const int4 *>(win + j * kS);
+#pragma unroll
+            for (int i = 0; i < T / 4; ++i) {
+                const int4 q = pr[i];
+                rv[4 * i] = q.x; rv[4 * i + 1] = q.y; rv[4 * i + 2] = q.z; rv[4 * i + 3] = q.w;
+            }
+#pragma unroll
+            for (int i = 0; i < kA / 4; ++i) {
+                const int4 q = pa[i];
+                av[4 * i] = q.x; av[4 * i + 1] = q.y; av[4 * i + 2] = q.z; av[4 * i + 3] = q.w;
+            }
+            if constexpr (kA % 4 != 0) {
+#pragma unroll
+                for (int i = kA & ~3; i < kA; ++i) av[i] = win[j * kS + i];
+            }
+#pragma unroll
+            for (int k = 0; k < kW; ++k) acc[k].add(rv, av + k, j);
+        }
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            const unsigned long long key = stage::ssd_key(acc[k].total, k - RAD, d - RAD);
+            best = key < best ? key : best;
+        }
+    }
+    // idle lanes read the last group (their result is unused)
+    const int base = min(grp, kG - 1) * kW;
+    unsigned long long m = ~0ull;
+#pragma unroll
+    for (int k = 0; k < kW; ++k) {
+        const unsigned long long o = __shfl_sync(0xffffffffu, best, base + k);
+        m = o < m ? o : m;
+    }
+    if (active && d == 0) {
+        const int ty = tile / ltx, tx = tile - ty * ltx;
+        const int2 cc = stage::ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
+        const int bdx = (int)(m & 15ull) - 7, bdy = (int)((m >> 4) & 15ull) - 7;
+        HMFSR_ST(vec + (size_t)f * ntiles + tile, make_int2(cc.x + bdx, cc.y + bdy));
+    }
 }
 
 template <int T>
@@ -44,11 +162,12 @@ __global__ void __launch_bounds__(128) k_quadfit(const uint16_t *__restrict__ L0
 }
 
 template <int T>
-__global__ void k_lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+__global__ void __launch_bounds__(128, 6) k_lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
                            const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
                            int32_t *__restrict__ motion_int) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    stage::lk_group<T>(L0, lh, lw, lty, ltx, vec0, ref, iters, motion, motion_int, t / T, threadIdx.x & 31, blockIdx.y);
+    stage::lk_group<T>(L0, lh, lw, lty, ltx, vec0, ref, iters, motion, motion_int, t / (T / 2), threadIdx.x & 31,
+                       blockIdx.y);
 }
 
 template <int T>
@@ -66,19 +185,31 @@ static const int kFactors[3] = {2, 4, 4};
 // dy spread over the lanes of a group (measured at 12 MP on level 1, 96k tile-frames: the
 // grouped form 9 us faster than one thread per tile, both at 64 registers).
 
-template <int T, int RAD>
-static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
+template <int T, int RAD, int PART>
+static void launch_ssd_part(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
     const int tiles = L.lty[l] * L.ltx[l];
     const int2 *parent = top ? nullptr : L.vec[l + 1];
     const int pty = top ? 0 : L.lty[l + 1], ptx = top ? 0 : L.ltx[l + 1];
     if constexpr (RAD <= 2 && T <= 8) {
-        k_ssd_rows<T, RAD><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l],
-                                                                     parent, pty, ptx, fsh, ref, L.vec[l]);
+        k_ssd_rows<T, RAD, PART><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(
+            L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
+    } else if constexpr (T <= 16 && StagedSsd<T, RAD>::kBytes <= 40 * 1024) {
+        constexpr int kTilesPerBlock = StagedSsd<T, RAD>::kWarps * StagedSsd<T, RAD>::kG;
+        k_ssd_staged<T, RAD, PART><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
+            L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
     } else {
         constexpr int kTilesPerBlock = 4 * (32 / (2 * RAD + 1));
-        k_ssd_group<T, RAD><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
+        k_ssd_group<T, RAD, PART><<<dim3(div_up(tiles, kTilesPerBlock), n), 128, 0, s>>>(
             L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
     }
+}
+
+// Level values are at most 4 WL (a level-0 texel sums four samples <= WL; coarser levels
+// average): below 2^14 for WL <= 4095, where 16 squared differences fit a 32-bit partial.
+template <int T, int RAD>
+static void launch_ssd(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, int wl, cudaStream_t s) {
+    if (wl <= 4095) launch_ssd_part<T, RAD, 16>(L, l, n, ref, fsh, top, s);
+    else launch_ssd_part<T, RAD, 4>(L, l, n, ref, fsh, top, s);
 }
 
 template <int T>
@@ -90,20 +221,20 @@ static void run_search(const Geom &g, const hmfsr_align_params &p, const AlignLe
         const bool top = (l == L.n_levels - 1);
         const int fsh = top ? 0 : kShift[l];
         switch (p.radius[l]) {
-            case 0: launch_ssd<T, 0>(L, l, n, g.ref, fsh, top, s); break;
-            case 1: launch_ssd<T, 1>(L, l, n, g.ref, fsh, top, s); break;
-            case 2: launch_ssd<T, 2>(L, l, n, g.ref, fsh, top, s); break;
-            case 3: launch_ssd<T, 3>(L, l, n, g.ref, fsh, top, s); break;
-            case 4: launch_ssd<T, 4>(L, l, n, g.ref, fsh, top, s); break;
-            case 5: launch_ssd<T, 5>(L, l, n, g.ref, fsh, top, s); break;
-            case 6: launch_ssd<T, 6>(L, l, n, g.ref, fsh, top, s); break;
-            default: launch_ssd<T, stage::kMaxRad>(L, l, n, g.ref, fsh, top, s); break;
+            case 0: launch_ssd<T, 0>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 1: launch_ssd<T, 1>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 2: launch_ssd<T, 2>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 3: launch_ssd<T, 3>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 4: launch_ssd<T, 4>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 5: launch_ssd<T, 5>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            case 6: launch_ssd<T, 6>(L, l, n, g.ref, fsh, top, g.wl, s); break;
+            default: launch_ssd<T, stage::kMaxRad>(L, l, n, g.ref, fsh, top, g.wl, s); break;
         }
     }
     const int tiles0 = L.lty[0] * L.ltx[0];
     if constexpr (T <= 8)
-        k_lk_group<T><<<dim3(div_up(tiles0 * T, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
-                                                                   L.vec[0], g.ref, p.lk_iters, motion, motion_int);
+        k_lk_group<T><<<dim3(div_up(tiles0 * (T / 2), 128), n), 128, 0, s>>>(
+            L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0], L.vec[0], g.ref, p.lk_iters, motion, motion_int);
     else
         k_lk<T><<<dim3(div_up(tiles0 * 32, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
                                                            L.vec[0], g.ref, p.lk_iters, motion, motion_int);

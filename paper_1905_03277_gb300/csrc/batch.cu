@@ -33,7 +33,7 @@ constexpr int kMaxDeps = 6;
 // queue order: every stage after the stages it depends on
 constexpr int kOrder[] = {S_LUMA, S_PREP, S_DOWN1, S_DOWN2, S_DOWN3, S_SSD3, S_SSD2, S_SSD1, S_SSD0,
                           S_LK, S_STRENGTH, S_ROB, S_MERGE};
-constexpr int kLkTiles = kBatchThreads / 8;  // Lucas-Kanade tiles per sub-item (8 lanes per tile)
+constexpr int kLkTiles = kBatchThreads / 4;  // Lucas-Kanade tiles per sub-item (4 lanes per tile)
 
 struct BatchBurst {
     const uint16_t *burst;
@@ -190,7 +190,7 @@ __device__ __forceinline__ void run_sub(const BatchBurst &b, int s, int k, int t
         }
         case S_LK: {
             const int per = div_up(b.L.lty[0] * b.L.ltx[0], kLkTiles);
-            const int f = k / per, tile = (k - f * per) * kLkTiles + tid / 8;
+            const int f = k / per, tile = (k - f * per) * kLkTiles + tid / 4;
             stage::lk_group<8>(b.L.img[0], b.L.lh[0], b.L.lw[0], b.L.lty[0], b.L.ltx[0], b.L.vec[0], g.ref,
                                b.lk_iters, b.motion, nullptr, tile, tid & 31, f);
             break;

@@ -113,16 +113,18 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// Squared differences of one tile row against one candidate row, exactly: luminance
-// values are below 2^15 (4 x 7281), so 4 squared differences fit 32 bits.
-template <int T>
+// Squared differences of one tile row against one candidate row, exactly, summed PART at
+// a time in 32 bits before the 64-bit total: with level values v <= vmax, PART terms fit
+// 32 bits while PART vmax^2 < 2^32 (PART = 4 for vmax < 2^15, any white level up to
+// 7281; PART = 16 for vmax < 2^14, white levels up to 4095).
+template <int T, int PART = 4>
 __device__ __forceinline__ unsigned long long row_ssd(const int *rv, const int *av) {
     unsigned long long acc = 0;
 #pragma unroll
-    for (int i0 = 0; i0 < T; i0 += 4) {
+    for (int i0 = 0; i0 < T; i0 += PART) {
         unsigned int part = 0;
 #pragma unroll
-        for (int i = i0; i < i0 + 4 && i < T; ++i) {
+        for (int i = i0; i < i0 + PART && i < T; ++i) {
             const int d = rv[i] - av[i];
             part += (unsigned int)(d * d);
         }
@@ -130,6 +132,39 @@ __device__ __forceinline__ unsigned long long row_ssd(const int *rv, const int *
     }
     return acc;
 }
+
+// One tile row's squared differences as a 32-bit partial (T <= PART terms).
+template <int T>
+__device__ __forceinline__ unsigned int row_sq32(const int *rv, const int *av) {
+    unsigned int part = 0;
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        const int d = rv[i] - av[i];
+        part += (unsigned int)(d * d);
+    }
+    return part;
+}
+
+// Exact SSD accumulation over the rows of a tile for one candidate: rows are summed into a
+// 32-bit partial PART / T rows at a time (T <= PART), else split PART terms at a time.
+template <int T, int PART>
+struct SsdAcc {
+    static constexpr int kRows = PART >= T ? PART / T : 1;  // rows per 32-bit partial
+    unsigned long long total = 0;
+    unsigned int part = 0;
+    // add row j (0 <= j < T) of the tile
+    __device__ __forceinline__ void add(const int *rv, const int *av, int j) {
+        if constexpr (PART >= T) {
+            part += row_sq32<T>(rv, av);
+            if ((j + 1) % kRows == 0 || j == T - 1) {
+                total += part;
+                part = 0;
+            }
+        } else {
+            total += row_ssd<T, PART>(rv, av);
+        }
+    }
+};
 
 // The block-matching key: smallest SSD, then smallest |dx| + |dy|, then smaller dy, then
 // smaller dx -- one 64-bit key whose minimum decides.
@@ -165,6 +200,76 @@ __device__ __forceinline__ void load_row(const uint16_t *__restrict__ row, int x
     }
 }
 
+// N consecutive values of one level row from column x through whole 16-byte loads: the
+// chunks that cover [x, x + N) are read and the N values picked out at the run-time offset
+// x mod 8 (selects on its bits, then a 16-bit funnel shift), so a warp's loads touch each
+// sector once instead of once per 2-byte value.  Needs a row that starts on a 16-byte
+// boundary and 0 <= x, x + N <= its width (a multiple of 8), so no chunk leaves the row.
+// kX8: x is a multiple of 8 (no picking).
+template <int N, bool kX8 = false>
+__device__ __forceinline__ void load_row_vec(const uint16_t *__restrict__ row, int x, int (&v)[N]) {
+    if constexpr (kX8) {
+        static_assert(N % 8 == 0, "whole chunks");
+        const uint4 *p = reinterpret_cast<const uint4 *>(row + x);
+#pragma unroll
+        for (int c = 0; c < N / 8; ++c) {
+            const uint4 q = HMFSR_LDG(p + c);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[8 * c + 2 * k] = (int)(w[k] & 0xffffu);
+                v[8 * c + 2 * k + 1] = (int)(w[k] >> 16);
+            }
+        }
+    } else {
+        constexpr int kC = (N + 14) / 8;  // chunks at the largest offset, 7
+        constexpr int kO = (N + 1) / 2;   // 32-bit words of output
+        static_assert(kO + 3 < 4 * kC, "the selects stay inside the loaded words");
+        const int s = x & 7;
+        const uint4 *p = reinterpret_cast<const uint4 *>(row + (x - s));
+        uint32_t w[4 * kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) {
+            // chunk c holds values 8 c - s .. 8 c - s + 7 of the span: needed iff 8 c < s + N
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (c < kC - 1 || s + N > 8 * c) q = HMFSR_LDG(p + c);
+            w[4 * c] = q.x;
+            w[4 * c + 1] = q.y;
+            w[4 * c + 2] = q.z;
+            w[4 * c + 3] = q.w;
+        }
+        const int qw = s >> 1;
+        const unsigned int sh = (unsigned int)(s & 1) * 16u;
+        uint32_t X[kO + 1];  // X[m] = w[qw + m]
+#pragma unroll
+        for (int m = 0; m <= kO; ++m) {
+            const uint32_t a = (qw & 1) ? w[m + 1] : w[m];
+            const uint32_t b = (qw & 1) ? w[m + 3] : w[m + 2];
+            X[m] = (qw & 2) ? b : a;
+        }
+#pragma unroll
+        for (int k = 0; k < kO; ++k) {
+            const uint32_t W = __funnelshift_r(X[k], X[k + 1], sh);
+            v[2 * k] = (int)(W & 0xffffu);
+            if (2 * k + 1 < N) v[2 * k + 1] = (int)(W >> 16);
+        }
+    }
+}
+
+// load_row, through load_row_vec where `vec` says the rows are 16-byte aligned and the span
+// lies inside the row
+template <int N, bool kX8 = false>
+__device__ __forceinline__ void load_row2(const uint16_t *__restrict__ row, int x, int lw, bool inside, bool vec,
+                                          int (&v)[N]) {
+    if (vec) load_row_vec<N, kX8>(row, x, v);
+    else load_row(row, x, lw, inside, v);
+}
+
+// a level's rows start on 16-byte boundaries
+__device__ __forceinline__ bool rows_aligned16(const uint16_t *img, int lw) {
+    return (lw & 7) == 0 && (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+}
+
 // the tile's columns x0 .. x0 + T - 1 and its candidates' xa .. xa + T + 2 RAD - 1 all lie
 // inside a level row of lw texels
 __device__ __forceinline__ bool ssd_inside(int x0, int xa, int T, int RAD, int lw) {
@@ -177,7 +282,7 @@ __device__ __forceinline__ bool ssd_inside(int x0, int xa, int T, int RAD, int l
 // 2 RAD + 1 candidate sums of that row of offsets in registers.  Ties: smallest SSD,
 // then smallest |dx| + |dy|, then smaller dy, then smaller dx -- one 64-bit key whose
 // minimum decides.
-template <int T, int RAD>
+template <int T, int RAD, int PART = 4>
 __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                     const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                     int2 *__restrict__ vec, int tile, int f) {
@@ -195,23 +300,22 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
     const uint16_t *A = img + (size_t)f * lh * lw;
     const int x0 = tx * T, y0 = ty * T, xa = x0 + cx - RAD;
     const bool inside = ssd_inside(x0, xa, T, RAD, lw);
+    const bool vrow = inside && rows_aligned16(img, lw);
     unsigned long long best = ~0ull;
     for (int dy = -RAD; dy <= RAD; ++dy) {
-        unsigned long long acc[kW];
-#pragma unroll
-        for (int k = 0; k < kW; ++k) acc[k] = 0;
+        SsdAcc<T, PART> acc[kW];
         for (int j = 0; j < T; ++j) {
             const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
             const uint16_t *arow = A + (size_t)clampi(y0 + j + cy + dy, 0, lh - 1) * lw;
             int rv[T], av[T + 2 * RAD];
-            load_row(rrow, x0, lw, inside, rv);
-            load_row(arow, xa, lw, inside, av);
+            load_row2<T, T % 8 == 0>(rrow, x0, lw, inside, vrow, rv);
+            load_row2(arow, xa, lw, inside, vrow, av);
 #pragma unroll
-            for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
+            for (int k = 0; k < kW; ++k) acc[k].add(rv, av + k, j);
         }
 #pragma unroll
         for (int k = 0; k < kW; ++k) {
-            const unsigned long long key = ssd_key(acc[k], k - RAD, dy);
+            const unsigned long long key = ssd_key(acc[k].total, k - RAD, dy);
             best = key < best ? key : best;
         }
     }
@@ -222,7 +326,7 @@ __device__ __forceinline__ void ssd(const uint16_t *__restrict__ img, int lh, in
 // The same search with the tile rows outermost (small radii): each candidate row is read
 // once and serves the 2 RAD + 1 offsets dy that use it; a rolling window of 2 RAD + 1
 // candidate rows stays in registers.  Same sums and keys as ssd(), so the same vector.
-template <int T, int RAD>
+template <int T, int RAD, int PART = 4>
 __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                          const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                          int2 *__restrict__ vec, int tile, int f) {
@@ -239,26 +343,25 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
     const uint16_t *A = img + (size_t)f * lh * lw;
     const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD;
     const bool inside = ssd_inside(x0, xa, T, RAD, lw);
-    unsigned long long acc[kW][kW];
-#pragma unroll
-    for (int a = 0; a < kW; ++a)
-#pragma unroll
-        for (int b = 0; b < kW; ++b) acc[a][b] = 0;
+    // per-thread 16-byte row loads measured slower here (fewer loads in flight); the
+    // 2-byte loads of 32 neighbouring tiles share their sectors in L1
+    const bool vrow = false;
+    SsdAcc<T, PART> acc[kW][kW];
     int av[kW][kA];  // av[d]: candidate row y0 + j + d - RAD (+ the centre's dy)
 #pragma unroll
     for (int d = 0; d < kW - 1; ++d) {
         const uint16_t *arow = A + (size_t)clampi(y0 + d - RAD + cc.y, 0, lh - 1) * lw;
-        load_row(arow, xa, lw, inside, av[d]);
+        load_row2(arow, xa, lw, inside, vrow, av[d]);
     }
 #pragma unroll
     for (int j = 0; j < T; ++j) {
-        load_row(A + (size_t)clampi(y0 + j + RAD + cc.y, 0, lh - 1) * lw, xa, lw, inside, av[kW - 1]);
+        load_row2(A + (size_t)clampi(y0 + j + RAD + cc.y, 0, lh - 1) * lw, xa, lw, inside, vrow, av[kW - 1]);
         int rv[T];
-        load_row(R + (size_t)min(y0 + j, lh - 1) * lw, x0, lw, inside, rv);
+        load_row2<T, T % 8 == 0>(R + (size_t)min(y0 + j, lh - 1) * lw, x0, lw, inside, vrow, rv);
 #pragma unroll
         for (int d = 0; d < kW; ++d)
 #pragma unroll
-            for (int k = 0; k < kW; ++k) acc[d][k] += row_ssd<T>(rv, av[d] + k);
+            for (int k = 0; k < kW; ++k) acc[d][k].add(rv, av[d] + k, j);
 #pragma unroll
         for (int d = 0; d < kW - 1; ++d)
 #pragma unroll
@@ -269,7 +372,7 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
     for (int d = 0; d < kW; ++d)
 #pragma unroll
         for (int k = 0; k < kW; ++k) {
-            const unsigned long long key = ssd_key(acc[d][k], k - RAD, d - RAD);
+            const unsigned long long key = ssd_key(acc[d][k].total, k - RAD, d - RAD);
             best = key < best ? key : best;
         }
     const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
@@ -281,7 +384,7 @@ __device__ __forceinline__ void ssd_rows(const uint16_t *__restrict__ img, int l
 // its remaining lanes idle.  Each lane gathers the group's keys by shuffles and takes
 // their minimum; the group's first lane writes.  Every lane of the warp calls this; f is
 // the same for the whole warp.
-template <int T, int RAD>
+template <int T, int RAD, int PART = 4>
 __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
                                           const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
                                           int2 *__restrict__ vec, int tile0, int lane, int f) {
@@ -303,21 +406,20 @@ __device__ __forceinline__ void ssd_group(const uint16_t *__restrict__ img, int 
         const uint16_t *A = img + (size_t)f * lh * lw;
         const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD;
         const bool inside = ssd_inside(x0, xa, T, RAD, lw);
-        unsigned long long acc[kW];
-#pragma unroll
-        for (int k = 0; k < kW; ++k) acc[k] = 0;
+        const bool vrow = inside && rows_aligned16(img, lw);
+        SsdAcc<T, PART> acc[kW];
         for (int j = 0; j < T; ++j) {
             const uint16_t *rrow = R + (size_t)min(y0 + j, lh - 1) * lw;
             const uint16_t *arow = A + (size_t)clampi(y0 + j + cc.y + dy, 0, lh - 1) * lw;
             int rv[T], av[T + 2 * RAD];
-            load_row(rrow, x0, lw, inside, rv);
-            load_row(arow, xa, lw, inside, av);
+            load_row2<T, T % 8 == 0>(rrow, x0, lw, inside, vrow, rv);
+            load_row2(arow, xa, lw, inside, vrow, av);
 #pragma unroll
-            for (int k = 0; k < kW; ++k) acc[k] += row_ssd<T>(rv, av + k);
+            for (int k = 0; k < kW; ++k) acc[k].add(rv, av + k, j);
         }
 #pragma unroll
         for (int k = 0; k < kW; ++k) {
-            const unsigned long long key = ssd_key(acc[k], k - RAD, dy);
+            const unsigned long long key = ssd_key(acc[k].total, k - RAD, dy);
             best = key < best ? key : best;
         }
     }
@@ -422,19 +524,21 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
     }
 }
 
-// The same refinement with T lanes per tile (T <= 8, 32 / T tiles per warp): lane c of a
-// group owns column c of the tile and walks its T rows, so the bilinear samples of a
-// column share their rows (T + 1 rows of two samples per iteration instead of 4 T
-// samples) and neighbouring lanes read neighbouring texels.  Sums over the group by
-// butterfly shuffles inside the group; every lane of the warp runs every iteration (a
-// skipped or absent tile adds nothing and keeps its vector), so the shuffles stay
-// converged.  f is the same for the whole warp.
+// The same refinement with T / 2 lanes per tile (T <= 8, 64 / T tiles per warp): lane c of
+// a group owns columns 2 c and 2 c + 1 of the tile and walks its T rows, so neighbouring
+// columns share their texels (4 loads per row for the two gradients, 3 per row for the two
+// bilinear samples) and the per-tile work of the solve is repeated in fewer lanes.  The
+// gradient rows roll down the tile where no row is clamped (the tile ends inside the
+// level).  Sums over the group by butterfly shuffles inside the group; every lane of the
+// warp runs every iteration (a skipped or absent tile adds nothing and keeps its vector),
+// so the shuffles stay converged.  f is the same for the whole warp.
 template <int T>
 __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
                                          const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
                                          int32_t *__restrict__ motion_int, int tile, int lane, int f) {
-    static_assert(T == 4 || T == 8, "T lanes per tile");
-    const int c = lane & (T - 1);
+    static_assert(T == 4 || T == 8, "T / 2 lanes per tile");
+    constexpr int kL = T / 2;
+    const int c = 2 * (lane & (kL - 1));
     const bool active = tile < lty * ltx;
     const size_t o = (size_t)f * lty * ltx + tile;
     if (f == ref) {
@@ -449,25 +553,52 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
     const uint16_t *R = L0 + (size_t)ref * lh * lw;
     const uint16_t *A = L0 + (size_t)f * lh * lw;
     const int2 u = active ? HMFSR_LD(vec0 + o) : make_int2(0, 0);
-    const int x = min(tx * T + c, lw - 1), y0 = ty * T;
-    const int xm = max(x - 1, 0), xp = min(x + 1, lw - 1);
-    float gxs[T], gys[T], rv[T];
+    // the lane's two pixel columns (clamped into the level) and their gradient neighbours:
+    // x0 + 1 is x1's column or, where both clamp to the last column, x0 itself
+    const int x0 = min(tx * T + c, lw - 1), x1 = min(tx * T + c + 1, lw - 1);
+    const int xm = max(x0 - 1, 0), xp = min(x1 + 1, lw - 1);
+    const bool same = (x1 == x0);
+    const int y0 = ty * T;
+    float gxs[2 * T], gys[2 * T], rv[2 * T];
     long long hxx = 0, hxy = 0, hyy = 0;
+    {
+        const bool roll = (y0 + T <= lh);
+        int pm0 = 0, pm1 = 0, c0 = 0, c1 = 0;
+        if (roll) {
+            const uint16_t *rm = R + max(y0 - 1, 0) * lw, *rc = R + y0 * lw;
+            pm0 = HMFSR_LDG(rm + x0); pm1 = HMFSR_LDG(rm + x1);
+            c0 = HMFSR_LDG(rc + x0); c1 = HMFSR_LDG(rc + x1);
+        }
 #pragma unroll
-    for (int j = 0; j < T; ++j) {
-        const int y = min(y0 + j, lh - 1);
-        const uint16_t *row = R + y * lw;  // 32-bit offsets: a level holds < 2^31 texels
-        const int gx = (int)HMFSR_LDG(row + xp) - (int)HMFSR_LDG(row + xm);
-        const int gy = (int)HMFSR_LDG(R + min(y + 1, lh - 1) * lw + x) - (int)HMFSR_LDG(R + max(y - 1, 0) * lw + x);
-        gxs[j] = (float)gx * 0.125f;
-        gys[j] = (float)gy * 0.125f;
-        rv[j] = (float)HMFSR_LDG(row + x);
-        hxx += (long long)(gx * gx);
-        hxy += (long long)(gx * gy);
-        hyy += (long long)(gy * gy);
+        for (int j = 0; j < T; ++j) {
+            const int y = min(y0 + j, lh - 1);
+            const uint16_t *row = R + y * lw;  // 32-bit offsets: a level holds < 2^31 texels
+            if (!roll) {
+                const uint16_t *rm = R + max(y - 1, 0) * lw;
+                pm0 = HMFSR_LDG(rm + x0); pm1 = HMFSR_LDG(rm + x1);
+                c0 = HMFSR_LDG(row + x0); c1 = HMFSR_LDG(row + x1);
+            }
+            const uint16_t *rp = R + min(y + 1, lh - 1) * lw;
+            const int n0 = HMFSR_LDG(rp + x0), n1 = HMFSR_LDG(rp + x1);
+            const int lm = HMFSR_LDG(row + xm), lp = HMFSR_LDG(row + xp);
+            const int gx0 = c1 - lm, gx1 = lp - (same ? lm : c0);
+            const int gy0 = n0 - pm0, gy1 = n1 - pm1;
+            gxs[2 * j] = (float)gx0 * 0.125f;
+            gxs[2 * j + 1] = (float)gx1 * 0.125f;
+            gys[2 * j] = (float)gy0 * 0.125f;
+            gys[2 * j + 1] = (float)gy1 * 0.125f;
+            rv[2 * j] = (float)c0;
+            rv[2 * j + 1] = (float)c1;
+            // |g| < 2^15: two squares or products fit a 32-bit int
+            hxx += (long long)(gx0 * gx0 + gx1 * gx1);
+            hxy += (long long)(gx0 * gy0 + gx1 * gy1);
+            hyy += (long long)(gy0 * gy0 + gy1 * gy1);
+            pm0 = c0; pm1 = c1;
+            c0 = n0; c1 = n1;
+        }
     }
 #pragma unroll
-    for (int m = T / 2; m > 0; m >>= 1) {
+    for (int m = kL / 2; m > 0; m >>= 1) {
         hxx += __shfl_xor_sync(0xffffffffu, hxx, m);
         hxy += __shfl_xor_sync(0xffffffffu, hxy, m);
         hyy += __shfl_xor_sync(0xffffffffu, hyy, m);
@@ -484,23 +615,29 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
         const float fdx = floorf(dx), fdy = floorf(dy);
         const float ax = dx - fdx, ay = dy - fdy;
         const int ox = u.x + (int)fdx, oy = u.y + (int)fdy;
-        const int x0 = clampi(x + ox, 0, lw - 1), x1 = clampi(x + ox + 1, 0, lw - 1);
+        // sample columns: pixel 0 between s0 and s1, pixel 1 between s1 and s2 (or, where
+        // both pixels are the clamped last column, between s0 and s1 as well)
+        const int s0 = clampi(x0 + ox, 0, lw - 1), s1 = clampi(x0 + ox + 1, 0, lw - 1);
+        const int s2 = clampi(x1 + ox + 1, 0, lw - 1);
         float bx = 0.f, by = 0.f;
         if (y0 + T <= lh && y0 + oy >= 0 && y0 + oy + T < lh) {
             // the tile's rows and the sampled rows are inside the level: one row after another
             const uint16_t *a = A + (y0 + oy) * lw;
-            float i00 = (float)HMFSR_LDG(a + x0), i10 = (float)HMFSR_LDG(a + x1);
+            float t0 = (float)HMFSR_LDG(a + s0), t1 = (float)HMFSR_LDG(a + s1), t2 = (float)HMFSR_LDG(a + s2);
 #pragma unroll
             for (int j = 0; j < T; ++j) {
                 a += lw;
-                const float i01 = (float)HMFSR_LDG(a + x0), i11 = (float)HMFSR_LDG(a + x1);
-                const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
-                const float ia = fmaf(ay, bot, (1.f - ay) * top);
-                const float r = (ia - rv[j]) * 0.25f;
-                bx = fmaf(gxs[j], r, bx);
-                by = fmaf(gys[j], r, by);
-                i00 = i01;
-                i10 = i11;
+                const float b0 = (float)HMFSR_LDG(a + s0), b1 = (float)HMFSR_LDG(a + s1), b2 = (float)HMFSR_LDG(a + s2);
+                const float top0 = fmaf(ax, t1, (1.f - ax) * t0), bot0 = fmaf(ax, b1, (1.f - ax) * b0);
+                const float top1 = same ? top0 : fmaf(ax, t2, (1.f - ax) * t1);
+                const float bot1 = same ? bot0 : fmaf(ax, b2, (1.f - ax) * b1);
+                const float ia0 = fmaf(ay, bot0, (1.f - ay) * top0), ia1 = fmaf(ay, bot1, (1.f - ay) * top1);
+                const float r0 = (ia0 - rv[2 * j]) * 0.25f, r1 = (ia1 - rv[2 * j + 1]) * 0.25f;
+                bx = fmaf(gxs[2 * j], r0, bx);
+                by = fmaf(gys[2 * j], r0, by);
+                bx = fmaf(gxs[2 * j + 1], r1, bx);
+                by = fmaf(gys[2 * j + 1], r1, by);
+                t0 = b0; t1 = b1; t2 = b2;
             }
         } else {
 #pragma unroll
@@ -508,17 +645,21 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
                 const int iy = min(y0 + j, lh - 1) + oy;
                 const uint16_t *a0 = A + clampi(iy, 0, lh - 1) * lw;
                 const uint16_t *a1 = A + clampi(iy + 1, 0, lh - 1) * lw;
-                const float i00 = (float)HMFSR_LDG(a0 + x0), i10 = (float)HMFSR_LDG(a0 + x1);
-                const float i01 = (float)HMFSR_LDG(a1 + x0), i11 = (float)HMFSR_LDG(a1 + x1);
-                const float top = fmaf(ax, i10, (1.f - ax) * i00), bot = fmaf(ax, i11, (1.f - ax) * i01);
-                const float ia = fmaf(ay, bot, (1.f - ay) * top);
-                const float r = (ia - rv[j]) * 0.25f;
-                bx = fmaf(gxs[j], r, bx);
-                by = fmaf(gys[j], r, by);
+                const float t0 = (float)HMFSR_LDG(a0 + s0), t1 = (float)HMFSR_LDG(a0 + s1), t2 = (float)HMFSR_LDG(a0 + s2);
+                const float b0 = (float)HMFSR_LDG(a1 + s0), b1 = (float)HMFSR_LDG(a1 + s1), b2 = (float)HMFSR_LDG(a1 + s2);
+                const float top0 = fmaf(ax, t1, (1.f - ax) * t0), bot0 = fmaf(ax, b1, (1.f - ax) * b0);
+                const float top1 = same ? top0 : fmaf(ax, t2, (1.f - ax) * t1);
+                const float bot1 = same ? bot0 : fmaf(ax, b2, (1.f - ax) * b1);
+                const float ia0 = fmaf(ay, bot0, (1.f - ay) * top0), ia1 = fmaf(ay, bot1, (1.f - ay) * top1);
+                const float r0 = (ia0 - rv[2 * j]) * 0.25f, r1 = (ia1 - rv[2 * j + 1]) * 0.25f;
+                bx = fmaf(gxs[2 * j], r0, bx);
+                by = fmaf(gys[2 * j], r0, by);
+                bx = fmaf(gxs[2 * j + 1], r1, bx);
+                by = fmaf(gys[2 * j + 1], r1, by);
             }
         }
 #pragma unroll
-        for (int m = T / 2; m > 0; m >>= 1) {
+        for (int m = kL / 2; m > 0; m >>= 1) {
             bx += __shfl_xor_sync(0xffffffffu, bx, m);
             by += __shfl_xor_sync(0xffffffffu, by, m);
         }
