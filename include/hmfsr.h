@@ -53,7 +53,10 @@ typedef struct {
     int pitch_elems;   /* row stride in elements, even, >= width                   */
     int ref;           /* index of the base frame, 0 <= ref < n_frames             */
     int cfa;           /* 0 = RGGB (the only layout supported)                     */
-    int white_level;   /* e.g. 4095 for 12-bit data                                */
+    int white_level;   /* e.g. 4095 for 12-bit data; 1..7281.  Every sample must   */
+                       /* lie in [0, white_level]: the exact integer sums of the   */
+                       /* alignment are sized for it (larger samples give        */
+                       /* unspecified vectors)                                    */
     int black_level;   /* must be 0 (the synthetic data has none)                  */
 } hmfsr_burst_desc;
 

@@ -1008,14 +1008,13 @@ __device__ __forceinline__ void hf_flag_px(const uint16_t *__restrict__ burst, c
 
 // --------------------------------------------------------------------------------------
 // robustness (Eq. 5, 6) and its 5x5 minimum (Eq. 9) on one strip of base texels of one
-// frame: one warp, kRobOut columns, `rows` rows.  Lane l evaluates R at column
-// u0 - 2 + l for the rows v0 - 2 .. v0 + rows + 1, walking down: within a motion
-// tile the bilinear neighbours of the row below are the bottom neighbours of this row,
-// so each row reads two new sums instead of four.  The 5-wide row minimum comes from
-// the next four lanes (lanes 0 .. kRobOut - 1 write); a rolling window of five row
-// minima gives the column minimum.  Every lane of the warp calls this.
+// frame: one warp, kRobOut columns, `rows` rows.  Each lane evaluates R at two texel
+// columns for the rows v0 - 2 .. v0 + rows + 1, walking down: within a motion tile the
+// bilinear neighbours of the row below are the bottom neighbours of this row, so each row
+// reads new sums for the bottom neighbours only.  A rolling window of five row minima
+// gives the column minimum.  Every lane of the warp calls this.
 // --------------------------------------------------------------------------------------
-constexpr int kRobOut = 28, kRobStrip = 64;  // kRobStrip: default strip height, as for kPrepStrip
+constexpr int kRobStrip = 64;  // default strip height, as for kPrepStrip
 constexpr float kLog2e = 1.44269504088896340736f;
 
 // Wiener-shrunk squared difference of one channel (Eq. 6): (d d^2 / (d^2 + dmd^2))^2 added
@@ -1026,45 +1025,80 @@ __device__ __forceinline__ float wiener_add(float d, float dmd2, float dd) {
     return fmaf(w, w, dd);
 }
 
+// --------------------------------------------------------------------------------------
+// Lane l of a warp owns texel columns u0 - 2 + 2 l and u0 - 1 + 2 l (u0 even, so both lie
+// in one motion tile); the warp writes the kRobOut columns u0 .. u0 + kRobOut - 1 (lanes
+// 1 .. 30).  The pair shares the middle column of its bilinear neighbours (three per row),
+// the loop and tile bookkeeping, and a 5-wide row minimum built from the two neighbouring
+// lanes' pairs.  The guide sums become floats exactly (a 16- or 17-bit value in the
+// mantissa of 2^23, minus 2^23), so every difference base - neighbour is exact, as an
+// integer difference would be.
+// --------------------------------------------------------------------------------------
+constexpr int kRobOut = 60;
+
+// exact float of 0 <= v < 2^23
+__device__ __forceinline__ float small_uint_to_float(uint32_t v) { return __uint_as_float(0x4B000000u | v) - 8388608.f; }
+
+struct GuideSums {
+    float r, b, g;
+};
+__device__ __forceinline__ GuideSums guide_sums(uint2 s) {
+    return {small_uint_to_float(s.x & 0xffffu), small_uint_to_float(s.x >> 16), small_uint_to_float(s.y)};
+}
+
+// R of one texel (Eq. 5, 6) from its base sums and the four bilinear neighbours' sums
+// (top-left, top-right, bottom-left, bottom-right) with weights b00 .. b11
+__device__ __forceinline__ float rob_texel(const GuideSums &s, const GuideSums &n00, const GuideSums &n10,
+                                           const GuideSums &n01, const GuideSums &n11, float b00, float b10, float b01,
+                                           float b11, const float4 &st, float sc, float t_thr) {
+    float dR = fmaf(b00, s.r - n00.r, fmaf(b10, s.r - n10.r, fmaf(b01, s.r - n01.r, b11 * (s.r - n11.r))));
+    float dB = fmaf(b00, s.b - n00.b, fmaf(b10, s.b - n10.b, fmaf(b01, s.b - n01.b, b11 * (s.b - n11.b))));
+    float dG = fmaf(b00, s.g - n00.g, fmaf(b10, s.g - n10.g, fmaf(b01, s.g - n01.g, b11 * (s.g - n11.g))));
+    dR *= (1.f / 9.f);
+    dB *= (1.f / 9.f);
+    dG *= (1.f / 18.f);
+    const float dd = wiener_add(dB, st.w, wiener_add(dG, st.z, wiener_add(dR, st.y, 0.f)));
+    const float ex = fast_exp2(-(dd * fast_rcp(st.x)) * kLog2e);
+    return fminf(fmaxf(fmaf(sc, ex, -t_thr), 0.f), 1.f);
+}
+
 // kHF: hf_flag holds the base texels' high-frequency flags, which reject (R = 0) where
 // the tile's motion span exceeds m_th (otherwise both are unused)
 template <bool kHF = false>
 __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const float4 *__restrict__ base_stats,
-                                          const float2 *__restrict__ motion, const float *__restrict__ s_tile,
-                                          const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
-                                          int frame, int lane, const unsigned char *__restrict__ hf_flag = nullptr,
-                                          float m_th = 0.f, int rows = kRobStrip) {
+                                           const float2 *__restrict__ motion, const float *__restrict__ s_tile,
+                                           const Geom &g, float t_thr, float *__restrict__ rhat, int u0, int v0,
+                                           int frame, int lane, const unsigned char *__restrict__ hf_flag = nullptr,
+                                           float m_th = 0.f, int rows = kRobStrip) {
     const size_t hw = (size_t)g.hh * g.wh;
-    const int wh = g.wh, u = u0 - 2 + lane;
-    const bool col_ok = u >= 0 && u < wh;
-    const int uc = clampi(u, 0, wh - 1);
-    const int ht = g.tile / 2;  // motion tile in texels
+    const int wh = g.wh, ua = u0 - 2 + 2 * lane;
+    const bool ok_a = ua >= 0 && ua < wh, ok_b = ua + 1 >= 0 && ua + 1 < wh;
+    const int uc = clampi(ua, 0, wh - 1);
+    const int ht = g.tile / 2;  // motion tile in texels (even)
     const int txi = min(uc / ht, g.tx - 1);
     const uint2 *S1b = s1 + (size_t)g.ref * hw;
     const uint2 *S1n = s1 + (size_t)frame * hw;
     const float2 *mvf = motion + (size_t)frame * g.ty * g.tx + txi;
     const float *stf = s_tile + (size_t)frame * g.ty * g.tx + txi;
     float *out = rhat + (size_t)frame * hw;
-    // tile row of the first row and the position within it, advanced row by row
     const int vfirst = max(v0 - 2, 0);
     int tq = vfirst / ht, tr = vfirst - tq * ht;
-    int cur_tile = -1, fly = 0, x0 = 0, x1 = 0;
-    bool span = false;  // the tile's motion span exceeds m_th (high-frequency rejection only)
+    int cur_tile = -1, fly = 0, x0 = 0, x1 = 0, x2 = 0;
+    bool span = false;
     float b00 = 0.f, b10 = 0.f, b01 = 0.f, b11 = 0.f, sc = 0.f;
-    uint2 nt0 = make_uint2(0u, 0u), nt1 = nt0, nb0 = nt0, nb1 = nt0;  // sums at the top / bottom neighbours
+    GuideSums t0{}, t1{}, t2{}, n0{}, n1{}, n2{};  // sums at the top / bottom neighbours x0, x1, x2
     bool have_prev = false;
-    float h0 = kBig, h1 = kBig, h2 = kBig, h3 = kBig;  // row minima of the four rows above
-    int off = (v0 - 2) * wh + uc;                        // this lane's texel in the row (32-bit offsets)
+    float ha[4] = {kBig, kBig, kBig, kBig}, hb[4] = {kBig, kBig, kBig, kBig};  // row minima of the rows above
+    int off = (v0 - 2) * wh + uc;  // texel a's offset in the row (32-bit offsets)
     for (int e = 0; e < rows + 4; ++e, off += wh) {
         const int v = v0 - 2 + e;
-        float R = kBig;
+        float ra = kBig, rb = kBig;
         if (v >= 0 && v < g.hh) {  // the same for the whole warp
             const int tyi = min(tq, g.ty - 1);
             if (tyi != cur_tile) {
                 cur_tile = tyi;
                 const float2 mv = HMFSR_LD(mvf + tyi * g.tx);
                 sc = HMFSR_LD(stf + tyi * g.tx);
-                // aligned position (u, v) + v/2 split into an exact integer part and fraction
                 const float hx = 0.5f * mv.x, hy = 0.5f * mv.y;
                 const float flx = floorf(hx), flyf = floorf(hy);
                 const float fx = hx - flx, fy = hy - flyf;
@@ -1072,59 +1106,54 @@ __device__ __forceinline__ void rob_strip(const uint2 *__restrict__ s1, const fl
                 fly = (int)flyf;
                 x0 = clampi(uc + (int)flx, 0, wh - 1);
                 x1 = clampi(uc + (int)flx + 1, 0, wh - 1);
+                x2 = clampi(uc + (int)flx + 2, 0, wh - 1);
                 have_prev = false;
                 if (kHF) span = motion_span_exceeds(motion + (size_t)frame * g.ty * g.tx, g.ty, g.tx, tyi, txi, m_th);
             }
             if (++tr == ht) { tr = 0; ++tq; }
             const int iy = v + fly;
             if (have_prev) {
-                nt0 = nb0;
-                nt1 = nb1;
+                t0 = n0; t1 = n1; t2 = n2;
             } else {
                 const int o0 = clampi(iy, 0, g.hh - 1) * wh;
-                nt0 = HMFSR_LD(S1n + o0 + x0);
-                nt1 = HMFSR_LD(S1n + o0 + x1);
+                t0 = guide_sums(HMFSR_LD(S1n + o0 + x0));
+                t1 = guide_sums(HMFSR_LD(S1n + o0 + x1));
+                t2 = guide_sums(HMFSR_LD(S1n + o0 + x2));
             }
             const int o1 = clampi(iy + 1, 0, g.hh - 1) * wh;
-            nb0 = HMFSR_LD(S1n + o1 + x0);
-            nb1 = HMFSR_LD(S1n + o1 + x1);
+            n0 = guide_sums(HMFSR_LD(S1n + o1 + x0));
+            n1 = guide_sums(HMFSR_LD(S1n + o1 + x1));
+            n2 = guide_sums(HMFSR_LD(S1n + o1 + x2));
             have_prev = true;
-            if (kHF && col_ok && span && HMFSR_LD(hf_flag + off)) {
-                R = 0.f;  // high-frequency content with a large local motion span: rejected
-            } else if (col_ok) {
-                const uint2 sb = HMFSR_LD(S1b + off);
-                const float4 st = HMFSR_LD(base_stats + off);
-                // d_ms = mu_base - mu_aligned = sum_k beta_k (S1_base - S1_k) / 9, from exact
-                // integer differences
-                const int ri = (int)(sb.x & 0xffffu), bi = (int)(sb.x >> 16), gi = (int)sb.y;
-                float dR = fmaf(b00, (float)(ri - (int)(nt0.x & 0xffffu)), fmaf(b10, (float)(ri - (int)(nt1.x & 0xffffu)),
-                           fmaf(b01, (float)(ri - (int)(nb0.x & 0xffffu)), b11 * (float)(ri - (int)(nb1.x & 0xffffu)))));
-                float dB = fmaf(b00, (float)(bi - (int)(nt0.x >> 16)), fmaf(b10, (float)(bi - (int)(nt1.x >> 16)),
-                           fmaf(b01, (float)(bi - (int)(nb0.x >> 16)), b11 * (float)(bi - (int)(nb1.x >> 16)))));
-                float dG = fmaf(b00, (float)(gi - (int)nt0.y), fmaf(b10, (float)(gi - (int)nt1.y),
-                           fmaf(b01, (float)(gi - (int)nb0.y), b11 * (float)(gi - (int)nb1.y))));
-                dR *= (1.f / 9.f);
-                dB *= (1.f / 9.f);
-                dG *= (1.f / 18.f);
-                const float dd = wiener_add(dB, st.w, wiener_add(dG, st.z, wiener_add(dR, st.y, 0.f)));
-                // Eq. 5: s exp(-dd / sigma^2) - t, clamped to [0, 1]
-                const float ex = fast_exp2(-(dd * fast_rcp(st.x)) * kLog2e);
-                R = fminf(fmaxf(fmaf(sc, ex, -t_thr), 0.f), 1.f);
+            if (ok_a) {
+                if (kHF && span && HMFSR_LD(hf_flag + off)) ra = 0.f;
+                else ra = rob_texel(guide_sums(HMFSR_LD(S1b + off)), t0, t1, n0, n1, b00, b10, b01, b11,
+                                    HMFSR_LD(base_stats + off), sc, t_thr);
+            }
+            if (ok_b) {
+                if (kHF && span && HMFSR_LD(hf_flag + off + 1)) rb = 0.f;
+                else rb = rob_texel(guide_sums(HMFSR_LD(S1b + off + 1)), t1, t2, n1, n2, b00, b10, b01, b11,
+                                    HMFSR_LD(base_stats + off + 1), sc, t_thr);
             }
         } else {
             have_prev = false;
         }
-        // 5-wide row minimum from lanes l .. l + 4
-        float m = fminf(R, __shfl_down_sync(0xffffffffu, R, 1));
-        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 2));
-        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 3));
-        m = fminf(m, __shfl_down_sync(0xffffffffu, R, 4));
-        if (e >= 4) {
-            const int vo = v - 2, uo = u0 + lane;
-            if (lane < kRobOut && uo < wh && vo < g.hh)
-                HMFSR_ST(out + vo * wh + uo, fminf(fminf(fminf(h0, h1), fminf(h2, h3)), m));
+        // 5-wide row minima: the previous lane's pair, this pair, the next lane's pair
+        const float pa = __shfl_up_sync(0xffffffffu, ra, 1), pb = __shfl_up_sync(0xffffffffu, rb, 1);
+        const float na = __shfl_down_sync(0xffffffffu, ra, 1), nb = __shfl_down_sync(0xffffffffu, rb, 1);
+        const float mid = fminf(ra, rb);
+        const float ma = fminf(fminf(pa, pb), fminf(mid, na));
+        const float mb = fminf(fminf(pb, mid), fminf(na, nb));
+        if (e >= 4 && lane >= 1 && lane <= 30) {
+            const int vo = v - 2;
+            if (vo < g.hh) {
+                if (ua < wh) HMFSR_ST(out + vo * wh + ua, fminf(fminf(fminf(ha[0], ha[1]), fminf(ha[2], ha[3])), ma));
+                if (ua + 1 < wh)
+                    HMFSR_ST(out + vo * wh + ua + 1, fminf(fminf(fminf(hb[0], hb[1]), fminf(hb[2], hb[3])), mb));
+            }
         }
-        h0 = h1; h1 = h2; h2 = h3; h3 = m;
+        ha[0] = ha[1]; ha[1] = ha[2]; ha[2] = ha[3]; ha[3] = ma;
+        hb[0] = hb[1]; hb[1] = hb[2]; hb[2] = hb[3]; hb[3] = mb;
     }
 }
 
