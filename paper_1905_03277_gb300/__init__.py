@@ -473,8 +473,9 @@ def pyramid_levels(h: int, w: int, n_levels_max: int = 4) -> int:
 def launches_per_call(n_frames: int, h: int, w: int, n_levels_max: int = 4) -> dict:
     """Kernel launches made by one hmfsr_align / hmfsr_merge_prepare / accumulate call."""
     nl = pyramid_levels(h, w, n_levels_max)
-    # align: levels 0 and 1 in one launch, one per coarser level, one search per level, LK
-    return {"align": 1 + max(nl - 2, 0) + nl + 1, "merge_prepare": 3 if n_frames > 1 else 2, "merge_accumulate": 2}
+    # align: levels 0 and 1 in one launch, levels 2 and 3 in one, one search per level, LK
+    return {"align": 1 + (1 if nl > 2 else 0) + nl + 1, "merge_prepare": 3 if n_frames > 1 else 2,
+            "merge_accumulate": 2}
 
 
 def merge_static(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1),

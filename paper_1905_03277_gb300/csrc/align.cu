@@ -11,9 +11,113 @@ __global__ void k_luma01(const uint16_t *__restrict__ burst, int h, int pitch, i
                   blockIdx.z);
 }
 
-__global__ void k_down(const uint16_t *__restrict__ src, int sh, int sw, uint16_t *__restrict__ dst, int dh, int dw,
-                       int fct) {
-    stage::down(src, sh, sw, dst, dh, dw, fct, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, blockIdx.z);
+// Levels 2 and 3 in one pass: a 16 x 16 block makes a 16 x 16 patch of level 2 (integer
+// floor means of 4 x 4 level-1 texels, as down does) in shared memory and, when `l3` is
+// set, the 4 x 4 level-3 texels over it (floor means of 4 x 4 level-2 texels).
+__global__ void __launch_bounds__(256) k_down23(const uint16_t *__restrict__ l1, int h1, int w1,
+                                                uint16_t *__restrict__ l2, int h2, int w2, uint16_t *__restrict__ l3,
+                                                int h3, int w3) {
+    __shared__ uint32_t patch[16][16];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4, f = blockIdx.z;
+    const int x = blockIdx.x * 16 + tx, y = blockIdx.y * 16 + ty;
+    uint32_t v = 0;
+    if (x < w2 && y < h2) {
+        const uint16_t *p = l1 + (size_t)f * h1 * w1 + (size_t)(4 * y) * w1 + 4 * x;
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s += HMFSR_LD(p + (size_t)j * w1 + i);
+        v = s / 16u;
+        HMFSR_ST(l2 + ((size_t)f * h2 + y) * w2 + x, (uint16_t)v);
+    }
+    if (l3 == nullptr) return;
+    patch[ty][tx] = v;
+    __syncthreads();
+    if (tx < 4 && ty < 4) {
+        const int X = blockIdx.x * 4 + tx, Y = blockIdx.y * 4 + ty;
+        if (X < w3 && Y < h3) {  // its 4 x 4 level-2 texels lie inside level 2 (w3 = w2 / 4, h3 = h2 / 4)
+            uint32_t s = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) s += patch[4 * ty + j][4 * tx + i];
+            HMFSR_ST(l3 + ((size_t)f * h3 + Y) * w3 + X, (uint16_t)(s / 16u));
+        }
+    }
+}
+
+// Block matching of one tile per block for the coarse levels, where there are few tiles:
+// the tile's candidate window and reference are staged in shared memory and thread c of
+// the (2 RAD + 1)^2 offsets sums its own candidate, so a tile takes the latency of one
+// candidate's sum; the block's minimum key decides (same sums and keys as ssd()).
+template <int T, int RAD>
+struct TileSsd {
+    static constexpr int kW = 2 * RAD + 1, kA = T + 2 * RAD;
+    static constexpr int kThreads = ((kW * kW + 31) / 32) * 32;
+};
+
+template <int T, int RAD, int PART>
+__global__ void __launch_bounds__(TileSsd<T, RAD>::kThreads) k_ssd_tile(const uint16_t *__restrict__ img, int lh,
+                                                                        int lw, int lty, int ltx,
+                                                                        const int2 *__restrict__ parent, int pty,
+                                                                        int ptx, int fsh, int ref,
+                                                                        int2 *__restrict__ vec) {
+    using S = TileSsd<T, RAD>;
+    constexpr int kW = S::kW, kA = S::kA, kNT = S::kThreads, kWarps = kNT / 32;
+    __shared__ int win[kA][kA];
+    __shared__ int rf[T][T];
+    __shared__ unsigned long long wmin[kWarps];
+    const int tile = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
+    int2 *out = vec + (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        if (tid == 0) HMFSR_ST(out, make_int2(0, 0));
+        return;
+    }
+    const int ty = tile / ltx, tx = tile - ty * ltx;
+    const int2 cc = stage::ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f);
+    const uint16_t *R = img + (size_t)ref * lh * lw;
+    const uint16_t *A = img + (size_t)f * lh * lw;
+    const int x0 = tx * T, y0 = ty * T, xa = x0 + cc.x - RAD, ya = y0 + cc.y - RAD;
+    for (int k = tid; k < kA * kA; k += kNT) {
+        const int r = k / kA, c = k - r * kA;
+        win[r][c] = HMFSR_LDG(A + (size_t)clampi(ya + r, 0, lh - 1) * lw + clampi(xa + c, 0, lw - 1));
+    }
+    for (int k = tid; k < T * T; k += kNT) {
+        const int j = k / T, i = k - j * T;
+        rf[j][i] = HMFSR_LDG(R + (size_t)min(y0 + j, lh - 1) * lw + clampi(x0 + i, 0, lw - 1));
+    }
+    __syncthreads();
+    unsigned long long key = ~0ull;
+    if (tid < kW * kW) {
+        const int dyi = tid / kW, dxi = tid - dyi * kW;
+        stage::SsdAcc<T, PART> acc;
+#pragma unroll 2
+        for (int j = 0; j < T; ++j) {
+            int rv[T], av[T];
+#pragma unroll
+            for (int i = 0; i < T; ++i) {
+                rv[i] = rf[j][i];
+                av[i] = win[j + dyi][i + dxi];
+            }
+            acc.add(rv, av, j);
+        }
+        key = stage::ssd_key(acc.total, dxi - RAD, dyi - RAD);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        key = k2 < key ? k2 : key;
+    }
+    if ((tid & 31) == 0) wmin[tid >> 5] = key;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long m = wmin[0];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) m = wmin[w] < m ? wmin[w] : m;
+        const int bdx = (int)(m & 15ull) - 7, bdy = (int)((m >> 4) & 15ull) - 7;
+        HMFSR_ST(out, make_int2(cc.x + bdx, cc.y + bdy));
+    }
 }
 
 template <int T, int RAD, int PART>
@@ -179,18 +283,22 @@ __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, i
 
 }  // namespace
 
-static const int kFactors[3] = {2, 4, 4};
-
 // Block matching of one level: rows outermost for small radii and tiles, else the offsets
 // dy spread over the lanes of a group (measured at 12 MP on level 1, 96k tile-frames: the
 // grouped form 9 us faster than one thread per tile, both at 64 registers).
+
+// at most this many tile-frames: a level is searched one tile per block (k_ssd_tile)
+constexpr long long kTileSearchMax = 16384;
 
 template <int T, int RAD, int PART>
 static void launch_ssd_part(const AlignLevels &L, int l, int n, int ref, int fsh, bool top, cudaStream_t s) {
     const int tiles = L.lty[l] * L.ltx[l];
     const int2 *parent = top ? nullptr : L.vec[l + 1];
     const int pty = top ? 0 : L.lty[l + 1], ptx = top ? 0 : L.ltx[l + 1];
-    if constexpr (RAD <= 2 && T <= 8) {
+    if (RAD >= 2 && (long long)tiles * n <= kTileSearchMax) {
+        k_ssd_tile<T, RAD, PART><<<dim3(tiles, n), TileSsd<T, RAD>::kThreads, 0, s>>>(
+            L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
+    } else if constexpr (RAD <= 2 && T <= 8) {
         k_ssd_rows<T, RAD, PART><<<dim3(div_up(tiles, 64), n), 64, 0, s>>>(
             L.img[l], L.lh[l], L.lw[l], L.lty[l], L.ltx[l], parent, pty, ptx, fsh, ref, L.vec[l]);
     } else if constexpr (T <= 16 && StagedSsd<T, RAD>::kBytes <= 40 * 1024) {
@@ -274,9 +382,13 @@ cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align
     const bool two = L.n_levels > 1;
     k_luma01<<<dim3(div_up(g.wh, 4 * 128), div_up(g.hh, 2), n), 128, 0, s>>>(
         burst, g.h, g.pitch, g.hh, g.wh, L.img[0], two ? L.img[1] : nullptr, two ? L.lh[1] : 0, two ? L.lw[1] : 0);
-    for (int l = 2; l < L.n_levels; ++l)
-        k_down<<<dim3(div_up(L.lw[l], 128), L.lh[l], n), 128, 0, s>>>(L.img[l - 1], L.lh[l - 1], L.lw[l - 1],
-                                                                       L.img[l], L.lh[l], L.lw[l], kFactors[l - 1]);
+    if (L.n_levels > 2) {
+        // levels 2 and 3 (factors 4 and 4) in one pass
+        const bool l3 = L.n_levels > 3;
+        k_down23<<<dim3(div_up(L.lw[2], 16), div_up(L.lh[2], 16), n), 256, 0, s>>>(
+            L.img[1], L.lh[1], L.lw[1], L.img[2], L.lh[2], L.lw[2], l3 ? L.img[3] : nullptr, l3 ? L.lh[3] : 0,
+            l3 ? L.lw[3] : 0);
+    }
     switch (p.tile) {
         case 8: run_search<4>(g, p, L, motion, motion_int, s); break;
         case 16: run_search<8>(g, p, L, motion, motion_int, s); break;
