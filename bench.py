@@ -407,6 +407,25 @@ def run_gpu(args):
     tuning["noise_table"] = (f"{ntab.shape[0]} levels x 4096 trials x 54 Philox-4x32-10 Irwin-Hall normals "
                              "(FP64 samples, rounding and clipping)")
 
+    # bounded memory: the same merge a chunk of frames at a time (the running sums of every
+    # output pixel kept in the workspace between chunks), against the resident merge
+    bounded = {"chunk_frames": 2}
+    crgb = hm.merge_chunked(raw, tmotion, p, scale, 0, chunk_frames=2)
+    bounded["identical_to_resident"] = bool(torch.equal(crgb, hm.merge(raw, tmotion, p, scale)))
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(5):
+        hm.merge_chunked(raw, tmotion, p, scale, 0, chunk_frames=2)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    bounded["chunked_merge_ms"] = t0.elapsed_time(t1) / 5
+    bounded["resident_merge_ms"] = tuning["merge_ms"]
+    for frames in (n, 4 * n):
+        bounded[f"workspace_mb_{frames}_frames"] = {
+            "resident": hm.workspace_size(hm._lib.OP_MERGE, (frames, h, w), p.tile, scale) / 1e6,
+            "chunked": hm.chunked_workspace_size((frames, h, w), p.tile, scale, 2) / 1e6}
+    del crgb
+
     # adjoint (fitting workload: 8 x 1024x1024 at 1.5x): forward with den, then backward
     fb = burstgen.make_burst("fit", seed=burstgen.SEED_BASE + 3 + 1000 * rank, device=dev)
     fraw = fb["raw"]
@@ -533,6 +552,7 @@ def run_gpu(args):
                 "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
                 "batched": batched,
                 "snr_tuning": tuning,
+                "bounded_memory": bounded,
                 "adjoint": {"workload": "fit: 8 x 1024x1024 RGGB, 1.5x output", "forward_ms": statistics.median(fwd_ms),
                             "backward_ms": statistics.median(bwd_ms),
                             "backward_over_forward": statistics.median(bwd_ms) / statistics.median(fwd_ms)}}

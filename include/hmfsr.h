@@ -152,6 +152,25 @@ hmfsr_status hmfsr_merge_accumulate(const uint16_t *burst_dev, const hmfsr_burst
                                     const hmfsr_merge_params *params, int scale_num, int scale_den, float *rgb_dev,
                                     float *den_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* Bounded-memory merge (Sec. 6 and Table 2: memory that does not grow with the frame
+ * count): the same outputs, bit for bit, as hmfsr_merge with these arguments, computed
+ * chunk_frames non-base frames at a time.  Each chunk's frames and the base frame are
+ * copied into a packed sub-burst in the workspace, their planes (kernel covariances,
+ * robustness) are prepared there, and the accumulation continues from the running sums
+ * of the earlier chunks: per output pixel and channel the numerator, the denominator
+ * and the exponent shift, 9 floats, kept in the workspace between chunks.  The frames
+ * are merged in hmfsr_merge's order (the base frame, then the others in order), so the
+ * sums are the same.  The closed-form noise model only (no hmfsr_merge_options).
+ *   chunk_frames  1..4096: non-base frames per chunk.
+ *   Workspace: hmfsr_merge_chunked_workspace_size(desc, tile, num, den, chunk_frames)
+ *   bytes, 256-byte aligned; for n_frames > chunk_frames it does not depend on n_frames.
+ *   Other arguments and errors as hmfsr_merge. */
+size_t hmfsr_merge_chunked_workspace_size(const hmfsr_burst_desc *desc, int tile, int scale_num, int scale_den,
+                                          int chunk_frames);
+hmfsr_status hmfsr_merge_chunked(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                 const hmfsr_merge_params *params, int scale_num, int scale_den, int chunk_frames,
+                                 float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes, void *stream);
+
 /* The per-frame merge stages alone, for inspection and testing (Sec. 5.1.2 and 5.2):
  *   omega_dev  optional float32 [n_frames][3][height/2][width/2]: the kernel covariance
  *              entries (Oxx, Oxy, Oyy) in raw px^2 at each half-res pixel (Eq. 4).

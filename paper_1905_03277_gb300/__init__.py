@@ -174,6 +174,37 @@ def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None 
     return (rgb, den) if with_den else rgb
 
 
+def merge_chunked(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1),
+                  ref: int = 0, chunk_frames: int = 2, with_den: bool = False, white_level: int = 4095, stream=None):
+    """hmfsr_merge_chunked: the same RGB as `merge`, bit for bit, from a workspace that does
+    not grow with the frame count (chunk_frames non-base frames at a time; the running
+    sums stay in the workspace between chunks)."""
+    L = _lib.load()
+    params = params or MergeParams()
+    d = _merge_inputs(burst, motion, params, ref, white_level)
+    n, h, w = burst.shape
+    ho, wo = out_size(h, w, scale)
+    rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
+    den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
+    nbytes = L.hmfsr_merge_chunked_workspace_size(ctypes.byref(d), params.tile, scale[0], scale[1], int(chunk_frames))
+    if nbytes == 0:
+        raise ValueError("unsupported burst shape, tile, scale or chunk size")
+    ws = _workspace(burst.device, nbytes, stream)
+    pc = params.c()
+    _lib.check(L.hmfsr_merge_chunked(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
+                                     int(chunk_frames), _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(),
+                                     _stream(burst.device, stream)), "hmfsr_merge_chunked")
+    return (rgb, den) if with_den else rgb
+
+
+def chunked_workspace_size(burst_shape, tile: int = 16, scale=(1, 1), chunk_frames: int = 2,
+                           white_level: int = 4095) -> int:
+    n, h, w = burst_shape
+    d = _lib.BurstDesc(n, h, w, w, 0, 0, white_level, 0)
+    return int(_lib.load().hmfsr_merge_chunked_workspace_size(ctypes.byref(d), tile, scale[0], scale[1],
+                                                              int(chunk_frames)))
+
+
 def merge_stages(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, ref: int = 0,
                  white_level: int = 4095, stream=None):
     """Per-frame merge stages: Omega entries float32 [n, 3, H/2, W/2] (Eq. 4) and the

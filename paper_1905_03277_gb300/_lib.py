@@ -113,7 +113,7 @@ class MergeParamsC(ctypes.Structure):
 OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD, OP_ALIGN_MERGE = 0, 1, 2, 3, 4
 PIPE_FP32_FMA, PIPE_MUFU_EX2 = 0, 1
 NOISE_LEVELS = 129
-EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_align_merge", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
+EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_align_merge", "hmfsr_merge_chunked", "hmfsr_merge_chunked_workspace_size", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
            "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
            "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_vectors",
            "hmfsr_batch_set_profile", "hmfsr_batch_stage_profile", "hmfsr_batch_configure",
@@ -150,6 +150,10 @@ def open_library(path: str):
     L.hmfsr_align_merge.argtypes = [vp, P(BurstDesc), P(AlignParamsC), P(MergeParamsC), ci, ci, vp, vp, vp, vp, vp, sz,
                                     vp]
     L.hmfsr_align_merge.restype = ci
+    L.hmfsr_merge_chunked_workspace_size.argtypes = [P(BurstDesc), ci, ci, ci, ci]
+    L.hmfsr_merge_chunked_workspace_size.restype = sz
+    L.hmfsr_merge_chunked.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, ci, vp, vp, vp, sz, vp]
+    L.hmfsr_merge_chunked.restype = ci
     L.hmfsr_merge_prepare.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), vp, sz, vp]
     L.hmfsr_merge_prepare.restype = ci
     L.hmfsr_merge_accumulate.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp, sz, vp]

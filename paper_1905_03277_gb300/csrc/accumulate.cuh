@@ -237,13 +237,48 @@ __device__ __forceinline__ void omega_form(const float4 &t0, const float4 &t1, c
     Bxy2 = 2.f * Nxy * sc;
 }
 
+// The accumulation in chunks of frames (bounded memory): the running sums of every output
+// pixel travel between launches in a state buffer of 9 planes of Ho x Wo floats
+// {numR, numG, numB, denR, denG, denB, mR, mG, mB}.  state_in: the sums so far (nullptr
+// for the first chunk, which starts empty); state_out: where to leave them (nullptr for
+// the last chunk, which normalises into the RGB output instead); skip_base: this chunk's
+// burst holds the base frame only for the robustness statistics, and its contribution was
+// made by an earlier chunk.  A pixel's state is read and written by the thread that owns
+// it, so state_in may equal state_out.
+struct ChunkIO {
+    const float *state_in = nullptr;
+    float *state_out = nullptr;
+    int skip_base = 0;
+    size_t plane = 0;  // Ho x Wo
+};
+
+__device__ __forceinline__ void load_state(const ChunkIO &io, size_t o, PixelAcc &a) {
+    const float *p = io.state_in + o;
+    const size_t q = io.plane;
+    a.numR = HMFSR_LD(p); a.numG = HMFSR_LD(p + q); a.numB = HMFSR_LD(p + 2 * q);
+    a.denR = HMFSR_LD(p + 3 * q); a.denG = HMFSR_LD(p + 4 * q); a.denB = HMFSR_LD(p + 5 * q);
+    a.mR = HMFSR_LD(p + 6 * q); a.mG = HMFSR_LD(p + 7 * q); a.mB = HMFSR_LD(p + 8 * q);
+}
+
+__device__ __forceinline__ void store_state(const ChunkIO &io, size_t o, const PixelAcc &a) {
+    float *p = io.state_out + o;
+    const size_t q = io.plane;
+    HMFSR_ST(p, a.numR); HMFSR_ST(p + q, a.numG); HMFSR_ST(p + 2 * q, a.numB);
+    HMFSR_ST(p + 3 * q, a.denR); HMFSR_ST(p + 4 * q, a.denG); HMFSR_ST(p + 5 * q, a.denB);
+    HMFSR_ST(p + 6 * q, a.mR); HMFSR_ST(p + 7 * q, a.mG); HMFSR_ST(p + 8 * q, a.mB);
+}
+
+// frame of step `it` of the accumulation order: the base frame, then the others in order
+__device__ __forceinline__ int frame_of_step(int it, int ref) { return it == 0 ? ref : (it <= ref ? it - 1 : it); }
+
 // SN/SD > 0: compile-time output scale SN/SD (constant divisors); 0: runtime snum/sden.
 // geo: the window geometry of every (frame, motion tile) for this scale (geo_entry).
-template <bool kDen, int SN, int SD>
+template <bool kDen, int SN, int SD, bool kChunk = false>
 __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, const int4 *__restrict__ geo,
                                          const Geom &g, const float4 *__restrict__ kern,
                                          const float *__restrict__ rhat_planes, int snum_rt, int sden_rt, int ho, int wo,
-                                         float *__restrict__ rgb, float *__restrict__ den_out, int X, int Y) {
+                                         float *__restrict__ rgb, float *__restrict__ den_out, int X, int Y,
+                                         const ChunkIO &io = ChunkIO{}) {
     if (X < 0 || Y < 0 || X >= wo || Y >= ho) return;
     constexpr int QC = 2 * SN, Q2C = 4 * SN;
     const int snum = SN > 0 ? SN : snum_rt, sden = SD > 0 ? SD : sden_rt;
@@ -271,13 +306,27 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
 
     PixelAcc acc;
     const size_t fstride = (size_t)g.h * g.pitch;
+    int it0 = 0;
+    if constexpr (kChunk) {
+        if (io.state_in) load_state(io, (size_t)Y * wo + X, acc);
+        it0 = io.skip_base ? 1 : 0;
+    }
 
     // frames in the order base frame, then the others; the next frame's geometry and
     // robustness are fetched while this one is merged
     int f_nx = g.ref;
-    int4 geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
+    int4 geo_nx = make_int4(0, 0, 0, 0);
     float rh_nx = 1.f;
-    for (int it = 0; it < g.n; ++it) {
+    if constexpr (kChunk) {
+        if (it0 < g.n) {
+            f_nx = frame_of_step(it0, g.ref);
+            geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
+            rh_nx = rhat_at(f_nx);
+        }
+    } else {
+        geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
+    }
+    for (int it = it0; it < g.n; ++it) {
         const int f = f_nx;
         const int4 gq = geo_nx;
         const float rh = rh_nx;
@@ -326,6 +375,12 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         accumulate_frame(q, rv, rh, ((kx ^ ky) & 1) != 0, (ky & 1) != 0, acc);
     }
     const size_t po = (size_t)ho * wo, o = (size_t)Y * wo + X;
+    if constexpr (kChunk) {
+        if (io.state_out) {
+            store_state(io, o, acc);
+            return;
+        }
+    }
     HMFSR_ST(rgb + o, acc.numR / acc.denR);
     HMFSR_ST(rgb + po + o, acc.numG / acc.denG);
     HMFSR_ST(rgb + 2 * po + o, acc.numB / acc.denB);
@@ -444,11 +499,12 @@ __device__ __forceinline__ void quad_frame(const float (&rv)[NY + 2][4], const Q
 
 // All frames of the block with top-left output pixel (X, Y) at scale 1 (X even; Y even
 // when NY = 2): the arithmetic of merge_px at scale 1, with the sharing described above.
-template <bool kDen, int NY>
+template <bool kDen, int NY, bool kChunk = false>
 __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, const int4 *__restrict__ geo,
                                             const Geom &g, const float4 *__restrict__ kern,
                                             const float *__restrict__ rhat_planes, float *__restrict__ rgb,
-                                            float *__restrict__ den_out, int X, int Y) {
+                                            float *__restrict__ den_out, int X, int Y,
+                                            const ChunkIO &io = ChunkIO{}) {
     const int ho = g.h, wo = g.w;
     if (X >= wo || Y >= ho) return;  // both sizes are even: a block is wholly inside or outside
     const int u = X >> 1;
@@ -491,13 +547,26 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
 
     PixelAcc acc[2 * NY];
     const size_t fstride = (size_t)g.h * g.pitch;
+    int it0 = 0;
+    if constexpr (kChunk) {
+        if (io.state_in) {
+#pragma unroll
+            for (int p = 0; p < 2 * NY; ++p) load_state(io, (size_t)(Y + (p >> 1)) * wo + X + (p & 1), acc[p]);
+        }
+        it0 = io.skip_base ? 1 : 0;
+    }
     // frames in the order base frame, then the others; the next frame's geometry and
     // Rhat are fetched while this one is merged
-    int f_nx = g.ref;
-    int4 geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
+    int f_nx = kChunk ? frame_of_step(it0, g.ref) : g.ref;
+    int4 geo_nx = make_int4(0, 0, 0, 0);
     float rh_nx[2 * NY];
-    rhat_at(f_nx, rh_nx);
-    for (int it = 0; it < g.n; ++it) {
+#pragma unroll
+    for (int p = 0; p < 2 * NY; ++p) rh_nx[p] = 1.f;
+    if (!kChunk || it0 < g.n) {
+        geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
+        rhat_at(f_nx, rh_nx);
+    }
+    for (int it = it0; it < g.n; ++it) {
         const int f = f_nx;
         const int4 gq = geo_nx;
         float rh[2 * NY];
@@ -564,6 +633,13 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
         }
     }
     const size_t po = (size_t)ho * wo;
+    if constexpr (kChunk) {
+        if (io.state_out) {
+#pragma unroll
+            for (int p = 0; p < 2 * NY; ++p) store_state(io, (size_t)(Y + (p >> 1)) * wo + X + (p & 1), acc[p]);
+            return;
+        }
+    }
 #pragma unroll
     for (int pb = 0; pb < NY; ++pb) {
         const size_t o = (size_t)(Y + pb) * wo + X;

@@ -155,6 +155,34 @@ size_t carve_merge(void *ws, const Geom &g, MergePlanes *P) {
     return c.off;
 }
 
+// Bounded-memory merge workspace: a sub-burst of slots = min(n, chunk + 1) packed frames
+// (slot 0 the base frame), their motion rows, the merge planes of that sub-burst, and the
+// running sums of every output pixel (9 planes of Ho x Wo floats).
+struct ChunkLayout {
+    uint16_t *sub = nullptr;
+    float *sub_motion = nullptr;
+    MergePlanes P;
+    float *state = nullptr;
+    hmfsr_burst_desc sd;
+    Geom gs;
+};
+
+size_t carve_chunked(void *ws, const hmfsr_burst_desc *d, int tile, int num, int den, int chunk, ChunkLayout *L) {
+    L->sd = *d;
+    L->sd.n_frames = d->n_frames < chunk + 1 ? d->n_frames : chunk + 1;
+    L->sd.pitch_elems = d->width;
+    L->sd.ref = 0;
+    L->gs = make_geom(&L->sd, tile);
+    const size_t ho = (size_t)(((long long)d->height * num) / den), wo = (size_t)(((long long)d->width * num) / den);
+    Carver c(ws);
+    L->sub = c.take<uint16_t>((size_t)L->sd.n_frames * d->height * d->width);
+    L->sub_motion = c.take<float>((size_t)L->sd.n_frames * L->gs.ty * L->gs.tx * 2);
+    const size_t planes = carve_merge(ws ? static_cast<char *>(ws) + c.off : nullptr, L->gs, &L->P);
+    c.off = align_up(c.off + planes);
+    L->state = c.take<float>(9 * ho * wo);
+    return c.off;
+}
+
 MergeConsts consts_of(const hmfsr_merge_params *p) {
     MergeConsts c;
     c.k_detail = p->k_detail; c.k_denoise = p->k_denoise; c.d_th = p->d_th; c.d_tr = p->d_tr;
@@ -358,6 +386,70 @@ hmfsr_status hmfsr_align_merge(const uint16_t *burst_dev, const hmfsr_burst_desc
     if (ea != cudaSuccess || ej != cudaSuccess || ef != cudaSuccess || ew != cudaSuccess) return HMFSR_ERR_CUDA;
     if (launch_merge_prep_motion(motion_dev, g, c, P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
     return cuda_status(launch_merge_accum(burst_dev, motion_dev, g, P, scale_num, scale_den, rgb_dev, den_dev, s));
+}
+
+size_t hmfsr_merge_chunked_workspace_size(const hmfsr_burst_desc *desc, int tile, int scale_num, int scale_den,
+                                          int chunk_frames) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why) || !valid_tile(tile) || !valid_scale(scale_num, scale_den) || chunk_frames < 1 ||
+        chunk_frames > 4096)
+        return 0;
+    ChunkLayout L;
+    return carve_chunked(nullptr, desc, tile, scale_num, scale_den, chunk_frames, &L);
+}
+
+hmfsr_status hmfsr_merge_chunked(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                 const hmfsr_merge_params *params, int scale_num, int scale_den, int chunk_frames,
+                                 float *rgb_dev, float *den_dev, void *ws, size_t ws_bytes, void *stream) {
+    hmfsr_status why;
+    if (!valid_desc(desc, &why)) return why;
+    if (!burst_dev || !motion_dev || !rgb_dev || !aligned4(burst_dev) || !aligned8(motion_dev) ||
+        !valid_merge_params(params) || !valid_scale(scale_num, scale_den) || chunk_frames < 1 || chunk_frames > 4096)
+        return HMFSR_ERR_INVALID_ARG;
+    ChunkLayout L;
+    const size_t need = carve_chunked(nullptr, desc, params->tile, scale_num, scale_den, chunk_frames, &L);
+    hmfsr_status st = check_ws(ws, ws_bytes, need);
+    if (st != HMFSR_OK) return st;
+    carve_chunked(ws, desc, params->tile, scale_num, scale_den, chunk_frames, &L);
+    const Geom g = make_geom(desc, params->tile);
+    cudaStream_t s = (cudaStream_t)stream;
+    const MergeConsts c = consts_of(params);
+    CheckScope chk;
+    chk.add(burst_dev, burst_bytes(desc));
+    chk.add(motion_dev, motion_bytes(g));
+    chk.add(rgb_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add(den_dev, rgb_bytes(desc, scale_num, scale_den));
+    chk.add_ws(ws, need);
+    const size_t frame_px = (size_t)desc->height * desc->width, motion_row = (size_t)g.ty * g.tx * 2;
+    // one frame of the burst into a slot of the packed sub-burst, with its motion row
+    auto put = [&](int f, int slot) -> bool {
+        const uint16_t *src = burst_dev + (size_t)f * desc->height * desc->pitch_elems;
+        if (cudaMemcpy2DAsync(L.sub + (size_t)slot * frame_px, (size_t)desc->width * 2, src,
+                              (size_t)desc->pitch_elems * 2, (size_t)desc->width * 2, desc->height,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return false;
+        return cudaMemcpyAsync(L.sub_motion + (size_t)slot * motion_row, motion_dev + (size_t)f * motion_row,
+                               motion_row * sizeof(float), cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+    };
+    if (!put(desc->ref, 0)) return HMFSR_ERR_CUDA;
+    const int others = desc->n_frames - 1;
+    const int chunks = others > 0 ? (others + chunk_frames - 1) / chunk_frames : 1;
+    for (int ci = 0; ci < chunks; ++ci) {
+        const int o0 = ci * chunk_frames;
+        const int m = others - o0 < chunk_frames ? others - o0 : chunk_frames;
+        for (int j = 0; j < m; ++j) {
+            const int o = o0 + j, f = o < desc->ref ? o : o + 1;  // the others in order
+            if (!put(f, 1 + j)) return HMFSR_ERR_CUDA;
+        }
+        Geom gc = L.gs;
+        gc.n = 1 + (m > 0 ? m : 0);
+        if (launch_merge_prep(L.sub, L.sub_motion, gc, c, L.P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
+        const bool last = (ci == chunks - 1);
+        if (launch_merge_accum_chunk(L.sub, L.sub_motion, gc, L.P, scale_num, scale_den, rgb_dev, den_dev,
+                                     ci > 0 ? L.state : nullptr, last ? nullptr : L.state, ci > 0, s) != cudaSuccess)
+            return HMFSR_ERR_CUDA;
+    }
+    return HMFSR_OK;
 }
 
 hmfsr_status hmfsr_merge_noise(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,

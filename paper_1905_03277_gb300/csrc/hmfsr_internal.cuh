@@ -205,6 +205,12 @@ cudaError_t launch_merge_prep_motion(const float *motion, const Geom &g, const M
                                      cudaStream_t s);
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
                                int snum, int sden, float *rgb, float *den, cudaStream_t s);
+// the accumulation of one chunk of frames of a bounded-memory merge: the running sums
+// from state_in (nullptr: start empty) to state_out (nullptr: normalise into rgb / den);
+// skip_base: the chunk's burst holds the base frame for the statistics only
+cudaError_t launch_merge_accum_chunk(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
+                                     int snum, int sden, float *rgb, float *den, const float *state_in,
+                                     float *state_out, bool skip_base, cudaStream_t s);
 cudaError_t launch_export_stages(const Geom &g, const MergePlanes &P, float *omega, float *rhat, cudaStream_t s);
 
 // adjoint of the merge: buffers beyond the forward planes

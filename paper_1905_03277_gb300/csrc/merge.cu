@@ -74,6 +74,50 @@ __global__ void __launch_bounds__(128, (NY == 2 ? 4 : 5)) k_merge_q1(const uint1
                                  blockIdx.y * 8 * NY + NY * qy);
 }
 
+// The same accumulation for one chunk of frames (bounded-memory merge): the running sums
+// come from and go to the state buffer of `io` (stage::ChunkIO).
+template <bool kDen, int SN, int SD>
+__global__ void __launch_bounds__(kMergeW *kMergeH, 8) k_merge_chunk(const uint16_t *__restrict__ burst,
+                                                                 const int4 *__restrict__ geo, Geom g,
+                                                                 const float4 *__restrict__ kern,
+                                                                 const float *__restrict__ rhat_planes, int snum_rt,
+                                                                 int sden_rt, int ho, int wo, float *__restrict__ rgb,
+                                                                 float *__restrict__ den_out, stage::ChunkIO io) {
+    stage::merge_px<kDen, SN, SD, true>(burst, geo, g, kern, rhat_planes, snum_rt, sden_rt, ho, wo, rgb, den_out,
+                                        blockIdx.x * kMergeW + threadIdx.x, blockIdx.y * kMergeH + threadIdx.y, io);
+}
+
+template <bool kDen, int NY>
+__global__ void __launch_bounds__(128, (NY == 2 ? 4 : 5)) k_merge_q1_chunk(const uint16_t *__restrict__ burst,
+                                                                          const int4 *__restrict__ geo, Geom g,
+                                                                          const float4 *__restrict__ kern,
+                                                                          const float *__restrict__ rhat_planes,
+                                                                          float *__restrict__ rgb,
+                                                                          float *__restrict__ den_out,
+                                                                          stage::ChunkIO io) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qx = (w & 1) * 8 + (lane & 7), qy = (w >> 1) * 4 + (lane >> 3);
+    stage::merge_quad1<kDen, NY, true>(burst, geo, g, kern, rhat_planes, rgb, den_out,
+                                       blockIdx.x * stage::kQuadW + 2 * qx, blockIdx.y * 8 * NY + NY * qy, io);
+}
+
+template <bool kDen>
+static void launch_k_merge_chunk(dim3 grid, cudaStream_t s, const uint16_t *burst, const int4 *mv, const Geom &g,
+                                 const MergePlanes &P, int snum, int sden, int ho, int wo, float *rgb, float *den,
+                                 const stage::ChunkIO &io) {
+    const dim3 block(kMergeW, kMergeH);
+    if (snum == sden)
+        k_merge_q1_chunk<kDen, stage::kQuadNY>
+            <<<dim3(div_up(wo, stage::kQuadW), div_up(ho, 8 * stage::kQuadNY)), 128, 0, s>>>(burst, mv, g, P.kern,
+                                                                                             P.rhat, rgb, den, io);
+    else if (snum == 3 && sden == 2)
+        k_merge_chunk<kDen, 3, 2><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den, io);
+    else if (snum == 2 && sden == 1)
+        k_merge_chunk<kDen, 2, 1><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den, io);
+    else
+        k_merge_chunk<kDen, 0, 0><<<grid, block, 0, s>>>(burst, mv, g, P.kern, P.rhat, snum, sden, ho, wo, rgb, den, io);
+}
+
 template <bool kDen>
 static void launch_k_merge(dim3 grid, cudaStream_t s, const uint16_t *burst, const int4 *mv, const Geom &g,
                            const MergePlanes &P, int snum, int sden, int ho, int wo, float *rgb, float *den) {
@@ -220,6 +264,28 @@ cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const
         launch_k_merge<true>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, den);
     else
         launch_k_merge<false>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_accum_chunk(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,
+                                     int snum, int sden, float *rgb, float *den, const float *state_in,
+                                     float *state_out, bool skip_base, cudaStream_t s) {
+    StageRange range("hmfsr merge: accumulation of one chunk of frames");
+    CheckedLaunches checked(s);
+    const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
+    const dim3 grid(div_up(wo, kMergeW), div_up(ho, kMergeH));
+    const int ntl = g.ty * g.tx;
+    k_geo<<<div_up(g.n * ntl, 128), 128, 0, s>>>(reinterpret_cast<const float2 *>(motion), g.n, ntl, g.ref, 2 * snum,
+                                                 P.geo);
+    stage::ChunkIO io;
+    io.state_in = state_in;
+    io.state_out = state_out;
+    io.skip_base = skip_base ? 1 : 0;
+    io.plane = (size_t)ho * wo;
+    if (den && !state_out)
+        launch_k_merge_chunk<true>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, den, io);
+    else
+        launch_k_merge_chunk<false>(grid, s, burst, P.geo, g, P, snum, sden, ho, wo, rgb, nullptr, io);
     return cudaGetLastError();
 }
 

@@ -161,6 +161,35 @@ def test_align_merge_rejects_bad_arguments_on_host(L):
     assert call(ws_bytes=ws_a + ws_m - 1) == -3
 
 
+def test_chunked_workspace_does_not_grow_with_the_frame_count(L):
+    # the bounded-memory merge's workspace depends on the chunk size and the output size,
+    # not on the frame count (Sec. 6, Table 2)
+    size = lambda n, k, sc=(1, 1): L.hmfsr_merge_chunked_workspace_size(ctypes.byref(desc(n=n, h=512, w=768)), 16,
+                                                                        sc[0], sc[1], k)
+    assert size(8, 2) == size(40, 2) == size(4096, 2) > 0
+    assert size(3, 2) == size(8, 2) and size(2, 2) < size(3, 2)
+    assert size(8, 1) < size(8, 2) < size(8, 4)
+    assert size(8, 2, (2, 1)) > size(8, 2)
+    resident = lambda n: L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(desc(n=n, h=512, w=768)), 16, 1, 1)
+    assert size(40, 2) < resident(40)
+    assert size(8, 0) == 0 and size(8, 4097) == 0 and size(8, 2, (1, 2)) == 0
+
+
+def test_chunked_merge_rejects_bad_arguments_on_host(L):
+    d = desc()
+    p = hm.MergeParams().c()
+
+    def call(k=2, ws_bytes=1 << 40, motion=16):
+        v = lambda x: ctypes.c_void_p(x) if x else None
+        return L.hmfsr_merge_chunked(v(16), ctypes.byref(d), v(motion), ctypes.byref(p), 1, 1, k, v(16), None, v(256),
+                                     ws_bytes, None)
+
+    need = L.hmfsr_merge_chunked_workspace_size(ctypes.byref(d), 16, 1, 1, 2)
+    assert call(k=0) == -1 and call(k=-3) == -1 and call(k=5000) == -1
+    assert call(motion=0) == -1
+    assert call(ws_bytes=need - 1) == -3
+
+
 def test_product_path_does_not_use_the_oracle():
     src_dir = os.path.join(ROOT, "paper_1905_03277_gb300")
     for fn in os.listdir(src_dir):

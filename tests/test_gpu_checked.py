@@ -159,6 +159,26 @@ def test_checked_merge_options_stay_in_bounds(dev, C, tiny_burst):
     assert status(C) == 0 and torch.equal(got, hm.merge_ex(raw, mv, p, (2, 1), noise_table=table, hf_loss=0.03))
 
 
+def test_checked_chunked_merge_stays_in_bounds(dev, C, tiny_burst):
+    status(C)
+    raw = tiny_burst["raw"].to(dev)
+    mv = torch.from_numpy(oracle.align(tiny_burst["raw"].numpy())[1].astype(np.float32)).to(dev)
+    p = hm.MergeParams(noise_a=tiny_burst["gain"], noise_b=tiny_burst["read"] ** 2)
+    for scale, k, ref in [((1, 1), 3, 0), ((3, 2), 2, 5), ((2, 1), 7, 7)]:
+        d = desc_of(raw, ref)
+        ho, wo = hm.out_size(raw.shape[1], raw.shape[2], scale)
+        rgb = torch.full((3, ho, wo), float("nan"), dtype=torch.float32, device=dev)
+        n = C.hmfsr_merge_chunked_workspace_size(ctypes.byref(d), p.tile, scale[0], scale[1], k)
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=dev)
+        off = (-buf.data_ptr()) % 256
+        ws = buf[off:off + n]
+        pc = p.c()
+        _lib.check(C.hmfsr_merge_chunked(ptr(raw), ctypes.byref(d), ptr(mv), ctypes.byref(pc), scale[0], scale[1], k,
+                                         ptr(rgb), None, ptr(ws), ws.numel(), stream(dev)), "checked chunked merge")
+        assert status(C) == 0, (scale, k, ref)
+        assert torch.equal(rgb, hm.merge(raw, mv, p, scale, ref))
+
+
 def test_checker_records_an_access_outside_the_registered_workspace(dev, C, tiny_burst):
     status(C)
     raw = tiny_burst["raw"].to(dev)
