@@ -443,7 +443,10 @@ hmfsr_status hmfsr_merge_chunked(const uint16_t *burst_dev, const hmfsr_burst_de
         }
         Geom gc = L.gs;
         gc.n = 1 + (m > 0 ? m : 0);
-        if (launch_merge_prep(L.sub, L.sub_motion, gc, c, L.P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
+        // the base frame's planes (slot 0) are made by the first chunk and kept
+        if (launch_merge_prep_frames(L.sub, gc, c, L.P, s, ci > 0 ? 1 : 0) != cudaSuccess ||
+            launch_merge_prep_motion(L.sub_motion, gc, c, L.P, s) != cudaSuccess)
+            return HMFSR_ERR_CUDA;
         const bool last = (ci == chunks - 1);
         if (launch_merge_accum_chunk(L.sub, L.sub_motion, gc, L.P, scale_num, scale_den, rgb_dev, den_dev,
                                      ci > 0 ? L.state : nullptr, last ? nullptr : L.state, ci > 0, s) != cudaSuccess)

@@ -199,8 +199,9 @@ cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmf
 // (motion strength and robustness)
 cudaError_t launch_merge_prep(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
                               const MergePlanes &P, cudaStream_t s);
+// first_frame: frames first_frame .. n - 1 only (the planes of the earlier ones are kept)
 cudaError_t launch_merge_prep_frames(const uint16_t *burst, const Geom &g, const MergeConsts &c, const MergePlanes &P,
-                                     cudaStream_t s);
+                                     cudaStream_t s, int first_frame = 0);
 cudaError_t launch_merge_prep_motion(const float *motion, const Geom &g, const MergeConsts &c, const MergePlanes &P,
                                      cudaStream_t s);
 cudaError_t launch_merge_accum(const uint16_t *burst, const float *motion, const Geom &g, const MergePlanes &P,

@@ -12,12 +12,12 @@ namespace {
 using stage::kMergeW;
 using stage::kMergeH;
 
-// 4 warps side by side: 128 texel columns x `rows` rows of one frame
+// 4 warps side by side: 128 texel columns x `rows` rows of frame f0 + blockIdx.z
 __global__ void __launch_bounds__(128) k_prep(const uint16_t *__restrict__ burst, Geom g, MergeConsts c,
                                               uint2 *__restrict__ s1, float4 *__restrict__ base_stats,
-                                              float4 *__restrict__ kern, int rows) {
+                                              float4 *__restrict__ kern, int rows, int f0) {
     stage::prep_strip(burst, g, c, s1, base_stats, kern, blockIdx.x * 128 + (threadIdx.x & ~31),
-                      blockIdx.y * rows, blockIdx.z, threadIdx.x & 31, rows);
+                      blockIdx.y * rows, f0 + blockIdx.z, threadIdx.x & 31, rows);
 }
 
 __global__ void k_strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1, float s2,
@@ -210,13 +210,14 @@ int strip_rows(int slots, long long blocks_per_rows, int hh, int halo, int lo, i
 }  // namespace
 
 cudaError_t launch_merge_prep_frames(const uint16_t *burst, const Geom &g, const MergeConsts &c, const MergePlanes &P,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, int first_frame) {
     StageRange range("hmfsr merge: 3x3 sums, base statistics and kernel covariance");
     CheckedLaunches checked(s);
-    const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * g.n,
+    const int nf = g.n - first_frame;
+    const int prep_rows = fill_rows(strip_slots(SK_PREP, (const void *)k_prep), (long long)div_up(g.wh, 128) * nf,
                                     g.hh, 8, stage::kPrepStrip);
-    k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), g.n), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
-                                                                                   P.kern, prep_rows);
+    k_prep<<<dim3(div_up(g.wh, 128), div_up(g.hh, prep_rows), nf), 128, 0, s>>>(burst, g, c, P.s1, P.base_stats,
+                                                                                  P.kern, prep_rows, first_frame);
     if (c.hf_loss > 0.f && g.n > 1)
         k_hf_flag<<<dim3(div_up(g.wh, 128), g.hh), 128, 0, s>>>(burst, P.s1, g, c.hf_loss, P.hf_flag);
     return cudaGetLastError();

@@ -179,6 +179,30 @@ def test_checked_chunked_merge_stays_in_bounds(dev, C, tiny_burst):
         assert torch.equal(rgb, hm.merge(raw, mv, p, scale, ref))
 
 
+def test_checked_one_call_path_stays_in_bounds(dev, C, tiny_burst):
+    # hmfsr_align_merge: the alignment on the library's side stream, the preparation beside it
+    status(C)
+    raw = tiny_burst["raw"].to(dev)
+    for scale, ref in [((1, 1), 0), ((3, 2), 4), ((2, 1), 7)]:
+        ap = hm.AlignParams()
+        p = hm.MergeParams(noise_a=tiny_burst["gain"], noise_b=tiny_burst["read"] ** 2)
+        d = desc_of(raw, ref)
+        n, h, w = raw.shape
+        ty, tx = hm.n_tiles(h, w, p.tile)
+        ho, wo = hm.out_size(h, w, scale)
+        motion = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=dev)
+        rgb = torch.full((3, ho, wo), float("nan"), dtype=torch.float32, device=dev)
+        _, ws = ws_of(C, _lib.OP_ALIGN_MERGE, d, p.tile, scale, dev)
+        a, m = ap.c(), p.c()
+        _lib.check(C.hmfsr_align_merge(ptr(raw), ctypes.byref(d), ctypes.byref(a), ctypes.byref(m), scale[0], scale[1],
+                                       ptr(motion), None, ptr(rgb), None, ptr(ws), ws.numel(), stream(dev)),
+                   "checked align_merge")
+        assert status(C) == 0, (scale, ref)
+        want_m = hm.align(raw, ref, ap)
+        assert torch.equal(motion, want_m)
+        assert torch.equal(rgb, hm.merge(raw, want_m, p, scale, ref))
+
+
 def test_checker_records_an_access_outside_the_registered_workspace(dev, C, tiny_burst):
     status(C)
     raw = tiny_burst["raw"].to(dev)
