@@ -791,8 +791,15 @@ __device__ __forceinline__ float4 kern_of_tensor(long long ta, long long tb, lon
     float k_al = s_al * s_al, k_ac = s_ac * s_ac;
     // half-angle unit vector e1 = (cos theta, sin theta), without cancellation
     float e1x, e1y;
-    if (cs >= 0.f) { e1x = fast_sqrt(fmaf(0.5f, cs, 0.5f)); e1y = sn * fast_rcp(2.f * e1x); }
-    else { e1y = fast_sqrt(fmaf(-0.5f, cs, 0.5f)); e1x = sn * fast_rcp(2.f * e1y); }
+    {
+        // the larger component from sqrt((1 + |cos 2theta|) / 2), the other from sin 2theta / 2x
+        // it; -0.5 cs for cs < 0 is the same product as 0.5 |cs|, so these are the same values
+        const float big = fast_sqrt(fmaf(0.5f, fabsf(cs), 0.5f));
+        const float other = sn * fast_rcp(2.f * big);
+        const bool pos = cs >= 0.f;
+        e1x = pos ? big : other;
+        e1y = pos ? other : big;
+    }
     // Omega = k_across e1 e1^T + k_along e2 e2^T (stretch along the edge, e2)
     //       = min I + |k_along - k_across| u u^T with u = e2 if k_along >= k_across else e1
     float dh = (1.f - D) * (kh_al - kh_ac) * (s_al + s_ac);  // k_along - k_across, no cancellation
@@ -849,11 +856,14 @@ __device__ __forceinline__ void prep_row(const PrepRow &p, PrepState &st, int r,
     const uint32_t c0 = R | (B << 16), c1 = G | ((R + G + B) << 16);  // {R, B}, {G, Lq}
     uint32_t l0 = __shfl_up_sync(0xffffffffu, c0, 1), l1 = __shfl_up_sync(0xffffffffu, c1, 1);
     uint32_t r0 = __shfl_down_sync(0xffffffffu, c0, 1), r1 = __shfl_down_sync(0xffffffffu, c1, 1);
-    if (lane == 0 || lane == 31) {
+    {
+        // lanes 0 and 31 take the strip's halo quad (p.ha, p.hb; zero in the other lanes)
         const uint32_t hR = p.ha & 0xffffu, hG = (p.ha >> 16) + (p.hb & 0xffffu), hB = p.hb >> 16;
         const uint32_t h0 = hR | (hB << 16), h1 = hG | ((hR + hG + hB) << 16);
-        if (lane == 0) { l0 = h0; l1 = h1; }
-        else { r0 = h0; r1 = h1; }
+        l0 = lane == 0 ? h0 : l0;
+        l1 = lane == 0 ? h1 : l1;
+        r0 = lane == 31 ? h0 : r0;
+        r1 = lane == 31 ? h1 : r1;
     }
     const uint32_t rb = l0 + c0 + r0;                              // R and B halves stay below 2^16
     const uint32_t gs = (l1 & 0xffffu) + G + (r1 & 0xffffu);
