@@ -129,8 +129,10 @@ hmfsr_status hmfsr_merge(const uint16_t *burst_dev, const hmfsr_burst_desc *desc
  * on a library-owned stream of the highest priority (one per device and calling host
  * thread, created on first use and kept until the thread exits); events join the two
  * before the robustness (Eq. 5-9) and the accumulation (Eq. 1-2).  The call is ordered
- * on `stream` like every other entry point and may be captured into a CUDA graph.  Two
- * calls from one host thread share that stream, so their alignments run in call order.
+ * on `stream` like every other entry point and may be captured into a CUDA graph once
+ * the thread has made one call outside capture (the first call creates the side stream
+ * and its two events).  Two calls from one host thread share that stream, so their
+ * alignments run in call order.  `stream` must belong to the current device.
  *   aparams->tile must equal mparams->tile (HMFSR_ERR_INVALID_ARG otherwise).
  *   motion_dev      float32 [n_frames][TY][TX][2], written, as hmfsr_align's.
  *   motion_int_dev  optional, as hmfsr_align's.
