@@ -312,29 +312,15 @@ __device__ __forceinline__ void merge_px(const uint16_t *__restrict__ burst, con
         it0 = io.skip_base ? 1 : 0;
     }
 
-    // frames in the order base frame, then the others; the next frame's geometry and
-    // robustness are fetched while this one is merged
-    int f_nx = g.ref;
-    int4 geo_nx = make_int4(0, 0, 0, 0);
-    float rh_nx = 1.f;
-    if constexpr (kChunk) {
-        if (it0 < g.n) {
-            f_nx = frame_of_step(it0, g.ref);
-            geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
-            rh_nx = rhat_at(f_nx);
-        }
-    } else {
-        geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
-    }
+    // frames in the order base frame, then the others; each frame's geometry and
+    // robustness are read at the top of its own iteration (fetching them a frame ahead
+    // spilled at 1.5x and measured 1.5-3% slower)
+    int f_nx = kChunk ? frame_of_step(it0, g.ref) : g.ref;
     for (int it = it0; it < g.n; ++it) {
         const int f = f_nx;
-        const int4 gq = geo_nx;
-        const float rh = rh_nx;
-        if (it + 1 < g.n) {
-            f_nx = (it + 1 <= g.ref) ? it : it + 1;
-            geo_nx = HMFSR_LDG(geo_px + (size_t)f_nx * ntl);
-            rh_nx = rhat_at(f_nx);
-        }
+        const int4 gq = HMFSR_LDG(geo_px + (size_t)f * ntl);
+        const float rh = rhat_at(f);
+        if (it + 1 < g.n) f_nx = (it + 1 <= g.ref) ? it : it + 1;
         if (!(rh > 0.f)) continue;  // a rejected frame adds nothing
         // window centre k = round(x0 + v) (ties up), exactly: F = floor(Q v)
         const int FX = gq.x, FY = gq.y;
@@ -555,28 +541,16 @@ __device__ __forceinline__ void merge_quad1(const uint16_t *__restrict__ burst, 
         }
         it0 = io.skip_base ? 1 : 0;
     }
-    // frames in the order base frame, then the others; the next frame's geometry and
-    // Rhat are fetched while this one is merged
+    // frames in the order base frame, then the others.  Each frame's geometry and Rhat are
+    // read at the top of its own iteration: fetching the next frame's a frame ahead held 8
+    // more registers through the loop, spilled, and measured 2.5% slower at 12 MP x 8
     int f_nx = kChunk ? frame_of_step(it0, g.ref) : g.ref;
-    int4 geo_nx = make_int4(0, 0, 0, 0);
-    float rh_nx[2 * NY];
-#pragma unroll
-    for (int p = 0; p < 2 * NY; ++p) rh_nx[p] = 1.f;
-    if (!kChunk || it0 < g.n) {
-        geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
-        rhat_at(f_nx, rh_nx);
-    }
     for (int it = it0; it < g.n; ++it) {
         const int f = f_nx;
-        const int4 gq = geo_nx;
+        const int4 gq = HMFSR_LDG(geo_q + (size_t)f * ntl);
         float rh[2 * NY];
-#pragma unroll
-        for (int p = 0; p < 2 * NY; ++p) rh[p] = rh_nx[p];
-        if (it + 1 < g.n) {
-            f_nx = (it + 1 <= g.ref) ? it : it + 1;
-            geo_nx = HMFSR_LDG(geo_q + (size_t)f_nx * ntl);
-            rhat_at(f_nx, rh_nx);
-        }
+        rhat_at(f, rh);
+        if (it + 1 < g.n) f_nx = (it + 1 <= g.ref) ? it : it + 1;
         bool any = false;
 #pragma unroll
         for (int p = 0; p < 2 * NY; ++p) any |= rh[p] > 0.f;
