@@ -526,7 +526,7 @@ def run_gpu(args):
             cpu = {"value": mp / (t_align + t_merge), "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"the whole step once: oracle alignment of the 8-frame 12-MP burst ({t_align:.2f} s) "
                              f"+ oracle merge of all {ho} output rows ({t_merge:.2f} s)"}
-        per_call = hm.launches_per_call(n, h, w, ap.n_levels)
+        per_call = hm.launches_per_call(n, h, w, ap.n_levels, ap.tile, ap.radius[0])
         launches = args.steps * sum(per_call.values())
         merge_only_ms = statistics.median([p_ + a_ for p_, a_ in zip(prep_ms, acc_ms)])
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -501,12 +501,16 @@ def pyramid_levels(h: int, w: int, n_levels_max: int = 4) -> int:
     return nl
 
 
-def launches_per_call(n_frames: int, h: int, w: int, n_levels_max: int = 4) -> dict:
+def launches_per_call(n_frames: int, h: int, w: int, n_levels_max: int = 4, tile: int = 16,
+                      radius0: int = 1) -> dict:
     """Kernel launches made by one hmfsr_align / hmfsr_merge_prepare / accumulate call."""
     nl = pyramid_levels(h, w, n_levels_max)
-    # align: levels 0 and 1 in one launch, levels 2 and 3 in one, one search per level, LK
-    return {"align": 1 + (1 if nl > 2 else 0) + nl + 1, "merge_prepare": 3 if n_frames > 1 else 2,
-            "merge_accumulate": 2}
+    # align: levels 0 and 1 in one launch, levels 2 and 3 in one, one search per level, LK;
+    # with tiles of 16 px or less and radius 1 at level 0, that level's search runs inside
+    # the Lucas-Kanade launch
+    fused = tile <= 16 and radius0 == 1
+    return {"align": 1 + (1 if nl > 2 else 0) + nl + (0 if fused else 1),
+            "merge_prepare": 3 if n_frames > 1 else 2, "merge_accumulate": 2}
 
 
 def merge_static(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1),

@@ -274,6 +274,32 @@ __global__ void __launch_bounds__(128, 6) k_lk_group(const uint16_t *__restrict_
                        blockIdx.y);
 }
 
+// Level 0 searched (radius 1) and refined in one launch: a tile's T / 2 lanes find its
+// integer vector (ssd0_lanes), write it to the level-0 vectors, and run Lucas-Kanade from it.
+template <int T, int PART>
+__global__ void __launch_bounds__(128, 6) k_ssd0_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                                    const int2 *__restrict__ parent, int pty, int ptx, int fsh,
+                                                    int ref, int2 *__restrict__ vec0, int iters,
+                                                    float *__restrict__ motion, int32_t *__restrict__ motion_int) {
+    constexpr int kL = T / 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, f = blockIdx.y;
+    const int tile = t / kL;
+    const bool lead = tile < lty * ltx && (lane & (kL - 1)) == 0;
+    const size_t o = (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        if (lead) {
+            HMFSR_ST(vec0 + o, make_int2(0, 0));
+            HMFSR_ST(motion + 2 * o, 0.f);
+            HMFSR_ST(motion + 2 * o + 1, 0.f);
+            if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
+        }
+        return;
+    }
+    const int2 u = stage::ssd0_lanes<T, PART>(L0, lh, lw, lty, ltx, parent, pty, ptx, fsh, ref, tile, lane, f);
+    if (lead) HMFSR_ST(vec0 + o, u);
+    stage::lk_group_u<T>(L0, lh, lw, lty, ltx, ref, iters, motion, motion_int, tile, lane, f, u);
+}
+
 template <int T>
 __global__ void k_lk(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx, const int2 *__restrict__ vec0,
                      int ref, int iters, float *__restrict__ motion, int32_t *__restrict__ motion_int) {
@@ -325,7 +351,9 @@ static void run_search(const Geom &g, const hmfsr_align_params &p, const AlignLe
                        int32_t *motion_int, cudaStream_t s) {
     static const int kShift[3] = {1, 2, 2};  // log2 of the factors 2, 4, 4
     const int n = g.n;
-    for (int l = L.n_levels - 1; l >= 0; --l) {
+    // level 0 at radius 1 with tiles of at most 8 texels: searched inside the refinement launch
+    const bool fused0 = (T <= 8) && p.radius[0] == 1;
+    for (int l = L.n_levels - 1; l >= (fused0 ? 1 : 0); --l) {
         const bool top = (l == L.n_levels - 1);
         const int fsh = top ? 0 : kShift[l];
         switch (p.radius[l]) {
@@ -340,12 +368,26 @@ static void run_search(const Geom &g, const hmfsr_align_params &p, const AlignLe
         }
     }
     const int tiles0 = L.lty[0] * L.ltx[0];
-    if constexpr (T <= 8)
+    if constexpr (T <= 8) {
+        if (fused0) {
+            const bool top = L.n_levels == 1;
+            const int2 *parent = top ? nullptr : L.vec[1];
+            const int pty = top ? 0 : L.lty[1], ptx = top ? 0 : L.ltx[1], fsh = top ? 0 : kShift[0];
+            const dim3 grid(div_up(tiles0 * (T / 2), 128), n);
+            if (g.wl <= 4095)
+                k_ssd0_lk<T, 16><<<grid, 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0], parent, pty, ptx,
+                                                      fsh, g.ref, L.vec[0], p.lk_iters, motion, motion_int);
+            else
+                k_ssd0_lk<T, 4><<<grid, 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0], parent, pty, ptx,
+                                                     fsh, g.ref, L.vec[0], p.lk_iters, motion, motion_int);
+            return;
+        }
         k_lk_group<T><<<dim3(div_up(tiles0 * (T / 2), 128), n), 128, 0, s>>>(
             L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0], L.vec[0], g.ref, p.lk_iters, motion, motion_int);
-    else
+    } else {
         k_lk<T><<<dim3(div_up(tiles0 * 32, 128), n), 128, 0, s>>>(L.img[0], L.lh[0], L.lw[0], L.lty[0], L.ltx[0],
                                                            L.vec[0], g.ref, p.lk_iters, motion, motion_int);
+    }
 }
 
 template <int T>

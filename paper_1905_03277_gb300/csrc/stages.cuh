@@ -532,27 +532,96 @@ __device__ __forceinline__ void lk(const uint16_t *__restrict__ L0, int lh, int 
 // level).  Sums over the group by butterfly shuffles inside the group; every lane of the
 // warp runs every iteration (a skipped or absent tile adds nothing and keeps its vector),
 // so the shuffles stay converged.  f is the same for the whole warp.
+// Level-0 block matching at radius 1 by a tile's T / 2 refinement lanes (f != ref): lane c
+// of the group sums the squared differences of the tile's columns 2 c and 2 c + 1 for the
+// 9 offsets, rolling over the T + 2 candidate rows it reads (4 columns each); butterfly
+// sums inside the group give every lane the tile's 9 exact sums, and the first-minimum
+// key picks the vector.  The sums, the keys and the clamping are those of ssd_rows, so the
+// vector is the same.  Every lane of the warp calls this.
+template <int T, int PART>
+__device__ __forceinline__ int2 ssd0_lanes(const uint16_t *__restrict__ img, int lh, int lw, int lty, int ltx,
+                                           const int2 *__restrict__ parent, int pty, int ptx, int fsh, int ref,
+                                           int tile, int lane, int f) {
+    static_assert(T == 4 || T == 8, "T / 2 lanes per tile");
+    constexpr int kL = T / 2;
+    constexpr int kRows = PART >= 2 * T ? T : PART / 2;  // rows per 32-bit partial (2 terms a row)
+    const int c = 2 * (lane & (kL - 1));
+    const bool active = tile < lty * ltx;
+    const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
+    const int2 cc = active ? ssd_centre(parent, pty, ptx, fsh, tx, ty, T, f) : make_int2(0, 0);
+    const uint16_t *R = img + (size_t)ref * lh * lw;
+    const uint16_t *A = img + (size_t)f * lh * lw;
+    const int x0 = tx * T, y0 = ty * T;
+    const int rc0 = min(x0 + c, lw - 1), rc1 = min(x0 + c + 1, lw - 1);
+    int ac[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ac[k] = clampi(x0 + cc.x - 1 + c + k, 0, lw - 1);
+    const int ya = y0 + cc.y - 1;  // candidate row r of the window is ya + r, r = 0 .. T + 1
+    int av[3][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const uint16_t *row = A + clampi(ya + r, 0, lh - 1) * lw;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) av[r][k] = HMFSR_LDG(row + ac[k]);
+    }
+    unsigned long long tot[3][3];
+    unsigned int part[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) { tot[a][b] = 0ull; part[a][b] = 0u; }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        const uint16_t *row = A + clampi(ya + j + 2, 0, lh - 1) * lw;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) av[2][k] = HMFSR_LDG(row + ac[k]);
+        const uint16_t *rrow = R + min(y0 + j, lh - 1) * lw;
+        const int rv0 = HMFSR_LDG(rrow + rc0), rv1 = HMFSR_LDG(rrow + rc1);
+#pragma unroll
+        for (int dyi = 0; dyi < 3; ++dyi)
+#pragma unroll
+            for (int dxi = 0; dxi < 3; ++dxi) {
+                const int d0 = rv0 - av[dyi][dxi], d1 = rv1 - av[dyi][dxi + 1];
+                part[dyi][dxi] += (unsigned int)(d0 * d0) + (unsigned int)(d1 * d1);
+            }
+        if ((j + 1) % kRows == 0 || j == T - 1) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) { tot[a][b] += part[a][b]; part[a][b] = 0u; }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { av[0][k] = av[1][k]; av[1][k] = av[2][k]; }
+    }
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            unsigned long long v = tot[a][b];
+#pragma unroll
+            for (int m = kL / 2; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+            const unsigned long long key = ssd_key(v, b - 1, a - 1);
+            best = key < best ? key : best;
+        }
+    const int bdx = (int)(best & 15ull) - 7, bdy = (int)((best >> 4) & 15ull) - 7;
+    return make_int2(cc.x + bdx, cc.y + bdy);
+}
+
+// the refinement of one tile from its integer vector u (f != ref); lk_group below reads u
+// from the level-0 vectors, the fused search-and-refine kernel passes the one it found
 template <int T>
-__device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
-                                         const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
-                                         int32_t *__restrict__ motion_int, int tile, int lane, int f) {
+__device__ __forceinline__ void lk_group_u(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx, int ref,
+                                           int iters, float *__restrict__ motion, int32_t *__restrict__ motion_int,
+                                           int tile, int lane, int f, int2 u) {
     static_assert(T == 4 || T == 8, "T / 2 lanes per tile");
     constexpr int kL = T / 2;
     const int c = 2 * (lane & (kL - 1));
     const bool active = tile < lty * ltx;
     const size_t o = (size_t)f * lty * ltx + tile;
-    if (f == ref) {
-        if (active && c == 0) {
-            HMFSR_ST(motion + 2 * o, 0.f);
-            HMFSR_ST(motion + 2 * o + 1, 0.f);
-            if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
-        }
-        return;
-    }
     const int ty = active ? tile / ltx : 0, tx = active ? tile - (tile / ltx) * ltx : 0;
     const uint16_t *R = L0 + (size_t)ref * lh * lw;
     const uint16_t *A = L0 + (size_t)f * lh * lw;
-    const int2 u = active ? HMFSR_LD(vec0 + o) : make_int2(0, 0);
     // the lane's two pixel columns (clamped into the level) and their gradient neighbours:
     // x0 + 1 is x1's column or, where both clamp to the last column, x0 itself
     const int x0 = min(tx * T + c, lw - 1), x1 = min(tx * T + c + 1, lw - 1);
@@ -675,6 +744,26 @@ __device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh
         HMFSR_ST(motion + 2 * o + 1, 2.f * ((float)u.y + dy));
         if (motion_int) { HMFSR_ST(motion_int + 2 * o, (int32_t)u.x); HMFSR_ST(motion_int + 2 * o + 1, (int32_t)u.y); }
     }
+}
+
+template <int T>
+__device__ __forceinline__ void lk_group(const uint16_t *__restrict__ L0, int lh, int lw, int lty, int ltx,
+                                         const int2 *__restrict__ vec0, int ref, int iters, float *__restrict__ motion,
+                                         int32_t *__restrict__ motion_int, int tile, int lane, int f) {
+    constexpr int kL = T / 2;
+    const int c = 2 * (lane & (kL - 1));
+    const bool active = tile < lty * ltx;
+    const size_t o = (size_t)f * lty * ltx + tile;
+    if (f == ref) {
+        if (active && c == 0) {
+            HMFSR_ST(motion + 2 * o, 0.f);
+            HMFSR_ST(motion + 2 * o + 1, 0.f);
+            if (motion_int) { HMFSR_ST(motion_int + 2 * o, 0); HMFSR_ST(motion_int + 2 * o + 1, 0); }
+        }
+        return;
+    }
+    const int2 u = active ? HMFSR_LD(vec0 + o) : make_int2(0, 0);
+    lk_group_u<T>(L0, lh, lw, lty, ltx, ref, iters, motion, motion_int, tile, lane, f, u);
 }
 
 // Subpixel refinement by a quadratic fit (Sec. 3.2: the variant the paper explored before
