@@ -29,6 +29,17 @@ __device__ __forceinline__ int floor_mul(int q, float v) {
 }
 
 // 2^x on the SFU (ex2.approx, flush-to-zero): relative error ~2^-22.
+// sqrt_rn(x) > t for the FP64 length x = Mx^2 + My^2 (x >= 0 or NaN) and the float t:
+// t^2 is exact in FP64, and a correctly rounded square root is monotone with t
+// representable, so sqrt_rn(x) > t implies x > t^2; the square root itself (a long FP64
+// sequence on this GPU) is then taken only when x > t^2, to settle the rounding at the
+// boundary.  The decision is the same as comparing sqrt_rn(x) with t.
+__device__ __forceinline__ bool length_exceeds(double x, float t) {
+    const double td = (double)t;
+    if (td < 0.0) return x == x;  // a length (not NaN) is >= 0 > t
+    return x > td * td && __dsqrt_rn(x) > td;
+}
+
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -138,8 +138,7 @@ __global__ void k_sel(const float2 *__restrict__ motion, int n, int ty, int tx, 
             mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
         }
     const double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
-    const double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
-    sel[i] = (M > (double)m_th) ? 0 : 1;
+    sel[i] = length_exceeds(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)), m_th) ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------------------

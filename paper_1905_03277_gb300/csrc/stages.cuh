@@ -1049,8 +1049,7 @@ __device__ __forceinline__ bool motion_span_exceeds(const float2 *__restrict__ m
             mny = fminf(mny, v.y); mxy = fmaxf(mxy, v.y);
         }
     double Mx = __dsub_rn((double)mxx, (double)mnx), My = __dsub_rn((double)mxy, (double)mny);
-    double M = __dsqrt_rn(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)));
-    return M > (double)m_th;
+    return length_exceeds(__dadd_rn(__dmul_rn(Mx, Mx), __dmul_rn(My, My)), m_th);
 }
 
 __device__ __forceinline__ void strength(const float2 *__restrict__ motion, int n, int ty, int tx, float m_th, float s1,
