@@ -12,7 +12,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libhmfsr.so")
-SOURCES = ("api.cu", "align.cu", "merge.cu", "merge_bwd.cu", "batch.cu", "merge_static.cu", "tuning.cu", "probe.cu")
+SOURCES = ("api.cu", "align.cu", "align_t4.cu", "align_t8.cu", "align_t16.cu", "align_t32.cu", "merge.cu",
+           "merge_bwd.cu", "batch.cu", "merge_static.cu", "tuning.cu", "probe.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic FMA contraction, so a device function gives the same bits in
 # every kernel it is inlined into (fused multiply-adds are written out with fmaf)
@@ -35,7 +36,7 @@ def _inputs():
 CHECKED_LIB_PATH = os.path.join(PKG, "libhmfsr_checked.so")
 # the units whose kernels the checked build checks (alignment and merge entry points);
 # the others link unchanged from the default build
-CHECKED_SOURCES = ("api.cu", "align.cu", "merge.cu")
+CHECKED_SOURCES = ("api.cu", "align.cu", "align_t4.cu", "align_t8.cu", "align_t16.cu", "align_t32.cu", "merge.cu")
 
 
 def _compile(nvcc, src, obj, extra, verbose):

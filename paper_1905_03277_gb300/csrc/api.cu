@@ -16,7 +16,9 @@ namespace {
 
 // the buffers of the entry-point call running on this host thread (checked build)
 thread_local CheckRanges t_check = {};
+#ifdef HMFSR_CHECKED
 size_t g_check_shrink = 0;  // test hook of the checked build: bytes taken off each registered workspace
+#endif
 
 // For the duration of one entry-point call: the caller's buffers, as its kernels may read
 // and write them (checked build; nothing in the default build).

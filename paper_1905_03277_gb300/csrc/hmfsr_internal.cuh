@@ -201,6 +201,13 @@ struct AlignLevels {
 };
 cudaError_t launch_align(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p, const AlignLevels &L,
                          float *motion, int32_t *motion_int, cudaStream_t s);
+// the searches and refinement for tiles of T level texels (one translation unit per T)
+template <int T>
+cudaError_t align_search_tiles(const Geom &g, const hmfsr_align_params &p, const AlignLevels &L, float *motion,
+                               int32_t *motion_int, cudaStream_t s);
+template <int T>
+cudaError_t align_quadfit_tiles(const Geom &g, const AlignLevels &L, float *motion, int32_t *motion_int,
+                                cudaStream_t s);
 // the same search, then the quadratic-fit subpixel step instead of Lucas-Kanade
 cudaError_t launch_align_quadfit(const uint16_t *burst, const Geom &g, const hmfsr_align_params &p,
                                  const AlignLevels &L, float *motion, int32_t *motion_int, cudaStream_t s);
