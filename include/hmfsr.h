@@ -192,7 +192,11 @@ hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_des
  *   grad_motion_dev  float32 [n_frames][TY][TX][2]: dL/dmotion (0 for the base frame).
  * Discrete decisions (window centres, tiles, s1/s2 selection, clamps, the 5x5 argmin)
  * carry no gradient.  The forward is recomputed from the burst; the reduction order is
- * fixed, so results are deterministic.  Workspace: HMFSR_OP_MERGE_BACKWARD. */
+ * fixed, so results are deterministic.  Workspace: HMFSR_OP_MERGE_BACKWARD.  Like
+ * hmfsr_align_merge, the call runs independent parts on the calling thread's side stream
+ * (the kernel-shape derivatives beside the preparation, the robustness derivatives beside
+ * the main adjoint kernel), joined by events: it is ordered on `stream`, and may be
+ * captured once the thread has made one call of either outside capture. */
 hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
                                   const hmfsr_merge_params *params, int scale_num, int scale_den,
                                   const float *rgb_dev, const float *den_dev, const float *grad_rgb_dev,

@@ -210,10 +210,11 @@ hmfsr_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HMFSR_OK : H
 // events that fork it from, and join it back to, the caller's stream.
 struct SideStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, aux = nullptr;
     ~SideStream() {
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);
+        if (aux) cudaEventDestroy(aux);
         if (s) cudaStreamDestroy(s);
     }
 };
@@ -229,17 +230,20 @@ SideStream *side_stream() {
     int least = 0, greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
     cudaStream_t s = nullptr;
-    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr, x = nullptr;
     if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) {
         if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
         if (s) cudaStreamDestroy(s);
         return nullptr;
     }
     ss.s = s;
     ss.fork = a;
     ss.join = b;
+    ss.aux = x;
     return &ss;
 }
 
@@ -609,10 +613,33 @@ hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_d
     carve_backward(ws, g, ho, wo, fwd, &B);
     cudaStream_t s = (cudaStream_t)stream;
     const MergeConsts c = consts_of(params);
-    if (launch_merge_prep(burst_dev, motion_dev, g, c, P, s) != cudaSuccess) return HMFSR_ERR_CUDA;
-    return cuda_status(launch_merge_backward(burst_dev, motion_dev, g, c, P, B, scale_num, scale_den, rgb_dev, den_dev,
-                                             grad_rgb_dev, grad_params_dev, grad_motion_dev, s));
+    SideStream *side = side_stream();
+    if (!side) return HMFSR_ERR_CUDA;
+    StageRange range("hmfsr merge adjoint");
+    // the kernel-shape derivatives (burst only) beside the preparation; the robustness
+    // derivatives (after the preparation) beside the main adjoint kernel; both joined
+    // before the parts that read them
+    cudaError_t e[10];
+    e[0] = cudaEventRecord(side->fork, s);
+    e[1] = cudaStreamWaitEvent(side->s, side->fork, 0);
+    e[2] = launch_bwd_shape(burst_dev, g, B, side->s);
+    e[3] = cudaEventRecord(side->join, side->s);
+    e[4] = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
+    e[5] = cudaEventRecord(side->aux, s);
+    e[6] = cudaStreamWaitEvent(side->s, side->aux, 0);
+    e[7] = launch_bwd_robust(motion_dev, g, c, P, B, side->s);
+    // the robustness part's completion, recorded after every wait above has been enqueued
+    e[8] = cudaEventRecord(side->fork, side->s);
+    e[9] = cudaStreamWaitEvent(s, side->join, 0);
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return HMFSR_ERR_CUDA;
+    if (launch_bwd_main(burst_dev, motion_dev, g, c, P, B, scale_num, scale_den, rgb_dev, den_dev, grad_rgb_dev, s) !=
+            cudaSuccess ||
+        cudaStreamWaitEvent(s, side->fork, 0) != cudaSuccess)
+        return HMFSR_ERR_CUDA;
+    return cuda_status(launch_bwd_finish(g, B, scale_num, scale_den, grad_params_dev, grad_motion_dev, s));
 }
+
 
 const char *hmfsr_status_string(hmfsr_status s) {
     switch (s) {

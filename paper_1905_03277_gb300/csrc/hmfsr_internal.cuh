@@ -248,9 +248,15 @@ struct BwdPlanes {
     int n_bwd_blocks, n_rp_blocks;
 };
 size_t carve_backward(void *ws, const Geom &g, int ho, int wo, size_t fwd_bytes, BwdPlanes *B);
-cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
-                                  const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
-                                  const float *lden, const float *grad_rgb, float *grad_params, float *grad_motion,
-                                  cudaStream_t s);
+// the adjoint's four parts (merge_bwd.cu): shape, then robust (after the preparation),
+// main (after shape and the preparation), finish (after robust and main)
+cudaError_t launch_bwd_shape(const uint16_t *burst, const Geom &g, const BwdPlanes &B, cudaStream_t s);
+cudaError_t launch_bwd_robust(const float *motion, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                              const BwdPlanes &B, cudaStream_t s);
+cudaError_t launch_bwd_main(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                            const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
+                            const float *lden, const float *grad_rgb, cudaStream_t s);
+cudaError_t launch_bwd_finish(const Geom &g, const BwdPlanes &B, int snum, int sden, float *grad_params,
+                              float *grad_motion, cudaStream_t s);
 
 }  // namespace hmfsr

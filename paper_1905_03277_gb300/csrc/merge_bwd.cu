@@ -650,23 +650,44 @@ size_t carve_backward(void *ws, const Geom &g, int ho, int wo, size_t fwd_bytes,
     return off;
 }
 
-cudaError_t launch_merge_backward(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
-                                  const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
-                                  const float *lden, const float *grad_rgb, float *grad_params, float *grad_motion,
-                                  cudaStream_t s) {
-    StageRange range("hmfsr merge adjoint");
-    const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
-    const float2 *mv = reinterpret_cast<const float2 *>(motion);
+// The adjoint in four parts (the call orders them; see hmfsr_merge_backward):
+//   shape  -- k_shape: the kernel-shape derivatives of every texel (needs the burst only)
+//   robust -- k_sel, k_rback, k_argmin: the robustness derivatives (needs the preparation)
+//   main   -- k_merge_bwd and the R-hat-bar gather (needs shape and the preparation)
+//   finish -- k_rpath and the two reductions (needs robust and main)
+cudaError_t launch_bwd_shape(const uint16_t *burst, const Geom &g, const BwdPlanes &B, cudaStream_t s) {
     const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
     k_shape<<<tex_grid, 128, 0, s>>>(burst, g.h, g.pitch, g.hh, g.wh, g.wl, B.shape);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_robust(const float *motion, const Geom &g, const MergeConsts &c, const MergePlanes &P,
+                              const BwdPlanes &B, cudaStream_t s) {
+    const float2 *mv = reinterpret_cast<const float2 *>(motion);
+    const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
     k_sel<<<div_up(g.n * g.ty * g.tx, 128), 128, 0, s>>>(mv, g.n, g.ty, g.tx, c.m_th, B.sel);
     k_rback<<<tex_grid, 128, 0, s>>>(P.s1, P.base_stats, mv, P.s_tile, B.sel, g, c, B.rb, B.flags);
     k_argmin<<<tex_grid, 128, 0, s>>>(B.rb, g, B.flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_main(const uint16_t *burst, const float *motion, const Geom &g, const MergeConsts &c,
+                            const MergePlanes &P, const BwdPlanes &B, int snum, int sden, const float *rgb,
+                            const float *lden, const float *grad_rgb, cudaStream_t s) {
+    const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
+    const float2 *mv = reinterpret_cast<const float2 *>(motion);
+    const dim3 tex_grid(div_up(g.wh, 128), g.hh, g.n);
     k_merge_bwd<<<dim3(div_up(wo, kBwdW), div_up(ho, kBwdH)), dim3(kBwdW, kBwdH), 0, s>>>(
         burst, mv, g, c, P.kern, B.shape, P.rhat, snum, sden, ho, wo, rgb, lden, grad_rgb, B.vbar_pix, B.rhbar_pix,
         B.part6);
     k_rhat_rows<<<dim3(div_up(g.wh, 128), ho, g.n), 128, 0, s>>>(B.rhbar_pix, g, snum, sden, ho, wo, B.rhbar_rows);
     k_rhat_cols<<<tex_grid, 128, 0, s>>>(B.rhbar_rows, g, snum, sden, ho, B.rhbar_tex);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_finish(const Geom &g, const BwdPlanes &B, int snum, int sden, float *grad_params,
+                              float *grad_motion, cudaStream_t s) {
+    const int ho = (int)(((long long)g.h * snum) / sden), wo = (int)(((long long)g.w * snum) / sden);
     k_rpath<<<dim3(div_up(g.wh, kRpThreads), g.hh, g.n), kRpThreads, 0, s>>>(B.rhbar_tex, B.flags, B.rb, g,
                                                                            B.vbar_tex, B.part2);
     k_motion_reduce<<<div_up(g.n * g.ty * g.tx, kRedThreads / 32), kRedThreads, 0, s>>>(B.vbar_pix, B.vbar_tex, g, snum,
