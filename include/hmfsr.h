@@ -203,6 +203,18 @@ hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_d
                                   float *grad_params_dev, float *grad_motion_dev, void *ws, size_t ws_bytes,
                                   void *stream);
 
+/* hmfsr_merge_backward that reuses the forward's per-frame planes: `ws` (sized for
+ * HMFSR_OP_MERGE_BACKWARD) was the workspace of an hmfsr_merge call with the same burst,
+ * desc, motion, params and scale, and nothing has written it since.  hmfsr_merge lays
+ * its planes at the start of the workspace, where the adjoint looks for them, so the
+ * preparation (kernel covariances, robustness) is not recomputed; results are those of
+ * hmfsr_merge_backward.  The library cannot check the precondition. */
+hmfsr_status hmfsr_merge_backward_prepared(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                                           const float *motion_dev, const hmfsr_merge_params *params, int scale_num,
+                                           int scale_den, const float *rgb_dev, const float *den_dev,
+                                           const float *grad_rgb_dev, float *grad_params_dev, float *grad_motion_dev,
+                                           void *ws, size_t ws_bytes, void *stream);
+
 /* hmfsr_merge without a workspace argument, for callers that cannot allocate device
  * memory where they merge (inside another framework's memory pool, on a real-time
  * capture path where cudaMalloc could stall other streams, or behind a plugin interface

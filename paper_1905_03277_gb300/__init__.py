@@ -154,10 +154,32 @@ def align(burst: torch.Tensor, ref: int = 0, params: AlignParams | None = None, 
     return (motion, mint) if with_int else motion
 
 
+def _own_workspace(workspace: torch.Tensor, nbytes: int, device) -> torch.Tensor:
+    """A caller's workspace tensor checked for the library: uint8 on the device, at least
+    nbytes, 256-byte aligned."""
+    if (workspace.dtype != torch.uint8 or not workspace.is_cuda or workspace.device != device
+            or not workspace.is_contiguous() or workspace.numel() < nbytes or workspace.data_ptr() % 256):
+        raise ValueError(f"workspace must be a contiguous, 256-byte aligned uint8 tensor of at least {nbytes} "
+                         "bytes on the burst's device")
+    return workspace
+
+
+def backward_workspace(burst_shape, tile: int = 16, scale=(1, 1), device=None, white_level: int = 4095):
+    """A workspace for `merge` followed by `merge_backward(..., prepared=True)`: sized for
+    the adjoint, 256-byte aligned."""
+    nbytes = workspace_size(_lib.OP_MERGE_BACKWARD, burst_shape, tile, scale, white_level)
+    if nbytes == 0:
+        raise ValueError("unsupported burst shape, tile or scale")
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + nbytes]
+
+
 def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None = None, scale=(1, 1), ref: int = 0,
-          with_den: bool = False, white_level: int = 4095, stream=None):
+          with_den: bool = False, white_level: int = 4095, stream=None, workspace: torch.Tensor | None = None):
     """Merged RGB float32 [3, Ho, Wo] in DN (hmfsr_merge).  With `with_den`, also the
-    per-channel log2 of Eq. 1's denominator."""
+    per-channel log2 of Eq. 1's denominator.  `workspace`: the caller's scratch (e.g. from
+    `backward_workspace`, so that `merge_backward(..., prepared=True)` reuses its planes)."""
     L = _lib.load()
     params = params or MergeParams()
     d = _merge_inputs(burst, motion, params, ref, white_level)
@@ -166,7 +188,8 @@ def merge(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams | None 
     rgb = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device)
     den = torch.empty((3, ho, wo), dtype=torch.float32, device=burst.device) if with_den else None
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes, stream)
+    ws = _own_workspace(workspace, nbytes, burst.device) if workspace is not None else \
+        _workspace(burst.device, nbytes, stream)
     pc = params.c()
     _lib.check(L.hmfsr_merge(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1],
                              _ptr(rgb), _ptr(den), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
@@ -535,10 +558,14 @@ PARAM_NAMES = ("k_detail", "k_denoise", "d_th", "d_tr", "k_stretch", "k_shrink",
 
 def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParams, rgb: torch.Tensor,
                    den: torch.Tensor, grad_rgb: torch.Tensor, scale=(1, 1), ref: int = 0, white_level: int = 4095,
-                   stream=None):
+                   stream=None, workspace: torch.Tensor | None = None, prepared: bool = False):
     """Adjoint of `merge` (hmfsr_merge_backward): (dL/dparams float32 [8] in PARAM_NAMES
     order, dL/dmotion float32 [n, TY, TX, 2]) for grad_rgb = dL/drgb, given the forward's
-    rgb and den (merge(..., with_den=True))."""
+    rgb and den (merge(..., with_den=True)).  With `prepared`, `workspace` is the one the
+    forward `merge` used with these arguments (hmfsr_merge_backward_prepared: its planes
+    are reused, not recomputed)."""
+    if prepared and workspace is None:
+        raise ValueError("prepared=True needs the forward's workspace")
     L = _lib.load()
     d = _merge_inputs(burst, motion, params, ref, white_level, rgb, den, grad_rgb)
     n, h, w = burst.shape
@@ -554,11 +581,13 @@ def merge_backward(burst: torch.Tensor, motion: torch.Tensor, params: MergeParam
     gm = torch.empty((n, ty, tx, 2), dtype=torch.float32, device=burst.device)
     grad_rgb = grad_rgb.contiguous().float()
     nbytes = L.hmfsr_workspace_size(_lib.OP_MERGE_BACKWARD, ctypes.byref(d), params.tile, scale[0], scale[1])
-    ws = _workspace(burst.device, nbytes, stream)
+    ws = _own_workspace(workspace, nbytes, burst.device) if workspace is not None else \
+        _workspace(burst.device, nbytes, stream)
     pc = params.c()
-    _lib.check(L.hmfsr_merge_backward(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0],
-                                      scale[1], _ptr(rgb), _ptr(den), _ptr(grad_rgb), _ptr(gp), _ptr(gm), _ptr(ws),
-                                      ws.numel(), _stream(burst.device, stream)), "hmfsr_merge_backward")
+    fn = L.hmfsr_merge_backward_prepared if prepared else L.hmfsr_merge_backward
+    _lib.check(fn(_ptr(burst), ctypes.byref(d), _ptr(motion), ctypes.byref(pc), scale[0], scale[1], _ptr(rgb),
+                  _ptr(den), _ptr(grad_rgb), _ptr(gp), _ptr(gm), _ptr(ws), ws.numel(), _stream(burst.device, stream)),
+               "hmfsr_merge_backward")
     return gp, gm
 
 
@@ -574,16 +603,21 @@ class MergeFn(torch.autograd.Function):
         vals = [float(x) for x in (values if values is not None else theta.detach().cpu().tolist())]
         p = MergeParams(**{**base.__dict__, **dict(zip(PARAM_NAMES, vals))})
         motion_c = motion.detach().contiguous()
-        rgb, den = merge(burst, motion_c, p, scale, ref, with_den=True)
+        # the forward's planes stay in a workspace of the adjoint's size, which the
+        # backward reuses instead of preparing them again
+        ws = backward_workspace(tuple(burst.shape), p.tile, scale, burst.device)
+        rgb, den = merge(burst, motion_c, p, scale, ref, with_den=True, workspace=ws)
         ctx.save_for_backward(motion_c, rgb, den)
-        ctx.burst, ctx.p, ctx.scale, ctx.ref = burst, p, scale, ref
+        ctx.burst, ctx.p, ctx.scale, ctx.ref, ctx.ws = burst, p, scale, ref, ws
         ctx.theta_device = theta.device
         return rgb
 
     @staticmethod
     def backward(ctx, grad_rgb):
         motion_c, rgb, den = ctx.saved_tensors
-        gp, gm = merge_backward(ctx.burst, motion_c, ctx.p, rgb, den, grad_rgb, ctx.scale, ctx.ref)
+        gp, gm = merge_backward(ctx.burst, motion_c, ctx.p, rgb, den, grad_rgb, ctx.scale, ctx.ref, workspace=ctx.ws,
+                                prepared=True)
+        ctx.ws = None
         return gp.to(ctx.theta_device), gm, None, None, None, None, None
 
 

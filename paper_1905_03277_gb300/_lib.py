@@ -115,7 +115,8 @@ OP_ALIGN, OP_MERGE, OP_MERGE_STAGES, OP_MERGE_BACKWARD, OP_ALIGN_MERGE = 0, 1, 2
 PIPE_FP32_FMA, PIPE_MUFU_EX2 = 0, 1
 NOISE_LEVELS = 129
 EXPORTS = ("hmfsr_workspace_size", "hmfsr_align", "hmfsr_merge", "hmfsr_align_merge", "hmfsr_merge_chunked", "hmfsr_merge_chunked_workspace_size", "hmfsr_merge_prepare", "hmfsr_merge_accumulate",
-           "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_static", "hmfsr_batch_plan_create",
+           "hmfsr_merge_stages", "hmfsr_merge_backward", "hmfsr_merge_backward_prepared", "hmfsr_merge_static",
+           "hmfsr_batch_plan_create",
            "hmfsr_batch_workspace_size", "hmfsr_batch_run", "hmfsr_batch_wait", "hmfsr_batch_vectors",
            "hmfsr_batch_set_profile", "hmfsr_batch_stage_profile", "hmfsr_batch_configure",
            "hmfsr_batch_tune", "hmfsr_batch_set_mode", "hmfsr_batch_free", "hmfsr_frame_sum", "hmfsr_snr_tuning",
@@ -163,6 +164,8 @@ def open_library(path: str):
     L.hmfsr_merge_stages.restype = ci
     L.hmfsr_merge_backward.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp, vp, vp, vp, sz, vp]
     L.hmfsr_merge_backward.restype = ci
+    L.hmfsr_merge_backward_prepared.argtypes = L.hmfsr_merge_backward.argtypes
+    L.hmfsr_merge_backward_prepared.restype = ci
     L.hmfsr_merge_static.argtypes = [vp, P(BurstDesc), vp, P(MergeParamsC), ci, ci, vp, vp, vp]
     L.hmfsr_merge_static.restype = ci
     pp = P(vp)

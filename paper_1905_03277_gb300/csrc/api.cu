@@ -591,11 +591,13 @@ hmfsr_status hmfsr_merge_stages(const uint16_t *burst_dev, const hmfsr_burst_des
     return cuda_status(launch_export_stages(g, P, omega_dev, rhat_dev, s));
 }
 
-hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
-                                  const hmfsr_merge_params *params, int scale_num, int scale_den,
-                                  const float *rgb_dev, const float *den_dev, const float *grad_rgb_dev,
-                                  float *grad_params_dev, float *grad_motion_dev, void *ws, size_t ws_bytes,
-                                  void *stream) {
+namespace {
+// the adjoint; prepared: the workspace already holds this call's merge planes (an
+// hmfsr_merge with the same arguments on the same workspace), so the preparation is skipped
+hmfsr_status merge_backward_impl(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                 const hmfsr_merge_params *params, int scale_num, int scale_den, const float *rgb_dev,
+                                 const float *den_dev, const float *grad_rgb_dev, float *grad_params_dev,
+                                 float *grad_motion_dev, void *ws, size_t ws_bytes, void *stream, bool prepared) {
     hmfsr_status why;
     if (!valid_desc(desc, &why)) return why;
     if (!burst_dev || !motion_dev || !rgb_dev || !den_dev || !grad_rgb_dev || !grad_params_dev || !grad_motion_dev ||
@@ -624,7 +626,7 @@ hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_d
     e[1] = cudaStreamWaitEvent(side->s, side->fork, 0);
     e[2] = launch_bwd_shape(burst_dev, g, B, side->s);
     e[3] = cudaEventRecord(side->join, side->s);
-    e[4] = launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
+    e[4] = prepared ? cudaSuccess : launch_merge_prep(burst_dev, motion_dev, g, c, P, s);
     e[5] = cudaEventRecord(side->aux, s);
     e[6] = cudaStreamWaitEvent(side->s, side->aux, 0);
     e[7] = launch_bwd_robust(motion_dev, g, c, P, B, side->s);
@@ -638,6 +640,25 @@ hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_d
         cudaStreamWaitEvent(s, side->fork, 0) != cudaSuccess)
         return HMFSR_ERR_CUDA;
     return cuda_status(launch_bwd_finish(g, B, scale_num, scale_den, grad_params_dev, grad_motion_dev, s));
+}
+}  // namespace
+
+hmfsr_status hmfsr_merge_backward(const uint16_t *burst_dev, const hmfsr_burst_desc *desc, const float *motion_dev,
+                                  const hmfsr_merge_params *params, int scale_num, int scale_den,
+                                  const float *rgb_dev, const float *den_dev, const float *grad_rgb_dev,
+                                  float *grad_params_dev, float *grad_motion_dev, void *ws, size_t ws_bytes,
+                                  void *stream) {
+    return merge_backward_impl(burst_dev, desc, motion_dev, params, scale_num, scale_den, rgb_dev, den_dev,
+                               grad_rgb_dev, grad_params_dev, grad_motion_dev, ws, ws_bytes, stream, false);
+}
+
+hmfsr_status hmfsr_merge_backward_prepared(const uint16_t *burst_dev, const hmfsr_burst_desc *desc,
+                                           const float *motion_dev, const hmfsr_merge_params *params, int scale_num,
+                                           int scale_den, const float *rgb_dev, const float *den_dev,
+                                           const float *grad_rgb_dev, float *grad_params_dev, float *grad_motion_dev,
+                                           void *ws, size_t ws_bytes, void *stream) {
+    return merge_backward_impl(burst_dev, desc, motion_dev, params, scale_num, scale_den, rgb_dev, den_dev,
+                               grad_rgb_dev, grad_params_dev, grad_motion_dev, ws, ws_bytes, stream, true);
 }
 
 

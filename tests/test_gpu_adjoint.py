@@ -121,3 +121,22 @@ def test_fit_lowers_loss_against_ground_truth(dev):
     params, hist, motions = fit(bursts, gts, base, steps=15, scale=(3, 2))
     assert hist[-1] < hist[0]
     assert all(getattr(params, k) > 0 for k in hm.PARAM_NAMES)
+
+
+@pytest.mark.parametrize("scale", [(1, 1), (3, 2), (2, 1)])
+def test_prepared_adjoint_equals_full_adjoint(dev, scale):
+    # hmfsr_merge_backward_prepared on the forward's workspace gives the same bits as the
+    # adjoint that prepares the planes itself
+    raw, mv, p, g = case(31, 64, 96, 4, scale)
+    b = torch.from_numpy(raw).to(dev)
+    m = torch.from_numpy(mv).to(dev)
+    gr = torch.from_numpy(g.astype(np.float32)).to(dev)
+    ws = hm.backward_workspace(tuple(b.shape), p.tile, scale, dev)
+    rgb, den = hm.merge(b, m, p, scale, with_den=True, workspace=ws)
+    assert torch.equal(rgb, hm.merge(b, m, p, scale))
+    gp1, gm1 = hm.merge_backward(b, m, p, rgb, den, gr, scale, workspace=ws, prepared=True)
+    gp0, gm0 = hm.merge_backward(b, m, p, rgb, den, gr, scale)
+    torch.cuda.synchronize()
+    assert torch.equal(gp1, gp0) and torch.equal(gm1, gm0)
+    with pytest.raises(ValueError):
+        hm.merge_backward(b, m, p, rgb, den, gr, scale, prepared=True)
