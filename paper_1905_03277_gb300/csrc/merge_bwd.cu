@@ -446,31 +446,77 @@ __device__ __forceinline__ float rhat_weight(int X, int t, int nt, int snum, int
     return (rx0 == t ? 1.f - fx : 0.f) + (rx1 == t ? fx : 0.f);
 }
 
-__global__ void k_rhat_rows(const float *__restrict__ rhbar_pix, Geom g, int snum, int sden, int ho, int wo,
-                            float *__restrict__ rows) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y, f = blockIdx.z;
-    if (u >= g.wh || f == g.ref) return;
+// the forward's two taps of output pixel X (along one axis): texels rx and rx + 1 (before
+// clamping) with weights 1 - fx and fx -- the quantities rhat_weight derives per texel
+__device__ __forceinline__ void rhat_taps(int X, int snum, int sden, int &rx, float &fx) {
+    const int Q2 = 4 * snum;
+    const float inv2Q = 0.25f / (float)snum;
+    const int Px = 2 * sden * X + sden - snum;
+    rx = floor_div(Px - snum, Q2);
+    fx = (float)(Px - snum - rx * Q2) * inv2Q;
+}
+
+// the output pixels one block of 128 texel columns reads: at most 4 x 128 + 2 x 13 at 4x
+constexpr int kRhatSpan = 1024 + 64;
+
+// R-hat-bar along x: for each output row, texel column u gathers the taps of the output
+// pixels in its range.  The block's pixels' taps are derived once into shared memory,
+// then every texel sums its own, in pixel order (the sums rhat_weight would give).
+__global__ void __launch_bounds__(128) k_rhat_rows(const float *__restrict__ rhbar_pix, Geom g, int snum, int sden,
+                                                   int ho, int wo, float *__restrict__ rows) {
+    __shared__ int s_rx[kRhatSpan];
+    __shared__ float s_fx[kRhatSpan];
+    const int u0 = blockIdx.x * blockDim.x, u = u0 + threadIdx.x, Y = blockIdx.y, f = blockIdx.z;
+    if (f == g.ref) return;  // the whole block
+    int lo0, hi0, lo1, hi1;
+    rhat_range(u0, g.wh, wo, snum, sden, lo0, hi0);
+    rhat_range(min(u0 + (int)blockDim.x - 1, g.wh - 1), g.wh, wo, snum, sden, lo1, hi1);
+    const int xs = lo0, xn = hi1 - lo0 + 1;  // the ranges grow with u: the block reads [lo0, hi1]
+    const bool staged = xn <= kRhatSpan;
+    if (staged) {
+        for (int k = threadIdx.x; k < xn; k += blockDim.x) rhat_taps(xs + k, snum, sden, s_rx[k], s_fx[k]);
+    }
+    __syncthreads();
+    if (u >= g.wh) return;
     int lo, hi;
     rhat_range(u, g.wh, wo, snum, sden, lo, hi);
     const float *row = rhbar_pix + (size_t)f * ho * wo + (size_t)Y * wo;
     float acc = 0.f;
     for (int X = lo; X <= hi; ++X) {
-        const float w = rhat_weight(X, u, g.wh, snum, sden);
+        float w;
+        if (staged) {
+            const int rx = s_rx[X - xs];
+            const float fx = s_fx[X - xs];
+            const int rx0 = clampi(rx, 0, g.wh - 1), rx1 = clampi(rx + 1, 0, g.wh - 1);
+            w = (rx0 == u ? 1.f - fx : 0.f) + (rx1 == u ? fx : 0.f);
+        } else {
+            w = rhat_weight(X, u, g.wh, snum, sden);
+        }
         if (w != 0.f) acc = fmaf(w, __ldg(row + X), acc);
     }
     rows[((size_t)f * ho + Y) * g.wh + u] = acc;
 }
 
-__global__ void k_rhat_cols(const float *__restrict__ rows, Geom g, int snum, int sden, int ho,
-                            float *__restrict__ rhbar_tex) {
+// R-hat-bar along y: the block's texels share their row v, so the weights of the output
+// rows in v's range are derived once into shared memory (the values rhat_weight gives)
+__global__ void __launch_bounds__(128) k_rhat_cols(const float *__restrict__ rows, Geom g, int snum, int sden,
+                                                   int ho, float *__restrict__ rhbar_tex) {
+    __shared__ float s_w[kRhatSpan];
     const int u = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.y, f = blockIdx.z;
-    if (u >= g.wh || f == g.ref) return;
+    if (f == g.ref) return;  // the whole block
     int lo, hi;
     rhat_range(v, g.hh, ho, snum, sden, lo, hi);
+    const int yn = hi - lo + 1;
+    const bool staged = yn <= kRhatSpan;
+    if (staged) {
+        for (int k = threadIdx.x; k < yn; k += blockDim.x) s_w[k] = rhat_weight(lo + k, v, g.hh, snum, sden);
+    }
+    __syncthreads();
+    if (u >= g.wh) return;
     const float *col = rows + (size_t)f * ho * g.wh + u;
     float acc = 0.f;
     for (int Y = lo; Y <= hi; ++Y) {
-        const float w = rhat_weight(Y, v, g.hh, snum, sden);
+        const float w = staged ? s_w[Y - lo] : rhat_weight(Y, v, g.hh, snum, sden);
         if (w != 0.f) acc = fmaf(w, __ldg(col + (size_t)Y * g.wh), acc);
     }
     rhbar_tex[(size_t)f * g.hh * g.wh + (size_t)v * g.wh + u] = acc;
